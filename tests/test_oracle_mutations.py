@@ -1,0 +1,91 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case monkeypatches one plausible error into the oracle (on the CPU) and
+checks that the corresponding closed-form pin no longer holds, so the pins
+are shown to be sensitive to that class of mistake.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import chfsi, fe, hamiltonian as ham
+
+FREE = 0.5 * (2 * np.pi / 10.0) ** 2
+
+
+def _free_first_shell(prob):
+    ev = np.linalg.eigvalsh(prob.dense_Htilde())
+    return ev[1:7]
+
+
+def test_dropped_half_in_kinetic_term_is_caught(monkeypatch):
+    ok = ham.Problem(3, 4, 10.0, True, lambda x: np.zeros(len(x)))
+    assert np.abs(_free_first_shell(ok) - FREE).max() < 2e-4 * FREE
+
+    def bad(self, e):
+        xq = self.basis.quad_coords(self.mesh.cell_origin(e))
+        return self.K + self.basis.potential_matrix(self.potential(xq))
+    monkeypatch.setattr(ham.Problem, "cell_hamiltonian", bad)
+    wrong = ham.Problem(3, 4, 10.0, True, lambda x: np.zeros(len(x)))
+    assert np.abs(_free_first_shell(wrong) - FREE).max() > 0.5 * FREE
+
+
+def test_wrong_periodic_wrap_is_caught(monkeypatch):
+    def bad_global(self, c, i):
+        g = c * self.p + i
+        if self.periodic:
+            return g if g < self.ncell * self.p else 1   # should wrap to 0
+        return -1 if g in (0, self.ncell * self.p) else g - 1
+    monkeypatch.setattr(fe.Mesh, "_global_1d", bad_global)
+    wrong = ham.Problem(3, 4, 10.0, True, lambda x: np.zeros(len(x)))
+    shell = _free_first_shell(wrong)
+    assert np.abs(shell - FREE).max() > 1e-2 * FREE or shell.max() - shell.min() > 1e-6
+
+
+def test_transposed_cholesky_factor_is_caught(monkeypatch):
+    def bad(X):
+        S = X.T @ X
+        L = np.linalg.cholesky(S)
+        Linv = sla.solve_triangular(L, np.eye(len(S)), lower=True)
+        return X @ Linv              # should be L^{-T}
+    monkeypatch.setattr(chfsi, "cholgs", bad)
+    X = np.random.default_rng(3).uniform(-1, 1, (200, 12))
+    Q = chfsi.cholgs(X)
+    assert np.abs(Q.T @ Q - np.eye(12)).max() > 1e-3
+
+
+def test_wrong_recurrence_sign_is_caught():
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((60, 60))
+    H = A + A.T
+    evals, evecs = np.linalg.eigh(H)
+    X = rng.standard_normal((60, 4))
+    a, b, a0 = evals[10], evals[-1] * 1.01, evals[0]
+    good = chfsi.chebyshev_filter(lambda Y: H @ Y, X, 6, a, b, a0)
+    ref = chfsi.exact_filter(evals, evecs, X, 6, a, b, a0)
+    assert np.linalg.norm(good - ref) < 1e-10 * np.linalg.norm(ref)
+    # planted: + sigma_k sigma_{k+1} Y_{k-1} instead of minus
+    e, c = (b - a) / 2, (b + a) / 2
+    s1 = e / (a0 - c)
+    s, Yp, Y = s1, X, (s1 / e) * (H @ X - c * X)
+    for _ in range(2, 7):
+        sn = 1 / (2 / s1 - s)
+        Yp, Y, s = Y, (2 * sn / e) * (H @ Y - c * Y) + s * sn * Yp, sn
+    assert np.linalg.norm(Y - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+def test_transposed_ritz_rotation_is_caught(monkeypatch):
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((80, 80))
+    H = A + A.T
+    evals, evecs = np.linalg.eigh(H)
+    V = evecs[:, :8] @ np.linalg.qr(rng.standard_normal((8, 8)))[0]
+
+    def bad(apply_Ht, X):
+        Hh = X.T @ apply_Ht(X)
+        D, Q = np.linalg.eigh(0.5 * (Hh + Hh.T))
+        return D, X @ Q.T            # should be X Q
+    monkeypatch.setattr(chfsi, "rayleigh_ritz", bad)
+    D, X = chfsi.rayleigh_ritz(lambda Y: H @ Y, V)
+    R = np.linalg.norm(H @ X - X * D[None, :], axis=0)
+    assert R.max() > 1e-3
