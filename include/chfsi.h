@@ -1,0 +1,183 @@
+/*
+ * chfsi.h -- C ABI of a GB300 (sm_103a) library for one Chebyshev-filtered
+ * subspace iteration (ChFSI) step of the real-space spectral finite-element
+ * Kohn-Sham method of arXiv:1903.10959 (DFT-FE), for a fixed effective
+ * potential on a uniform hexahedral mesh with Gauss-Lobatto-Legendre nodes.
+ *
+ * Problem statement (Sec. 2.4, Eqs. discreteHam, nonlocalHamDiscrete, hep):
+ * the FE discretisation gives H Psi = eps M Psi with H = H_loc + H_nl and a
+ * diagonal GLL mass M; the library works with the standard form
+ *   H~ = M^{-1/2} H M^{-1/2},   x~ = M^{1/2} Psi                (Eq. hep)
+ * and computes the lowest eigenpairs of H~ by ChFSI (step 7 of Algorithm scf):
+ * Chebyshev filter (Eq. chebFilter, Sec. 3.3), CholGS (Algorithm CholGS,
+ * Sec. 3.4) and Rayleigh-Ritz (Sec. 3.5).
+ *
+ * Conventions for every call:
+ *  - Wavefunction blocks X are DEVICE pointers owned by the caller, row-major
+ *    "DOF-major" (Sec. 3.3.1: the values of all vectors at one unknown are
+ *    contiguous): element (unknown j, vector i) is at X[j * ldx + i],
+ *    ldx >= ncol.  The element type is double for CHFSI_FP64 and float for
+ *    the mixed precisions.  The library never frees caller memory.
+ *  - Host arrays (eigenvalues, residuals, mass, inputs) are plain host
+ *    pointers owned by the caller.
+ *  - Every call runs on the context's CUDA stream.  Calls that return host
+ *    values (bounds, eigenvalues, residuals, mass) synchronise that stream;
+ *    the others are asynchronous.
+ *  - Errors are returned as chfsi_status; no exception crosses the ABI.  A
+ *    CUDA or cuSOLVER error is latched in the context (every later call
+ *    returns CHFSI_ERR_CUDA) and described by chfsi_last_error().
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef CHFSI_H
+#define CHFSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chfsi_ctx chfsi_ctx;
+
+typedef enum {
+  CHFSI_OK = 0,
+  CHFSI_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, bad order of calls) */
+  CHFSI_ERR_OOM = 2,      /* device allocation failed or exceeds the context's budget     */
+  CHFSI_ERR_CUDA = 3,     /* CUDA / cuSOLVER failure; see chfsi_last_error                */
+  CHFSI_ERR_NOT_SPD = 4,  /* CholGS: overlap matrix not positive definite (X unchanged)   */
+  CHFSI_ERR_EIG = 5,      /* Rayleigh-Ritz: eigensolver did not converge                 */
+  CHFSI_ERR_STATE = 6     /* call made before the data it needs (e.g. filter before build) */
+} chfsi_status;
+
+typedef enum {
+  /* Everything in binary64: cell products, recurrence, overlap, projection. */
+  CHFSI_FP64 = 0,
+  /* X stored in binary32; filter cell products on tcgen05 tensor cores as
+   * three TF32 products per term (hi*hi + hi*lo + lo*hi, FP32 accumulation),
+   * which keeps binary32 accuracy; off-diagonal blocks of S and H^ likewise;
+   * diagonal blocks, Cholesky, eigensolve and residuals in binary64. */
+  CHFSI_MIXED_TF32X3 = 1,
+  /* As above with one TF32 product per term (faster, ~5e-4 relative). */
+  CHFSI_MIXED_TF32 = 2
+} chfsi_precision;
+
+/* Uniform mesh of ncell[0] x ncell[1] x ncell[2] boxes on [0,len[0]] x ... .
+ * p: FE degree (1..8), n_e = (p+1)^3 nodes per cell, GLL nodes (Sec. 2.4).
+ * periodic != 0: periodic in all three directions (requires ncell[d] >= 2);
+ * otherwise homogeneous Dirichlet (boundary nodes eliminated).
+ * quad_points: Gauss-Legendre points per direction for the Hamiltonian
+ * integrals (0 selects p + 2); the mass always uses the GLL rule. */
+typedef struct {
+  int ncell[3];
+  double len[3];
+  int p;
+  int periodic;
+  int quad_points;
+} chfsi_mesh_desc;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL
+ * for the legacy default stream).  Builds the cell->unknown map, the colour
+ * schedule of the assembly and the global diagonal GLL mass (Sec. 2.4). */
+chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx** out);
+chfsi_status chfsi_destroy(chfsi_ctx* ctx);
+const char*  chfsi_last_error(const chfsi_ctx* ctx);
+
+/* Number of unknowns M: (n p)^3 periodic, (n p - 1)^3 Dirichlet (per axis). */
+int64_t      chfsi_num_dofs(const chfsi_ctx* ctx);
+
+/* Global diagonal mass M_jj (GLL quadrature; text after Eq. hep) -> host_out[M]. */
+chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out);
+
+/* Effective potential V(x) = -sum_a depth[a] exp(-|x - R_a|^2 / (2 width[a]^2)),
+ * R_a = xyz[3a..3a+2]; with periodic meshes each well is summed over the 27
+ * image shifts {-1,0,1}^3 * len.  Arrays are host, copied.  Invalidates any
+ * previous chfsi_build. */
+chfsi_status chfsi_set_potential_gaussians(chfsi_ctx* ctx, int n, const double* xyz,
+                                           const double* depth, const double* width);
+
+/* Separable nonlocal projectors (Eqs. nlps, nonlocalHamDiscrete): per site s,
+ * four channels chi = g(r) {1, x/sigma, y/sigma, z/sigma}, g = exp(-r^2/(2 sigma^2))
+ * for r <= rcut (0 beyond), r to the nearest periodic image, with couplings
+ * h[4 s + k] (Ha).  H_nl = sum C^T h C, C_{k,j} = int chi_k N_j.  n = 0 clears. */
+chfsi_status chfsi_set_projectors(chfsi_ctx* ctx, int n, const double* xyz, const double* h,
+                                  double sigma, double rcut);
+
+/* Build the cell matrices H~_e = D_e^{-1/2} (1/2 K_e + V_e) D_e^{-1/2}
+ * (Eq. discreteHam scaled as in Eq. hep; D_e = global mass at the cell's
+ * nodes) in binary64 on the host, and upload them together with the
+ * precision-specific device copies and the projector data. */
+chfsi_status chfsi_build(chfsi_ctx* ctx);
+
+/* Column block size of the filter (Sec. 3.3.1 "B^f"; default 200 or ncol if
+ * smaller) and diagonal block size of the mixed overlap/projection products
+ * (default 32).  Takes effect on the next call. */
+chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block);
+
+/* Fill rows x ncol of X (device, leading dimension ldx) with the seeded
+ * SplitMix64 stream (Steele, Lea & Flood 2014), mapped to [-1, 1): element
+ * (r, c) is draw r * ncol + c of the stream keyed by (seed, stream). */
+chfsi_status chfsi_fill_uniform(chfsi_ctx* ctx, void* X, int64_t ldx, int64_t rows, int ncol,
+                                uint64_t seed, uint64_t stream, chfsi_precision prec);
+
+/* Y = H~ X on ncol vectors (one application of Eq. hep's operator, the inner
+ * operation of Eq. chebFilter).  X and Y: device, M x ncol, must not overlap. */
+chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                         int ncol, chfsi_precision prec);
+
+/* Degree-m Chebyshev filter (Eq. chebFilter) in the scaled form of Zhou &
+ * Saad, in place on X (M x ncol): X <- T_m((H~ - c)/e) X / T_m((a0 - c)/e),
+ * c = (a + b)/2, e = (b - a)/2; [a, b] is the damped interval, a0 < a the
+ * lower end of the spectrum.  Requires a0 < a < b and degree >= 1. */
+chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree,
+                          double a, double b, double a0, chfsi_precision prec);
+
+/* CholGS (Algorithm CholGS): S = X^T X, S = L L^T, X <- X L^{-T}, in place on
+ * X (M x n).  Returns CHFSI_ERR_NOT_SPD and leaves X unchanged when the
+ * Cholesky factorisation fails (cuSOLVER potrf + trtri, binary64). */
+chfsi_status chfsi_cholgs(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec);
+
+/* Rayleigh-Ritz (Sec. 3.5): H^ = X^T H~ X, H^ Q = Q D (ascending, binary64
+ * cuSOLVER syevd), X <- X Q in place.  evals_host[n] receives D. */
+chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* ctx, void* X, int64_t ldx, int n,
+                                 chfsi_precision prec, double* evals_host);
+
+/* Residuals in binary64 for n pairs (columns of X, evals_host):
+ * res[i]  = ||H~ x_i - l_i x_i||_2 / ||x_i||_2, and, when gres != NULL,
+ * gres[i] = ||H Psi_i - l_i M Psi_i||_2 with Psi_i = M^{-1/2} x_i / ||x_i||
+ * (the generalized-problem residual of Eq. hep).  Either output may be NULL. */
+chfsi_status chfsi_residuals(chfsi_ctx* ctx, const void* X, int64_t ldx, int n,
+                             chfsi_precision prec, const double* evals_host,
+                             double* res_host, double* gres_host);
+
+/* Upper bound of spec(H~) by a k-step Lanczos run from the seeded start
+ * vector (stream 7 of chfsi_fill_uniform): b = max Ritz value of the
+ * tridiagonal + |beta_k| (the safeguard of Zhou & Saad; the paper ties the
+ * filter to this bound, Sec. 3.3).  Binary64. */
+chfsi_status chfsi_bounds(chfsi_ctx* ctx, int lanczos_steps, uint64_t seed, double* b_out);
+
+/* Full ChFSI loop on X (M x n, in/out): CholGS + RR on the start block, then
+ * `iters` times {filter(degree, a = max Ritz, b, a0 = min Ritz); CholGS; RR}
+ * (step 7 of Algorithm scf).  b: upper bound (chfsi_bounds).  evals_host[n]
+ * receives the final Ritz values.  When tol > 0 the loop stops early once
+ * the largest residual of the lowest n_check pairs is below tol (adaptive
+ * filtering, Sec. 3.3); n_check <= 0 means n.  iters_done may be NULL. */
+chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters, int degree,
+                         double b, double tol, int n_check, chfsi_precision prec,
+                         double* evals_host, int* iters_done);
+
+/* Psi^ = M^{-1/2} x~ in place (Eq. hep, recovery of the FE eigenvectors). */
+chfsi_status chfsi_unscale(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, chfsi_precision prec);
+
+/* Per-phase device times of the last chfsi_solve / filter / cholgs / rr call
+ * (milliseconds, CUDA events): out[0] filter, out[1] cholgs, out[2] rr,
+ * out[3] residual/other.  Synchronises. */
+chfsi_status chfsi_last_timings(chfsi_ctx* ctx, double* out4);
+
+/* Bytes of device memory the context currently holds. */
+int64_t      chfsi_device_bytes(const chfsi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFSI_H */

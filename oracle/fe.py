@@ -120,8 +120,9 @@ class CellBasis:
         return np.einsum("q,qjd,qkd->jk", self.W, self.dN, self.dN)
 
     def potential_matrix(self, vq: np.ndarray) -> np.ndarray:
-        """V_jk = int V N_j N_k with V given at the q^3 Gauss points (Eq. discreteHam)."""
-        return np.einsum("q,qj,qk->jk", self.W * vq, self.N, self.N)
+        """V_jk = int V N_j N_k with V given at the q^3 Gauss points (Eq. discreteHam):
+        sum over the points q of W_q V_q N_j(q) N_k(q)."""
+        return self.N.T @ ((self.W * vq)[:, None] * self.N)
 
     def gll_mass_diag(self) -> np.ndarray:
         """Cell mass by GLL quadrature at the element nodes: N_j(x_k) = delta_jk,
@@ -212,7 +213,22 @@ class Mesh:
         return out
 
     def dofmap(self) -> np.ndarray:
-        return np.stack([self.cell_dofs(e) for e in range(self.ncells)])
+        """cell_dofs for every cell, shape (ncells, ne) (same rule, vectorised)."""
+        n, p = self.ncell, self.p
+        e = np.arange(self.ncells)
+        c = np.stack([e % n, (e // n) % n, e // (n * n)], axis=1)
+        i = np.arange(p + 1)
+        g = c[:, :, None] * p + i[None, None, :]           # (ncells, 3, p+1)
+        if self.periodic:
+            g = g % (n * p)
+        else:
+            g = np.where((g == 0) | (g == n * p), -1, g - 1)
+        gx = g[:, 0][:, None, None, :]
+        gy = g[:, 1][:, None, :, None]
+        gz = g[:, 2][:, :, None, None]
+        d = gx + self.n1d * (gy + self.n1d * gz)
+        bad = (gx < 0) | (gy < 0) | (gz < 0)
+        return np.where(bad, -1, d).reshape(self.ncells, -1)
 
     def dof_coords(self) -> np.ndarray:
         """Physical coordinates of the unknowns (periodic nodes in [0, L))."""

@@ -91,6 +91,29 @@ class Problem:
         s = self.minv_sqrt if X.ndim == 1 else self.minv_sqrt[:, None]
         return s * self.apply_H(s * X)
 
+    def apply_Htilde_rows(self, rows, X: np.ndarray) -> np.ndarray:
+        """Rows ``rows`` of H~ X, summing only the cells that contain them (for
+        sampled checks on meshes too large for a full oracle apply)."""
+        if not hasattr(self, "_node_cells"):
+            dm = self.mesh.dofmap()
+            inv = {}
+            for e in range(self.mesh.ncells):
+                for l, g in enumerate(dm[e]):
+                    if g >= 0:
+                        inv.setdefault(int(g), []).append((e, l))
+            self._node_cells, self._dm = inv, dm
+        s = self.minv_sqrt
+        out = np.zeros((len(rows), X.shape[1]))
+        for ii, j in enumerate(rows):
+            for e, l in self._node_cells[int(j)]:
+                d = self._dm[e]
+                ok = d >= 0
+                out[ii] += self.cell_hamiltonian(e)[l, ok] @ (s[d[ok], None] * X[d[ok]])
+        if self.C is not None:
+            Z = self.C @ (s[:, None] * X)
+            out += self.C[:, np.asarray(rows)].T @ (self.hnl[:, None] * Z)
+        return s[np.asarray(rows), None] * out
+
     def dense_H(self) -> np.ndarray:
         """Assembled H (small meshes only)."""
         n = self.ndofs

@@ -1,0 +1,249 @@
+"""ctypes binding of libchfsi (include/chfsi.h): argument marshalling only.
+
+Every method of :class:`Context` calls the C entry point of the same name
+(``chfsi_<name>``); all arithmetic runs in the library's CUDA kernels.  Device
+buffers are passed as torch CUDA tensors (their ``data_ptr``), host arrays as
+numpy arrays.  There is no CPU fallback: loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchfsi.so")
+
+FP64, MIXED_TF32X3, MIXED_TF32 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED_TF32X3, "tf32x3": MIXED_TF32X3, "tf32": MIXED_TF32}
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_SPD", 5: "ERR_EIG",
+          6: "ERR_STATE"}
+
+
+class ChfsiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("ncell", C.c_int * 3), ("len", C.c_double * 3), ("p", C.c_int),
+                ("periodic", C.c_int), ("quad_points", C.c_int)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+_i64 = C.c_int64
+
+_SIGS = {
+    "chfsi_create": (C.c_int, [C.POINTER(MeshDesc), _vp, C.POINTER(_vp)]),
+    "chfsi_destroy": (C.c_int, [_vp]),
+    "chfsi_last_error": (C.c_char_p, [_vp]),
+    "chfsi_num_dofs": (_i64, [_vp]),
+    "chfsi_device_bytes": (_i64, [_vp]),
+    "chfsi_mass_diag": (C.c_int, [_vp, _dp]),
+    "chfsi_set_potential_gaussians": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
+    "chfsi_set_projectors": (C.c_int, [_vp, C.c_int, _dp, _dp, C.c_double, C.c_double]),
+    "chfsi_build": (C.c_int, [_vp]),
+    "chfsi_set_blocking": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "chfsi_fill_uniform": (C.c_int, [_vp, _vp, _i64, _i64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]),
+    "chfsi_apply": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int, C.c_int]),
+    "chfsi_filter": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_double, C.c_double,
+                               C.c_double, C.c_int]),
+    "chfsi_cholgs": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
+    "chfsi_rayleigh_ritz": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, _dp]),
+    "chfsi_residuals": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, _dp, _dp, _dp]),
+    "chfsi_bounds": (C.c_int, [_vp, C.c_int, C.c_uint64, _dp]),
+    "chfsi_solve": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                              C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]),
+    "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
+    "chfsi_last_timings": (C.c_int, [_vp, _dp]),
+}
+
+
+def load(path: str | None = None):
+    """Load libchfsi.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if path is None and _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libchfsi.so not built at %s: run __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _host(a, n=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _dev(t, prec=None):
+    """(pointer, leading dimension, ncol) of a 2-D row-major CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("device buffers must be CUDA tensors")
+    if t.dim() == 1:
+        return t.data_ptr(), 1, 1
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit column stride")
+    if prec is not None:
+        want = torch.float64 if prec == FP64 else torch.float32
+        if t.dtype != want:
+            raise TypeError("precision %d needs dtype %s, got %s" % (prec, want, t.dtype))
+    return t.data_ptr(), t.stride(0), t.shape[1]
+
+
+class Context:
+    """One discretised problem on the current CUDA device (chfsi_ctx)."""
+
+    def __init__(self, ncell, length, p, periodic=True, quad_points=0, stream=None):
+        lib = load()
+        if np.isscalar(ncell):
+            ncell = (ncell,) * 3
+        if np.isscalar(length):
+            length = (float(length),) * 3
+        d = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p), int(bool(periodic)),
+                     int(quad_points))
+        h = _vp()
+        s = _vp(stream.cuda_stream) if stream is not None else _vp(None)
+        self._lib = lib
+        st = lib.chfsi_create(C.byref(d), s, C.byref(h))
+        if st != 0:
+            raise ChfsiError(st, "chfsi_create failed")
+        self._h = h
+        self.ndofs = lib.chfsi_num_dofs(h)
+
+    def _check(self, st):
+        if st != 0:
+            raise ChfsiError(st, self._lib.chfsi_last_error(self._h).decode())
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.chfsi_destroy(self._h)
+            self._h = None
+
+    close = destroy
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def last_error(self) -> str:
+        return self._lib.chfsi_last_error(self._h).decode()
+
+    def device_bytes(self) -> int:
+        return self._lib.chfsi_device_bytes(self._h)
+
+    def mass_diag(self) -> np.ndarray:
+        out = np.empty(self.ndofs)
+        self._check(self._lib.chfsi_mass_diag(self._h, _ptr(out)))
+        return out
+
+    def set_potential_gaussians(self, centres, depths, widths):
+        n = len(depths)
+        c, d, w = _host(centres, 3 * n), _host(depths, n), _host(widths, n)
+        self._check(self._lib.chfsi_set_potential_gaussians(self._h, n, _ptr(c), _ptr(d), _ptr(w)))
+
+    def set_projectors(self, centres, h, sigma=0.8, rcut=3.0):
+        n = len(centres)
+        c, hh = _host(centres, 3 * n), _host(h, 4 * n)
+        self._check(self._lib.chfsi_set_projectors(self._h, n, _ptr(c), _ptr(hh), sigma, rcut))
+
+    def build(self):
+        self._check(self._lib.chfsi_build(self._h))
+
+    def set_blocking(self, filter_block=200, diag_block=32):
+        self._check(self._lib.chfsi_set_blocking(self._h, int(filter_block), int(diag_block)))
+
+    def fill_uniform(self, X, seed, stream=1, prec="fp64"):
+        pr = _prec(prec)
+        ptr, ld, ncol = _dev(X, pr)
+        self._check(self._lib.chfsi_fill_uniform(self._h, ptr, ld, X.shape[0], ncol, seed, stream, pr))
+
+    def apply(self, X, Y, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        py, ldy, _ = _dev(Y, pr)
+        self._check(self._lib.chfsi_apply(self._h, px, ldx, py, ldy, n, pr))
+
+    def filter(self, X, degree, a, b, a0, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        self._check(self._lib.chfsi_filter(self._h, px, ldx, n, degree, a, b, a0, pr))
+
+    def cholgs(self, X, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        self._check(self._lib.chfsi_cholgs(self._h, px, ldx, n, pr))
+
+    def rayleigh_ritz(self, X, prec="fp64") -> np.ndarray:
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        ev = np.empty(n)
+        self._check(self._lib.chfsi_rayleigh_ritz(self._h, px, ldx, n, pr, _ptr(ev)))
+        return ev
+
+    def residuals(self, X, evals, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        ev = _host(evals, n)
+        r, g = np.empty(n), np.empty(n)
+        self._check(self._lib.chfsi_residuals(self._h, px, ldx, n, pr, _ptr(ev), _ptr(r), _ptr(g)))
+        return r, g
+
+    def bounds(self, steps=20, seed=1) -> float:
+        b = np.zeros(1)
+        self._check(self._lib.chfsi_bounds(self._h, int(steps), int(seed), _ptr(b)))
+        return float(b[0])
+
+    def solve(self, X, iters, degree, b, tol=0.0, n_check=0, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        ev = np.empty(n)
+        done = C.c_int(0)
+        self._check(self._lib.chfsi_solve(self._h, px, ldx, n, int(iters), int(degree), float(b),
+                                          float(tol), int(n_check), pr, _ptr(ev), C.byref(done)))
+        return ev, done.value
+
+    def unscale(self, X, prec="fp64"):
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        self._check(self._lib.chfsi_unscale(self._h, px, ldx, n, pr))
+
+    def last_timings(self) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(self._lib.chfsi_last_timings(self._h, _ptr(out)))
+        return out

@@ -1,0 +1,790 @@
+// C-ABI entry points of libchfsi (declared in include/chfsi.h): context and
+// device-memory management, the filter / CholGS / Rayleigh-Ritz drivers and
+// the ChFSI loop (step 7 of Algorithm scf in arXiv:1903.10959).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cusolverDn.h>
+
+#include "internal.h"
+#include "tc.h"
+
+using namespace chfsi;
+
+struct chfsi_ctx {
+  HostMesh mesh;
+  Wells wells;
+  Projectors proj;
+  HostProjectors hproj;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool built = false;
+  chfsi_status latched = CHFSI_OK;
+  std::string err;
+  int filter_block = 200, diag_block = 32;
+  int64_t dev_bytes = 0;
+  // resident device data
+  double* d_Ht = nullptr;          // binary64 cell matrices
+  TcCellData tc;                   // tensor-core copies (mixed precisions)
+  int32_t* d_dofmap = nullptr;
+  uint8_t* d_modes = nullptr;
+  int32_t* d_cells = nullptr;
+  double* d_mass = nullptr;
+  int64_t* d_site_ptr = nullptr;
+  int32_t* d_site_dof = nullptr;
+  double* d_site_c = nullptr;
+  int64_t* d_dof_ptr = nullptr;
+  int32_t* d_dof_site = nullptr;
+  double* d_dof_c = nullptr;
+  float* d_site_c32 = nullptr;
+  float* d_dof_c32 = nullptr;
+  // grown scratch
+  DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam;
+  cusolverDnHandle_t sol = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double times[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+chfsi_status fail(chfsi_ctx* c, chfsi_status st, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (st == CHFSI_ERR_CUDA) c->latched = st;
+  }
+  return st;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, CHFSI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define CS(call)                                                                          \
+  do {                                                                                    \
+    cusolverStatus_t s_ = (call);                                                         \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                    \
+      return fail(ctx, CHFSI_ERR_CUDA, std::string(#call) + ": cusolver status " +         \
+                                           std::to_string((int)s_));                      \
+  } while (0)
+#define CHECK_CTX()                                                                       \
+  do {                                                                                    \
+    if (!ctx) return CHFSI_ERR_ARG;                                                       \
+    if (ctx->latched != CHFSI_OK) return ctx->latched;                                    \
+  } while (0)
+
+cudaError_t dalloc(chfsi_ctx* ctx, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e == cudaSuccess) ctx->dev_bytes += (int64_t)std::max<size_t>(bytes, 16);
+  return e;
+}
+void dfree(chfsi_ctx* ctx, void* p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    ctx->dev_bytes -= (int64_t)std::max<size_t>(bytes, 16);
+  }
+}
+template <class T>
+cudaError_t upload(chfsi_ctx* ctx, T** dst, const std::vector<T>& src) {
+  if (*dst) return cudaErrorInvalidValue;
+  cudaError_t e = dalloc(ctx, (void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+}
+template <class T>
+void release(chfsi_ctx* ctx, T*& p, size_t bytes) {
+  dfree(ctx, (void*)p, bytes);
+  p = nullptr;
+}
+
+chfsi_status grow(chfsi_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return CHFSI_OK;
+  if (b.ptr) {
+    cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, b.ptr, b.bytes);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = dalloc(ctx, &b.ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, CHFSI_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  b.bytes = bytes;
+  return CHFSI_OK;
+}
+
+bool is_mixed(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32; }
+bool valid_prec(chfsi_precision p) { return p == CHFSI_FP64 || is_mixed(p); }
+size_t esize(chfsi_precision p) { return p == CHFSI_FP64 ? 8 : 4; }
+
+void free_device_data(chfsi_ctx* ctx) {
+  const HostMesh& m = ctx->mesh;
+  release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
+  tc_free(ctx->tc);
+  release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
+  release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
+  release(ctx, ctx->d_site_c, ctx->hproj.site_c.size() * 8);
+  release(ctx, ctx->d_dof_ptr, ctx->hproj.dof_ptr.size() * 8);
+  release(ctx, ctx->d_dof_site, ctx->hproj.dof_site.size() * 4);
+  release(ctx, ctx->d_dof_c, ctx->hproj.dof_c.size() * 8);
+  release(ctx, ctx->d_site_c32, ctx->hproj.site_c.size() * 4);
+  release(ctx, ctx->d_dof_c32, ctx->hproj.dof_c.size() * 4);
+  ctx->built = false;
+}
+
+// One recurrence step over the ncol columns of a block:
+// Yout = alpha (H~ Yin - shift Yin) + beta Yprev, colour by colour.
+chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, int64_t ld_in,
+                        void* Yout, int64_t ld_out, const void* Yprev, int64_t ld_prev, int ncol,
+                        double alpha, double beta, double shift) {
+  const HostMesh& m = ctx->mesh;
+  const int B = std::max(ncol, 1);
+  const size_t es = esize(prec);
+  chfsi_status st;
+  if ((st = grow(ctx, ctx->Wb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+  const bool nl = ctx->hproj.nsite > 0;
+  if (nl) {
+    if ((st = grow(ctx, ctx->NLb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+    if ((st = grow(ctx, ctx->Zb, (size_t)4 * ctx->hproj.nsite * B * es)) != CHFSI_OK) return st;
+  }
+  const int ncolour = (int)m.colour_offsets.size() - 1;
+  if (prec == CHFSI_FP64) {
+    if (nl) {
+      CK(launch_nl_project_fp64(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c, ctx->hproj.nsite,
+                                (const double*)Yin, ld_in, ncol, (double*)ctx->Zb.ptr, ctx->stream));
+      CK(launch_nl_expand_fp64(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c, m.ndofs,
+                               (const double*)ctx->Zb.ptr, ncol, (double*)ctx->NLb.ptr, B, ctx->stream));
+    }
+    for (int c = 0; c < ncolour; ++c) {
+      CellLaunch L{};
+      L.Ht = ctx->d_Ht;
+      L.dofmap = ctx->d_dofmap;
+      L.modes = ctx->d_modes;
+      L.cells = ctx->d_cells + m.colour_offsets[c];
+      L.ncells_colour = m.colour_offsets[c + 1] - m.colour_offsets[c];
+      L.ne = m.ne;
+      L.ncol = ncol;
+      L.ld_in = ld_in;
+      L.ld_out = ld_out;
+      L.ld_prev = ld_prev;
+      CK(launch_cell_fp64(L, (const double*)Yin, (double*)Yout, (const double*)Yprev,
+                          (double*)ctx->Wb.ptr, nl ? (const double*)ctx->NLb.ptr : nullptr, B,
+                          FilterStep{alpha, beta, shift}, ctx->stream));
+    }
+    return CHFSI_OK;
+  }
+  // mixed precisions: binary32 storage, tcgen05 TF32 cell products
+  if (nl) {
+    CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
+                     (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
+    CK(tc_nl_expand(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c32, m.ndofs,
+                    (const float*)ctx->Zb.ptr, ncol, (float*)ctx->NLb.ptr, B, ctx->stream));
+  }
+  for (int c = 0; c < ncolour; ++c) {
+    TcCellArgs a{};
+    a.cells = ctx->d_cells + m.colour_offsets[c];
+    a.ncells = m.colour_offsets[c + 1] - m.colour_offsets[c];
+    a.dofmap = ctx->d_dofmap;
+    a.modes = ctx->d_modes;
+    a.ncol = ncol;
+    a.Yin = (const float*)Yin;
+    a.ld_in = ld_in;
+    a.Yout = (float*)Yout;
+    a.ld_out = ld_out;
+    a.Yprev = beta != 0.0 ? (const float*)Yprev : nullptr;
+    a.ld_prev = ld_prev;
+    a.W = (float*)ctx->Wb.ptr;
+    a.NL = nl ? (const float*)ctx->NLb.ptr : nullptr;
+    a.ld_w = B;
+    a.alpha = (float)alpha;
+    a.beta = (float)beta;
+    a.shift = (float)shift;
+    a.split3 = prec == CHFSI_MIXED_TF32X3;
+    CK(tc_cell_launch(ctx->tc, a, ctx->stream));
+  }
+  return CHFSI_OK;
+}
+
+// Y = H~ X in column blocks (Y separate from X).
+chfsi_status apply_blocks(chfsi_ctx* ctx, chfsi_precision prec, const void* X, int64_t ldx, void* Y,
+                          int64_t ldy, int ncol) {
+  const int B = std::max(1, std::min(ctx->filter_block, ncol));
+  const size_t es = esize(prec);
+  for (int b0 = 0; b0 < ncol; b0 += B) {
+    const int nb = std::min(B, ncol - b0);
+    chfsi_status st = apply_step(ctx, prec, (const char*)X + b0 * es, ldx, (char*)Y + b0 * es, ldy,
+                                 nullptr, 0, nb, 1.0, 0.0, 0.0);
+    if (st != CHFSI_OK) return st;
+  }
+  return CHFSI_OK;
+}
+
+chfsi_status check_x(chfsi_ctx* ctx, const void* X, int64_t ldx, int ncol, chfsi_precision prec) {
+  if (!valid_prec(prec)) return fail(ctx, CHFSI_ERR_ARG, "unknown precision");
+  if (!ctx->built) return fail(ctx, CHFSI_ERR_STATE, "chfsi_build has not been called");
+  if (ncol < 0 || (ncol > 0 && (!X || ldx < ncol))) return fail(ctx, CHFSI_ERR_ARG, "bad X / ldx / ncol");
+  return CHFSI_OK;
+}
+
+void tic(chfsi_ctx* ctx) { cudaEventRecord(ctx->ev[0], ctx->stream); }
+void toc(chfsi_ctx* ctx, int slot) {
+  cudaEventRecord(ctx->ev[1], ctx->stream);
+  cudaEventSynchronize(ctx->ev[1]);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+  ctx->times[slot] += ms;
+}
+
+chfsi_status filter_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
+                         double b, double a0, chfsi_precision prec) {
+  const HostMesh& m = ctx->mesh;
+  const int B = std::max(1, std::min(ctx->filter_block, ncol));
+  const size_t es = esize(prec);
+  chfsi_status st;
+  if ((st = grow(ctx, ctx->T1, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+  const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+  const double s1 = e / (a0 - c);
+  for (int b0 = 0; b0 < ncol; b0 += B) {
+    const int nb = std::min(B, ncol - b0);
+    char* Xb = (char*)X + b0 * es;
+    // Y0 = Xb, Y1 -> T1, then Y_{k+1} overwrites Y_{k-1}
+    void* bufs[2] = {Xb, ctx->T1.ptr};
+    int64_t lds[2] = {ldx, (int64_t)nb};
+    int cur = 0;  // buffer holding Y_k
+    double sig = s1;
+    for (int k = 1; k <= degree; ++k) {
+      double alpha, beta;
+      if (k == 1) {
+        alpha = s1 / e;
+        beta = 0.0;
+      } else {
+        double sn = 1.0 / (2.0 / s1 - sig);
+        alpha = 2.0 * sn / e;
+        beta = -sig * sn;
+        sig = sn;
+      }
+      const int nxt = 1 - cur;  // holds Y_{k-2} (or is free at k = 1)
+      st = apply_step(ctx, prec, bufs[cur], lds[cur], bufs[nxt], lds[nxt], bufs[nxt], lds[nxt], nb,
+                      alpha, beta, c);
+      if (st != CHFSI_OK) return st;
+      cur = nxt;
+    }
+    if (cur == 1)
+      CK(cudaMemcpy2DAsync(Xb, ldx * es, ctx->T1.ptr, nb * es, nb * es, m.ndofs,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return CHFSI_OK;
+}
+
+// S(n x n, column-major, lower part) = A^T B for the precision's storage type.
+chfsi_status gram_impl(chfsi_ctx* ctx, chfsi_precision prec, const void* A, int64_t lda,
+                       const void* Bm, int64_t ldb, int n1, int n2, double* C, int64_t ldc,
+                       int lower) {
+  const HostMesh& m = ctx->mesh;
+  chfsi_status st;
+  if (prec == CHFSI_FP64) {
+    size_t want = (size_t)8 * 8 * n1 * n2;
+    if ((st = grow(ctx, ctx->part, want)) != CHFSI_OK) return st;
+    CK(launch_gram_fp64((const double*)A, lda, (const double*)Bm, ldb, m.ndofs, n1, n2, C, ldc,
+                        lower, (double*)ctx->part.ptr, ctx->part.bytes, ctx->stream));
+    return CHFSI_OK;
+  }
+  size_t want = tc_gram_partial_bytes(m.ndofs, n1, n2);
+  if ((st = grow(ctx, ctx->part, want)) != CHFSI_OK) return st;
+  CK(tc_gram_mixed((const float*)A, lda, (const float*)Bm, ldb, m.ndofs, n1, n2, C, ldc, lower,
+                   ctx->diag_block, prec == CHFSI_MIXED_TF32X3, ctx->part.ptr, ctx->part.bytes,
+                   ctx->stream));
+  return CHFSI_OK;
+}
+
+// X <- X U (U n x n column-major; trans / upper flags as launch_tallgemm_fp64).
+chfsi_status rotate_impl(chfsi_ctx* ctx, chfsi_precision prec, void* X, int64_t ldx, int n,
+                         const double* U, int upper, int trans) {
+  const HostMesh& m = ctx->mesh;
+  const size_t es = esize(prec);
+  chfsi_status st;
+  if ((st = grow(ctx, ctx->rot, (size_t)m.ndofs * n * es)) != CHFSI_OK) return st;
+  if (prec == CHFSI_FP64) {
+    CK(launch_tallgemm_fp64((const double*)X, ldx, U, n, m.ndofs, n, n, (double*)ctx->rot.ptr, n,
+                            upper, trans, ctx->stream));
+  } else {
+    CK(tc_tallgemm_mixed((const float*)X, ldx, U, n, m.ndofs, n, n, (float*)ctx->rot.ptr, n, upper,
+                         trans, ctx->diag_block, prec == CHFSI_MIXED_TF32X3, ctx->work.ptr,
+                         ctx->stream));
+  }
+  CK(cudaMemcpy2DAsync(X, ldx * es, ctx->rot.ptr, n * es, n * es, m.ndofs, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status ensure_solver(chfsi_ctx* ctx) {
+  if (!ctx->sol) {
+    CS(cusolverDnCreate(&ctx->sol));
+    CS(cusolverDnSetStream(ctx->sol, ctx->stream));
+  }
+  return CHFSI_OK;
+}
+
+chfsi_status cholgs_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec) {
+  chfsi_status st;
+  if (n == 0) return CHFSI_OK;
+  if ((st = ensure_solver(ctx)) != CHFSI_OK) return st;
+  if ((st = grow(ctx, ctx->Ssq, (size_t)n * n * 8 + 64)) != CHFSI_OK) return st;
+  double* S = (double*)ctx->Ssq.ptr;
+  int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
+  // 1. S = X^T X (lower triangle)
+  if ((st = gram_impl(ctx, prec, X, ldx, X, ldx, n, n, S, n, 1)) != CHFSI_OK) return st;
+  // 2. S = L L^T
+  int lw = 0;
+  CS(cusolverDnDpotrf_bufferSize(ctx->sol, CUBLAS_FILL_MODE_LOWER, n, S, n, &lw));
+  size_t dws = 0, hws = 0;
+  CS(cusolverDnXtrtri_bufferSize(ctx->sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n,
+                                 CUDA_R_64F, S, n, &dws, &hws));
+  size_t need = std::max<size_t>((size_t)lw * 8, dws) + 256;
+  if ((st = grow(ctx, ctx->work, need)) != CHFSI_OK) return st;
+  CS(cusolverDnDpotrf(ctx->sol, CUBLAS_FILL_MODE_LOWER, n, S, n, (double*)ctx->work.ptr, lw, dinfo));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (info != 0)
+    return fail(ctx, CHFSI_ERR_NOT_SPD, "CholGS: potrf info = " + std::to_string(info));
+  // 3. L^{-1} (lower, in place)
+  std::vector<char> hwork(hws + 16);
+  CS(cusolverDnXtrtri(ctx->sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, S, n,
+                      ctx->work.ptr, dws, hwork.data(), hws, dinfo));
+  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (info != 0) return fail(ctx, CHFSI_ERR_NOT_SPD, "CholGS: trtri info = " + std::to_string(info));
+  // 4. X <- X L^{-T}: U(k, j) = Linv(j, k), nonzero for k <= j
+  return rotate_impl(ctx, prec, X, ldx, n, S, 1, 1);
+}
+
+chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
+                     double* evals_host) {
+  const HostMesh& m = ctx->mesh;
+  chfsi_status st;
+  if (n == 0) return CHFSI_OK;
+  if ((st = ensure_solver(ctx)) != CHFSI_OK) return st;
+  if ((st = grow(ctx, ctx->Ssq, (size_t)n * n * 8 + 64)) != CHFSI_OK) return st;
+  if ((st = grow(ctx, ctx->lam, (size_t)n * 8 + 64)) != CHFSI_OK) return st;
+  double* Hh = (double*)ctx->Ssq.ptr;
+  int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
+  const size_t es = esize(prec);
+  const int B = std::max(1, std::min(ctx->filter_block, n));
+  if ((st = grow(ctx, ctx->T1, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+  // 1. H^ = X^T (H~ X), lower triangle, one column block at a time
+  for (int j0 = 0; j0 < n; j0 += B) {
+    const int nb = std::min(B, n - j0);
+    if ((st = apply_step(ctx, prec, (const char*)X + j0 * es, ldx, ctx->T1.ptr, nb, nullptr, 0, nb,
+                         1.0, 0.0, 0.0)) != CHFSI_OK)
+      return st;
+    if ((st = gram_impl(ctx, prec, (const char*)X + j0 * es, ldx, ctx->T1.ptr, nb, n - j0, nb,
+                        Hh + j0 + (int64_t)j0 * n, n, 1)) != CHFSI_OK)
+      return st;
+  }
+  // 2. H^ Q = Q D (binary64 syevd, ascending)
+  int lw = 0;
+  double* W = (double*)ctx->lam.ptr;
+  CS(cusolverDnDsyevd_bufferSize(ctx->sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Hh, n,
+                                 W, &lw));
+  if ((st = grow(ctx, ctx->work, (size_t)lw * 8 + 256)) != CHFSI_OK) return st;
+  CS(cusolverDnDsyevd(ctx->sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Hh, n, W,
+                      (double*)ctx->work.ptr, lw, dinfo));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (evals_host)
+    CK(cudaMemcpyAsync(evals_host, W, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (info != 0) return fail(ctx, CHFSI_ERR_EIG, "RR: syevd info = " + std::to_string(info));
+  // 3. X <- X Q
+  return rotate_impl(ctx, prec, X, ldx, n, Hh, 0, 0);
+}
+
+chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
+                           const double* evals, double* res, double* gres) {
+  const HostMesh& m = ctx->mesh;
+  chfsi_status st;
+  if (n == 0) return CHFSI_OK;
+  const int B = std::max(1, std::min(ctx->filter_block, n));
+  // binary64 copies of the block and of H~ x (residual check always in binary64)
+  if ((st = grow(ctx, ctx->rot, (size_t)m.ndofs * B * 8 * 2)) != CHFSI_OK) return st;
+  if ((st = grow(ctx, ctx->lam, (size_t)n * 8 * 4 + 64)) != CHFSI_OK) return st;
+  if ((st = grow(ctx, ctx->part, (size_t)3 * n * 8 * 512)) != CHFSI_OK) return st;
+  double* X64 = (double*)ctx->rot.ptr;
+  double* Y64 = X64 + (size_t)m.ndofs * B;
+  double* dl = (double*)ctx->lam.ptr;
+  double* out = dl + n;
+  CK(cudaMemcpyAsync(dl, evals, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<double> sq(3 * (size_t)n);
+  for (int j0 = 0; j0 < n; j0 += B) {
+    const int nb = std::min(B, n - j0);
+    CK(launch_copy_cols((const char*)X + j0 * esize(prec), ldx, X64, nb, m.ndofs, nb,
+                        prec == CHFSI_FP64, 1, ctx->stream));
+    if ((st = apply_step(ctx, CHFSI_FP64, X64, nb, Y64, nb, nullptr, 0, nb, 1.0, 0.0, 0.0)) != CHFSI_OK)
+      return st;
+    CK(launch_resid_norms(Y64, nb, X64, nb, m.ndofs, nb, dl + j0, ctx->d_mass, out,
+                          (double*)ctx->part.ptr, ctx->part.bytes, ctx->stream));
+    std::vector<double> h(3 * (size_t)nb);
+    CK(cudaMemcpyAsync(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < nb; ++i) {
+      double xx = h[2 * nb + i];
+      if (res) res[j0 + i] = std::sqrt(h[i] / xx);
+      if (gres) gres[j0 + i] = std::sqrt(h[nb + i] / xx);
+    }
+  }
+  return CHFSI_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx** out) {
+  if (!desc || !out) return CHFSI_ERR_ARG;
+  *out = nullptr;
+  if (desc->p < 1 || desc->p > 8) return CHFSI_ERR_ARG;
+  for (int a = 0; a < 3; ++a) {
+    if (desc->ncell[a] < 1 || !(desc->len[a] > 0.0)) return CHFSI_ERR_ARG;
+    if (desc->periodic && desc->ncell[a] < 2) return CHFSI_ERR_ARG;
+    if (!desc->periodic && desc->ncell[a] * desc->p < 2) return CHFSI_ERR_ARG;
+  }
+  if (desc->quad_points < 0 || desc->quad_points > 16) return CHFSI_ERR_ARG;
+  int64_t nd = 1;
+  for (int a = 0; a < 3; ++a) nd *= desc->periodic ? (int64_t)desc->ncell[a] * desc->p
+                                                   : (int64_t)desc->ncell[a] * desc->p - 1;
+  if (nd >= (int64_t)1 << 31) return CHFSI_ERR_ARG;
+  chfsi_ctx* ctx = new chfsi_ctx();
+  ctx->stream = (cudaStream_t)stream;
+  cudaGetDevice(&ctx->device);
+  build_mesh(*desc, ctx->mesh);
+  const HostMesh& m = ctx->mesh;
+  cudaError_t e;
+  if ((e = upload(ctx, &ctx->d_dofmap, m.dofmap)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_modes, m.modes)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_cells, m.colour_cells)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_mass, m.mass)) != cudaSuccess ||
+      (e = cudaEventCreate(&ctx->ev[0])) != cudaSuccess ||
+      (e = cudaEventCreate(&ctx->ev[1])) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    chfsi_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA;
+  }
+  *out = ctx;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
+  if (!ctx) return CHFSI_ERR_ARG;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  free_device_data(ctx);
+  const HostMesh& m = ctx->mesh;
+  release(ctx, ctx->d_dofmap, m.dofmap.size() * 4);
+  release(ctx, ctx->d_modes, m.modes.size());
+  release(ctx, ctx->d_cells, m.colour_cells.size() * 4);
+  release(ctx, ctx->d_mass, m.mass.size() * 8);
+  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
+                    &ctx->part, &ctx->vec, &ctx->lam})
+    dfree(ctx, b->ptr, b->bytes);
+  if (ctx->sol) cusolverDnDestroy(ctx->sol);
+  for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete ctx;
+  return CHFSI_OK;
+}
+
+const char* chfsi_last_error(const chfsi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t chfsi_num_dofs(const chfsi_ctx* ctx) { return ctx ? ctx->mesh.ndofs : -1; }
+
+int64_t chfsi_device_bytes(const chfsi_ctx* ctx) { return ctx ? ctx->dev_bytes : -1; }
+
+chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out) {
+  CHECK_CTX();
+  if (!host_out) return CHFSI_ERR_ARG;
+  std::memcpy(host_out, ctx->mesh.mass.data(), ctx->mesh.mass.size() * 8);
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_potential_gaussians(chfsi_ctx* ctx, int n, const double* xyz,
+                                           const double* depth, const double* width) {
+  CHECK_CTX();
+  if (n < 0 || (n > 0 && (!xyz || !depth || !width))) return fail(ctx, CHFSI_ERR_ARG, "bad wells");
+  for (int i = 0; i < n; ++i)
+    if (!(width[i] > 0.0)) return fail(ctx, CHFSI_ERR_ARG, "well width must be positive");
+  ctx->wells.xyz.assign(xyz, xyz + 3 * n);
+  ctx->wells.depth.assign(depth, depth + n);
+  ctx->wells.width.assign(width, width + n);
+  ctx->built = false;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_projectors(chfsi_ctx* ctx, int n, const double* xyz, const double* h,
+                                  double sigma, double rcut) {
+  CHECK_CTX();
+  if (n < 0 || (n > 0 && (!xyz || !h || !(sigma > 0.0) || !(rcut > 0.0))))
+    return fail(ctx, CHFSI_ERR_ARG, "bad projectors");
+  ctx->proj.xyz.assign(xyz, xyz + 3 * (size_t)n);
+  ctx->proj.h.assign(h, h + 4 * (size_t)n);
+  ctx->proj.sigma = sigma;
+  ctx->proj.rcut = rcut;
+  ctx->built = false;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_build(chfsi_ctx* ctx) {
+  CHECK_CTX();
+  CK(cudaStreamSynchronize(ctx->stream));
+  free_device_data(ctx);
+  const HostMesh& m = ctx->mesh;
+  std::vector<double> Ht;
+  build_cell_matrices(m, ctx->wells, Ht);
+  build_projectors(m, ctx->proj, ctx->hproj);
+  cudaError_t e;
+  if ((e = upload(ctx, &ctx->d_Ht, Ht)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                std::string("cell matrices: ") + cudaGetErrorString(e));
+  }
+  if (ctx->hproj.nsite > 0) {
+    std::vector<float> sc32(ctx->hproj.site_c.begin(), ctx->hproj.site_c.end());
+    std::vector<float> dc32(ctx->hproj.dof_c.begin(), ctx->hproj.dof_c.end());
+    CK(upload(ctx, &ctx->d_site_ptr, ctx->hproj.site_ptr));
+    CK(upload(ctx, &ctx->d_site_dof, ctx->hproj.site_dof));
+    CK(upload(ctx, &ctx->d_site_c, ctx->hproj.site_c));
+    CK(upload(ctx, &ctx->d_dof_ptr, ctx->hproj.dof_ptr));
+    CK(upload(ctx, &ctx->d_dof_site, ctx->hproj.dof_site));
+    CK(upload(ctx, &ctx->d_dof_c, ctx->hproj.dof_c));
+    CK(upload(ctx, &ctx->d_site_c32, sc32));
+    CK(upload(ctx, &ctx->d_dof_c32, dc32));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  cudaError_t te = tc_build(ctx->tc, Ht, m.ncells, m.ne, ctx->stream, &ctx->dev_bytes);
+  if (te != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, te == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                std::string("tensor-core cell data: ") + cudaGetErrorString(te));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->built = true;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block) {
+  CHECK_CTX();
+  if (filter_block < 1 || diag_block < 1) return fail(ctx, CHFSI_ERR_ARG, "block sizes must be >= 1");
+  ctx->filter_block = filter_block;
+  ctx->diag_block = diag_block;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_fill_uniform(chfsi_ctx* ctx, void* X, int64_t ldx, int64_t rows, int ncol,
+                                uint64_t seed, uint64_t stream, chfsi_precision prec) {
+  CHECK_CTX();
+  if (!valid_prec(prec) || rows < 0 || ncol < 0 || (rows * ncol > 0 && (!X || ldx < ncol)))
+    return fail(ctx, CHFSI_ERR_ARG, "bad fill arguments");
+  CK(launch_fill_uniform(X, ldx, rows, ncol, stream_key(seed, stream), prec == CHFSI_FP64, ctx->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy, int ncol,
+                         chfsi_precision prec) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, ncol, prec);
+  if (st != CHFSI_OK) return st;
+  if (ncol > 0 && (!Y || ldy < ncol)) return fail(ctx, CHFSI_ERR_ARG, "bad Y / ldy");
+  return apply_blocks(ctx, prec, X, ldx, Y, ldy, ncol);
+}
+
+chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
+                          double b, double a0, chfsi_precision prec) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, ncol, prec);
+  if (st != CHFSI_OK) return st;
+  if (degree < 1 || !(a0 < a) || !(a < b)) return fail(ctx, CHFSI_ERR_ARG, "filter needs degree >= 1 and a0 < a < b");
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  tic(ctx);
+  st = filter_impl(ctx, X, ldx, ncol, degree, a, b, a0, prec);
+  if (st == CHFSI_OK) toc(ctx, 0);
+  return st;
+}
+
+chfsi_status chfsi_cholgs(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  tic(ctx);
+  st = cholgs_impl(ctx, X, ldx, n, prec);
+  if (st == CHFSI_OK) toc(ctx, 1);
+  return st;
+}
+
+chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
+                                 double* evals_host) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  tic(ctx);
+  st = rr_impl(ctx, X, ldx, n, prec, evals_host);
+  if (st == CHFSI_OK) toc(ctx, 2);
+  return st;
+}
+
+chfsi_status chfsi_residuals(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
+                             const double* evals_host, double* res_host, double* gres_host) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (n > 0 && !evals_host) return fail(ctx, CHFSI_ERR_ARG, "evals required");
+  return residual_impl(ctx, X, ldx, n, prec, evals_host, res_host, gres_host);
+}
+
+chfsi_status chfsi_bounds(chfsi_ctx* ctx, int lanczos_steps, uint64_t seed, double* b_out) {
+  CHECK_CTX();
+  if (!ctx->built) return fail(ctx, CHFSI_ERR_STATE, "chfsi_build has not been called");
+  if (lanczos_steps < 1 || !b_out) return fail(ctx, CHFSI_ERR_ARG, "bad Lanczos arguments");
+  const int64_t M = ctx->mesh.ndofs;
+  chfsi_status st;
+  if ((st = grow(ctx, ctx->vec, (size_t)M * 8 * 3 + 64)) != CHFSI_OK) return st;
+  double* v = (double*)ctx->vec.ptr;
+  double* vp = v + M;
+  double* w = vp + M;
+  double* dot = (double*)ctx->lam.ptr;
+  if ((st = grow(ctx, ctx->lam, 64)) != CHFSI_OK) return st;
+  dot = (double*)ctx->lam.ptr;
+  if ((st = grow(ctx, ctx->part, (size_t)8 * 1024)) != CHFSI_OK) return st;
+  CK(launch_fill_uniform(v, 1, M, 1, stream_key(seed, 7), 1, ctx->stream));
+  CK(cudaMemsetAsync(vp, 0, M * 8, ctx->stream));
+  auto dotp = [&](const double* x, const double* y, double* r) -> chfsi_status {
+    CK(launch_gram_fp64(x, 1, y, 1, M, 1, 1, dot, 1, 0, (double*)ctx->part.ptr, ctx->part.bytes,
+                        ctx->stream));
+    CK(cudaMemcpyAsync(r, dot, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return CHFSI_OK;
+  };
+  double nv = 0.0;
+  if ((st = dotp(v, v, &nv)) != CHFSI_OK) return st;
+  CK(launch_scal_copy(v, v, M, 1.0 / std::sqrt(nv), ctx->stream));
+  std::vector<double> al, be;
+  double bprev = 0.0;
+  for (int k = 0; k < lanczos_steps; ++k) {
+    if ((st = apply_step(ctx, CHFSI_FP64, v, 1, w, 1, nullptr, 0, 1, 1.0, 0.0, 0.0)) != CHFSI_OK) return st;
+    CK(launch_axpy2(w, v, vp, M, 0.0, -bprev, ctx->stream));
+    double a = 0.0;
+    if ((st = dotp(w, v, &a)) != CHFSI_OK) return st;
+    CK(launch_axpy2(w, v, vp, M, -a, 0.0, ctx->stream));
+    double bb = 0.0;
+    if ((st = dotp(w, w, &bb)) != CHFSI_OK) return st;
+    bb = std::sqrt(bb);
+    al.push_back(a);
+    be.push_back(bb);
+    if (bb == 0.0) break;
+    CK(cudaMemcpyAsync(vp, v, M * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(launch_scal_copy(v, w, M, 1.0 / bb, ctx->stream));
+    bprev = bb;
+  }
+  // largest eigenvalue of the k x k tridiagonal by bisection (Sturm counts)
+  const int k = (int)al.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(be[i]) : 0.0);
+    lo = std::min(lo, al[i] - r);
+    hi = std::max(hi, al[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+      double off = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+      d = (al[i] - x) - (i > 0 ? off / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) cnt++;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-14 * std::max(1.0, std::fabs(hi)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= k) hi = mid;
+    else lo = mid;
+  }
+  *b_out = hi + std::fabs(be[k - 1]);
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters, int degree, double b,
+                         double tol, int n_check, chfsi_precision prec, double* evals_host,
+                         int* iters_done) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (n < 1 || iters < 0 || degree < 1 || !evals_host) return fail(ctx, CHFSI_ERR_ARG, "bad solve arguments");
+  if (n_check <= 0 || n_check > n) n_check = n;
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  std::vector<double> D(n), res(n);
+  tic(ctx);
+  if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
+  toc(ctx, 1);
+  tic(ctx);
+  if ((st = rr_impl(ctx, X, ldx, n, prec, D.data())) != CHFSI_OK) return st;
+  toc(ctx, 2);
+  int it = 0;
+  for (; it < iters; ++it) {
+    double a = D[n - 1], a0 = D[0];
+    if (!(a < b)) return fail(ctx, CHFSI_ERR_ARG, "upper bound b must exceed the largest Ritz value");
+    if (!(a0 < a)) a0 = a - 1e-3 * std::max(1.0, std::fabs(a));
+    tic(ctx);
+    if ((st = filter_impl(ctx, X, ldx, n, degree, a, b, a0, prec)) != CHFSI_OK) return st;
+    toc(ctx, 0);
+    tic(ctx);
+    if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
+    toc(ctx, 1);
+    tic(ctx);
+    if ((st = rr_impl(ctx, X, ldx, n, prec, D.data())) != CHFSI_OK) return st;
+    toc(ctx, 2);
+    if (tol > 0.0) {
+      tic(ctx);
+      if ((st = residual_impl(ctx, X, ldx, n_check, prec, D.data(), res.data(), nullptr)) != CHFSI_OK)
+        return st;
+      toc(ctx, 3);
+      double mx = *std::max_element(res.begin(), res.begin() + n_check);
+      if (mx < tol) { ++it; break; }
+    }
+  }
+  std::memcpy(evals_host, D.data(), (size_t)n * 8);
+  if (iters_done) *iters_done = it;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_unscale(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, chfsi_precision prec) {
+  CHECK_CTX();
+  if (!valid_prec(prec) || ncol < 0 || (ncol > 0 && (!X || ldx < ncol))) return fail(ctx, CHFSI_ERR_ARG, "bad X");
+  const HostMesh& m = ctx->mesh;
+  chfsi_status st;
+  if ((st = grow(ctx, ctx->vec, (size_t)m.ndofs * 8 * 3 + 64)) != CHFSI_OK) return st;
+  std::vector<double> s(m.ndofs);
+  for (int64_t j = 0; j < m.ndofs; ++j) s[j] = 1.0 / std::sqrt(m.mass[j]);
+  CK(cudaMemcpyAsync(ctx->vec.ptr, s.data(), s.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_scale_rows(X, ldx, m.ndofs, ncol, (const double*)ctx->vec.ptr, prec == CHFSI_FP64, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_last_timings(chfsi_ctx* ctx, double* out4) {
+  CHECK_CTX();
+  if (!out4) return CHFSI_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < 4; ++i) out4[i] = ctx->times[i];
+  return CHFSI_OK;
+}
+
+}  // extern "C"

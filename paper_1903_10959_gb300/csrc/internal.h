@@ -1,0 +1,142 @@
+// Internal declarations shared by the translation units of libchfsi.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/chfsi.h"
+
+namespace chfsi {
+
+// Assembly modes of one (cell, local node) pair.  Cells are processed colour
+// by colour; cells of one colour share no unknown.  For each unknown the
+// first cell (lowest colour) stores its contribution into the partial-sum
+// buffer W, intermediate cells add into W, and the last cell adds W to its
+// own contribution and finishes the Chebyshev update of that unknown.  An
+// unknown covered by a single cell is finished directly.
+enum NodeMode : uint8_t {
+  MODE_FINAL_DIRECT = 0,  // only contributor: finish from the cell result
+  MODE_STORE = 1,         // first of several: W = contribution
+  MODE_ACCUM = 2,         // middle: W += contribution
+  MODE_FINAL = 3,         // last: finish from W + contribution
+  MODE_SKIP = 4           // eliminated (Dirichlet) node
+};
+
+// ---------------------------------------------------------------- host mesh
+struct HostMesh {
+  int n[3];
+  double len[3], h[3];
+  int p, n1, ne, q;            // degree, nodes per direction, nodes per cell, quad points
+  bool periodic;
+  int64_t nd[3];               // unknowns per direction
+  int64_t ndofs;
+  int64_t ncells;
+  std::vector<int32_t> dofmap; // ncells * ne, -1 for eliminated
+  std::vector<uint8_t> modes;  // ncells * ne
+  std::vector<int32_t> colour_cells;   // cells ordered by colour
+  std::vector<int64_t> colour_offsets; // ncolours + 1
+  std::vector<double> mass;    // ndofs
+  // 1-D rules
+  std::vector<double> gll_x, gll_w, gq_x, gq_w;
+  std::vector<double> B, D;    // (q x n1) basis values / d/dxi at Gauss points
+};
+
+void build_mesh(const chfsi_mesh_desc& d, HostMesh& m);        // map, colours, modes, mass
+void gll_rule(int p, std::vector<double>& x, std::vector<double>& w);
+void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
+
+struct Wells {
+  std::vector<double> xyz, depth, width;
+};
+struct Projectors {
+  std::vector<double> xyz, h;
+  double sigma = 0.8, rcut = 3.0;
+};
+
+// Cell matrices H~_e (binary64, row-major ne x ne per cell) for all cells.
+void build_cell_matrices(const HostMesh& m, const Wells& w, std::vector<double>& Ht);
+
+// Scaled projector matrix C~ = C M^{-1/2} in two compressed forms:
+//  by site: for site s, rows [site_ptr[s], site_ptr[s+1]) of (dof, c[4]);
+//  by dof:  for unknown j, entries [dof_ptr[j], dof_ptr[j+1]) of (site, c[4]).
+struct HostProjectors {
+  int nsite = 0;
+  std::vector<int64_t> site_ptr;
+  std::vector<int32_t> site_dof;
+  std::vector<double> site_c;      // 4 per entry
+  std::vector<int64_t> dof_ptr;
+  std::vector<int32_t> dof_site;
+  std::vector<double> dof_c;       // 4 per entry, already multiplied by h
+};
+void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& out);
+
+// --------------------------------------------------------------- device side
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct FilterStep {       // one recurrence step Y_out = alpha (H~ Y_in - c Y_in) + beta Y_prev
+  double alpha, beta, shift;
+};
+
+// Launchers implemented in kernels_fp64.cu / kernels_tc.cu.  All take the
+// context stream and return cudaGetLastError() of the launch.
+struct CellLaunch {
+  const double* Ht;           // ncells * ne * ne (binary64)
+  const float* Ht32;          // tensor-core layout (mixed), may be null
+  const int32_t* dofmap;
+  const uint8_t* modes;
+  const int32_t* cells;       // cells of this colour
+  int64_t ncells_colour;
+  int ne;
+  int ncol;
+  int64_t ld;                 // leading dimension of Yin / Yout / Yprev / W / NL
+  int64_t ld_in, ld_out, ld_prev;
+};
+
+cudaError_t launch_cell_fp64(const CellLaunch& L, const double* Yin, double* Yout,
+                             const double* Yprev, double* W, const double* NL, int64_t ld_w,
+                             FilterStep st, cudaStream_t s);
+
+cudaError_t launch_fill_uniform(void* X, int64_t ldx, int64_t rows, int ncol, uint64_t key,
+                                int is_double, cudaStream_t s);
+cudaError_t launch_copy_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int64_t rows,
+                             int ncol, int src_double, int dst_double, cudaStream_t s);
+cudaError_t launch_scale_rows(void* X, int64_t ldx, int64_t rows, int ncol, const double* sv,
+                              int is_double, cudaStream_t s);
+
+// Gram: C(n1 x n2, column-major ldc) = A^T B over rows [0, M); A col offset
+// handled by the caller through pointers.  lower_only: skip tiles strictly
+// above the diagonal (i < j) when A == B geometry is square-symmetric.
+cudaError_t launch_gram_fp64(const double* A, int64_t lda, const double* B, int64_t ldb,
+                             int64_t M, int n1, int n2, double* C, int64_t ldc, int lower_only,
+                             double* partial, size_t partial_bytes, cudaStream_t s);
+// C(M x n2, row-major ldc) = A(M x n1, row-major lda) * U, U(n1 x n2) column-major ldu
+// (trans_u: U(k, j) read from U[j + k*ldu]); upper_tri: U(k, j) = 0 for k > j.
+cudaError_t launch_tallgemm_fp64(const double* A, int64_t lda, const double* U, int64_t ldu,
+                                 int64_t M, int n1, int n2, double* C, int64_t ldc, int upper_tri,
+                                 int trans_u, cudaStream_t s);
+// col norms: out[i] = sum_j w_j (Y[j,i] - lam_i X[j,i])^2 (w null -> 1), binary64 accumulation
+cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* X, int64_t ldx,
+                               int64_t M, int n, const double* lam, const double* wgt,
+                               double* out_sq, double* partial, size_t partial_bytes,
+                               cudaStream_t s);
+cudaError_t launch_axpy2(double* w, const double* v, const double* vp, int64_t M, double a,
+                         double b, cudaStream_t s);
+cudaError_t launch_scal_copy(double* v, const double* w, int64_t M, double sc, cudaStream_t s);
+
+// nonlocal: Z (nproj x ncol) = C~ Y ; NL (M x ncol) = C~^T h Z
+cudaError_t launch_nl_project_fp64(const int64_t* site_ptr, const int32_t* site_dof,
+                                   const double* site_c, int nsite, const double* Y, int64_t ldy,
+                                   int ncol, double* Z, cudaStream_t s);
+cudaError_t launch_nl_expand_fp64(const int64_t* dof_ptr, const int32_t* dof_site,
+                                  const double* dof_c, int64_t M, const double* Z, int ncol,
+                                  double* NL, int64_t ldn, cudaStream_t s);
+
+uint64_t stream_key(uint64_t seed, uint64_t stream);
+
+}  // namespace chfsi

@@ -1,0 +1,57 @@
+// Tensor-core (tcgen05, sm_103a) kernels of the mixed-precision path.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace chfsi {
+
+// Device copies of the cell matrices for the tensor-core cell products.
+struct TcCellData {
+  float* hi = nullptr;     // TF32-rounded H~_e in the UMMA operand layout
+  float* lo = nullptr;     // TF32-rounded residual H~_e - hi (same layout)
+  size_t bytes = 0;        // bytes of each of hi / lo
+  int64_t ncells = 0;
+  int ne = 0, mt = 0, kt = 0;   // ne, row tiles of 128, K padded to a multiple of 8
+};
+
+struct TcCellArgs {
+  const int32_t* cells;
+  int64_t ncells;
+  const int32_t* dofmap;
+  const uint8_t* modes;
+  int ncol;
+  const float* Yin;
+  int64_t ld_in;
+  float* Yout;
+  int64_t ld_out;
+  const float* Yprev;
+  int64_t ld_prev;
+  float* W;
+  const float* NL;
+  int64_t ld_w;
+  float alpha, beta, shift;
+  int split3;
+};
+
+cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
+                     cudaStream_t s, int64_t* dev_bytes);
+void tc_free(TcCellData& d);
+cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_t s);
+size_t tc_gram_partial_bytes(int64_t M, int n1, int n2);
+cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
+                          int n1, int n2, double* C, int64_t ldc, int lower, int diag_block,
+                          int split3, void* partial, size_t partial_bytes, cudaStream_t s);
+cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int64_t ldu, int64_t M,
+                              int n1, int n2, float* C, int64_t ldc, int upper, int trans,
+                              int diag_block, int split3, void* work, cudaStream_t s);
+cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, const float* site_c,
+                          int nsite, const float* Y, int64_t ldy, int ncol, float* Z,
+                          cudaStream_t s);
+cudaError_t tc_nl_expand(const int64_t* dof_ptr, const int32_t* dof_site, const float* dof_c,
+                         int64_t M, const float* Z, int ncol, float* NL, int64_t ldn,
+                         cudaStream_t s);
+
+}  // namespace chfsi

@@ -119,6 +119,7 @@ def test_dofmap_covers_unknowns(periodic):
     mesh = fe.Mesh(3, 2, 6.0, periodic)
     dm = mesh.dofmap()
     assert dm.shape == (27, 27)
+    assert np.array_equal(dm, np.stack([mesh.cell_dofs(e) for e in range(27)]))
     used = dm[dm >= 0]
     assert set(used.tolist()) == set(range(mesh.ndofs))
     counts = np.bincount(used, minlength=mesh.ndofs)

@@ -98,3 +98,16 @@ def test_gaussian_wells_periodic_images():
     assert abs(v[0] + 2.0 * np.exp(-0.03 / 2)) < 1e-12
     v_np = ham.gaussian_wells(x, [[0.0, 0.0, 0.0]], [2.0], [1.0], 10.0, False)
     assert abs(v_np[1]) < 1e-30
+
+
+def test_sampled_rows_match_full_apply():
+    rng = np.random.default_rng(2)
+    c = rng.uniform(0, 6, (2, 3))
+    for periodic in (True, False):
+        prob = ham.wells_problem(3, 2, 6.0, periodic, c, [1.0, 2.0], [1.0, 0.9],
+                                 projectors=dict(centres=c[:1], sigma=0.8, rcut=2.0,
+                                                 h=[[1, 0.5, 0.7, 2.0]]))
+        X = rng.standard_normal((prob.ndofs, 4))
+        rows = rng.choice(prob.ndofs, 9, replace=False)
+        full = prob.apply_Htilde(X)
+        assert np.abs(prob.apply_Htilde_rows(rows, X) - full[rows]).max() < 1e-12 * np.abs(full).max()
