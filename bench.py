@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""ChFSI benchmark on GB300: seconds per ChFSI iteration on the periodic FCC
+Gaussian-well workload (16^3 cells, p = 6, 884,736 unknowns, N = 1000 wanted
+pairs + 100 buffer, filter block 200, Chebyshev degree 40).
+
+One step = one ChFSI iteration on device-resident data: Chebyshev filter
+(Eq. chebFilter), CholGS (Algorithm CholGS) and Rayleigh-Ritz (Sec. 3.5) of
+arXiv:1903.10959, each through the library's C ABI.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (extrapolated to one iteration by exact operation
+counts).  With N > 1 (torchrun) every rank runs an independent replica of the
+workload (the path has no data-path collective; "replicas only").
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ChFSI s/iter (filter + CholGS + RR), fcc-periodic 16^3 cells p=6"
+UNIT = "s/iter"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "tf32"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="small case for profiling runs")
+    return ap.parse_args()
+
+
+def workload(small=False):
+    from paper_1903_10959_gb300 import workloads as W
+    if small:
+        return W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=200, degree=40, iters=4, block=200)
+    return W.fcc_periodic()
+
+
+def workload_config(s, l2_note):
+    return {
+        "workload": "fcc-periodic %d^3 cells p=%d L=%g, %d unknowns, %d Gaussian wells, "
+                    "N=%d (+%d buffer), filter block %d, Chebyshev degree %d"
+                    % (s.ncell, s.p, s.L, s.ndofs, len(s.depths), s.n_want, s.n_buffer, s.block,
+                       s.degree),
+        "unknowns": s.ndofs, "n_sub": s.n_sub, "block": s.block, "degree": s.degree, "p": s.p,
+        "cells": s.ncell ** 3, "l2": l2_note,
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample_seconds(s, rows_sample=20000, cells_sample=24):
+    """Extrapolated seconds of one oracle ChFSI iteration on the workload.
+
+    Sample: the oracle's cell loop (H_e X_e gather/scatter, Eq. discreteHam) on
+    `cells_sample` cells x one filter block, the recurrence update, and the
+    dense CholGS / RR products on `rows_sample` rows; each timed piece is scaled
+    by its exact operation count to the full iteration."""
+    from oracle import hamiltonian as oham
+    prob = oham.wells_problem(s.ncell, s.p, s.L, True, s.centres, s.depths, s.widths)
+    n, B, m = s.n_sub, s.block, s.degree
+    M = prob.ndofs
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1, 1, (M, B))
+    cells = list(range(cells_sample))
+    for e in cells:
+        prob.cell_hamiltonian(e)            # build outside the timed region
+    dm = prob.mesh.dofmap()
+    out = np.zeros_like(X)
+    t0 = time.perf_counter()
+    for e in cells:
+        d = dm[e]
+        out[d] += prob.cell_hamiltonian(e) @ X[d]
+    t_cells = time.perf_counter() - t0
+    t_apply = t_cells / cells_sample * prob.mesh.ncells          # one H X on B columns
+    Xs = X[:rows_sample]
+    t0 = time.perf_counter()
+    Y = 0.5 * (Xs - 0.3 * Xs) - 0.2 * Xs                           # recurrence update
+    t_upd = (time.perf_counter() - t0) * M / rows_sample
+    nb = -(-n // B)
+    t_filter = m * nb * (t_apply + t_upd)
+    Xr = rng.uniform(-1, 1, (rows_sample, n))
+    t0 = time.perf_counter()
+    S = Xr.T @ Xr
+    t_gram = (time.perf_counter() - t0) * M / rows_sample
+    S = S + n * np.eye(n)
+    import scipy.linalg as sla
+    t0 = time.perf_counter()
+    L = np.linalg.cholesky(S)
+    Linv = sla.solve_triangular(L, np.eye(n), lower=True)
+    t_fact = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _ = Xr @ Linv.T
+    t_rot = (time.perf_counter() - t0) * M / rows_sample
+    t0 = time.perf_counter()
+    _ = np.linalg.eigh(0.5 * (S + S.T))
+    t_eig = time.perf_counter() - t0
+    del Y
+    t_cholgs = t_gram + t_fact + t_rot
+    t_rr = nb * t_apply + t_gram + t_eig + t_rot
+    total = t_filter + t_cholgs + t_rr
+    sample = ("oracle cell loop on %d of %d cells x %d columns, recurrence and dense products on "
+              "%d of %d rows, %dx%d Cholesky/eigh in full; scaled by exact operation counts to "
+              "one iteration" % (cells_sample, prob.mesh.ncells, B, rows_sample, M, n, n))
+    return total, sample, {"filter": t_filter, "cholgs": t_cholgs, "rr": t_rr}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s = workload(args.small)
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t, sample, _ = oracle_sample_seconds(s)
+        if i >= args.warmup:
+            times.append(t)
+    v = float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(s, "host memory"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_1903_10959_gb300 import Context, _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    s = workload(args.small)
+    prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32"}[args.prec]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    stream = torch.cuda.current_stream()
+    ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
+    ctx.set_potential_gaussians(s.centres, s.depths, s.widths)
+    ctx.build()
+    ctx.set_blocking(s.block, 8)
+    n, M = s.n_sub, ctx.ndofs
+    b = ctx.bounds(20, s.seed)
+    X = torch.empty((M, n), dtype=dt, device="cuda")
+    ctx.fill_uniform(X, s.seed, prec=prec)
+    ctx.cholgs(X, prec=prec)
+    state = {"D": ctx.rayleigh_ritz(X, prec=prec)}
+    phase = np.zeros(3)
+
+    def step():
+        D = state["D"]
+        ctx.filter(X, s.degree, float(D[-1]), b, float(D[0]), prec=prec)
+        phase[0] += ctx.last_timings()[0]
+        ctx.cholgs(X, prec=prec)
+        phase[1] += ctx.last_timings()[1]
+        state["D"] = ctx.rayleigh_ritz(X, prec=prec)
+        phase[2] += ctx.last_timings()[2]
+
+    for _ in range(args.warmup):
+        step()
+    phase[:] = 0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = _lib.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.kernel_launches() - l0
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    if dist:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        dist.barrier()
+    value = t / (args.steps * world)
+
+    # roofline of the dominant kernel (the tensor-core / binary64 cell kernel of the filter)
+    ncolour = 8
+    nblocks = -(-n // s.block)
+    launches_filter = args.steps * s.degree * nblocks * ncolour
+    filter_s = phase[0] / 1e3
+    ne = (s.p + 1) ** 3
+    sx = 8 if prec == "fp64" else 4
+    sh = 8
+    alg_bytes = args.steps * s.degree * (3 * sx * M * n + nblocks * s.ncell ** 3 * ne * ne * sh)
+    alg_flops = args.steps * s.degree * n * (s.ncell ** 3) * 2 * ne * ne
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    achieved = alg_bytes / filter_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "tc_cell_kernel" if prec != "fp64" else "cell_fp64_kernel",
+            "launches": launches_filter, "avg_launch_ms": phase[0] / launches_filter,
+            "bytes_per_launch": alg_bytes / launches_filter,
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    if prec == "fp64":
+        roof.update({"bound": "alu", "achieved": alg_flops / filter_s / 1e12, "peak": 1.0,
+                     "unit": "TFLOP/s", "frac": alg_flops / filter_s / 1e12 / 1.0,
+                     "peak_note": "binary64 DFMA peak 1.0 TFLOP/s measured by a DFMA probe"})
+
+    # end to end through host buffers: H2D of X, one iteration, D2H of X and the Ritz values
+    e2e = None
+    if args.e2e_steps > 0:
+        Xh = torch.empty((M, n), dtype=dt, pin_memory=True)
+        Xh.copy_(X.cpu())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            X.copy_(Xh, non_blocking=True)
+            step()
+            Xh.copy_(X, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        nbytes = M * n * X.element_size()
+        e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes + n * 8,
+               "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        tcpu, sample, parts = oracle_sample_seconds(s)
+        cpu = {"value": tcpu, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": sample, "phases_s": parts}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else ("tf32x3" if prec == "mixed" else "tf32"),
+        "data": "synthetic",
+        "config": workload_config(s, "inputs larger than L2: X %.1f GB, cell matrices %.1f GB"
+                                  % (M * n * sx / 1e9, s.ncell ** 3 * ne * ne * 8 / 1e9)),
+        "phases_ms_per_step": {"filter": phase[0] / args.steps, "cholgs": phase[1] / args.steps,
+                               "rr": phase[2] / args.steps},
+        "filter_tflops": {"algorithmic": alg_flops / filter_s / 1e12,
+                          "executed_tensor": (3 if prec == "mixed" else 1) * alg_flops / filter_s / 1e12
+                          if prec != "fp64" else None},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+    }
+    print(json.dumps(line), flush=True)
+    ctx.destroy()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -47,7 +47,8 @@ typedef enum {
   CHFSI_ERR_CUDA = 3,     /* CUDA / cuSOLVER failure; see chfsi_last_error                */
   CHFSI_ERR_NOT_SPD = 4,  /* CholGS: overlap matrix not positive definite (X unchanged)   */
   CHFSI_ERR_EIG = 5,      /* Rayleigh-Ritz: eigensolver did not converge                 */
-  CHFSI_ERR_STATE = 6     /* call made before the data it needs (e.g. filter before build) */
+  CHFSI_ERR_STATE = 6,    /* call made before the data it needs (e.g. filter before build) */
+  CHFSI_ERR_TIMEOUT = 7   /* a bounded device-side wait gave up (kernel unwound; see last_error) */
 } chfsi_status;
 
 typedef enum {
@@ -111,7 +112,7 @@ chfsi_status chfsi_build(chfsi_ctx* ctx);
 
 /* Column block size of the filter (Sec. 3.3.1 "B^f"; default 200 or ncol if
  * smaller) and diagonal block size of the mixed overlap/projection products
- * (default 32).  Takes effect on the next call. */
+ * (default 8, a power of two <= 32).  Takes effect on the next call. */
 chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block);
 
 /* Fill rows x ncol of X (device, leading dimension ldx) with the seeded
@@ -161,7 +162,10 @@ chfsi_status chfsi_bounds(chfsi_ctx* ctx, int lanczos_steps, uint64_t seed, doub
  * (step 7 of Algorithm scf).  b: upper bound (chfsi_bounds).  evals_host[n]
  * receives the final Ritz values.  When tol > 0 the loop stops early once
  * the largest residual of the lowest n_check pairs is below tol (adaptive
- * filtering, Sec. 3.3); n_check <= 0 means n.  iters_done may be NULL. */
+ * filtering, Sec. 3.3); n_check <= 0 means n.  iters_done may be NULL.
+ * Mixed precisions: every RR but the last uses the tensor-core operator;
+ * the last one applies H~ with binary64 cell products, so the returned
+ * eigenvalues carry only second-order error from the binary32 subspace. */
 chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters, int degree,
                          double b, double tol, int n_check, chfsi_precision prec,
                          double* evals_host, int* iters_done);
@@ -176,6 +180,10 @@ chfsi_status chfsi_last_timings(chfsi_ctx* ctx, double* out4);
 
 /* Bytes of device memory the context currently holds. */
 int64_t      chfsi_device_bytes(const chfsi_ctx* ctx);
+
+/* Number of kernels this library has launched so far (all contexts; a
+ * monotonic counter for accounting, e.g. launches per ChFSI iteration). */
+int64_t      chfsi_kernel_launches(void);
 
 #ifdef __cplusplus
 }

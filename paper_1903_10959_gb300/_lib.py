@@ -20,7 +20,7 @@ FP64, MIXED_TF32X3, MIXED_TF32 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "mixed": MIXED_TF32X3, "tf32x3": MIXED_TF32X3, "tf32": MIXED_TF32}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_SPD", 5: "ERR_EIG",
-          6: "ERR_STATE"}
+          6: "ERR_STATE", 7: "ERR_TIMEOUT"}
 
 
 class ChfsiError(RuntimeError):
@@ -62,6 +62,7 @@ _SIGS = {
                               C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]),
     "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
     "chfsi_last_timings": (C.c_int, [_vp, _dp]),
+    "chfsi_kernel_launches": (_i64, []),
 }
 
 
@@ -81,6 +82,11 @@ def load(path: str | None = None):
     if path == LIB_PATH:
         _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libchfsi so far (chfsi_kernel_launches)."""
+    return int(load().chfsi_kernel_launches())
 
 
 def exported_symbols():
@@ -185,7 +191,7 @@ class Context:
     def build(self):
         self._check(self._lib.chfsi_build(self._h))
 
-    def set_blocking(self, filter_block=200, diag_block=32):
+    def set_blocking(self, filter_block=200, diag_block=8):
         self._check(self._lib.chfsi_set_blocking(self._h, int(filter_block), int(diag_block)))
 
     def fill_uniform(self, X, seed, stream=1, prec="fp64"):

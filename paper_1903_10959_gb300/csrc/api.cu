@@ -15,6 +15,13 @@
 
 using namespace chfsi;
 
+#include <atomic>
+namespace chfsi {
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace chfsi
+
 struct chfsi_ctx {
   HostMesh mesh;
   Wells wells;
@@ -25,7 +32,7 @@ struct chfsi_ctx {
   bool built = false;
   chfsi_status latched = CHFSI_OK;
   std::string err;
-  int filter_block = 200, diag_block = 32;
+  int filter_block = 200, diag_block = 8;
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices
@@ -181,6 +188,14 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     return CHFSI_OK;
   }
   // mixed precisions: binary32 storage, tcgen05 TF32 cell products
+  if (!ctx->tc.hi) {
+    cudaError_t pe = tc_pack_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("tensor-core cell data: ") + cudaGetErrorString(pe));
+    }
+  }
   if (nl) {
     CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
                      (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
@@ -230,6 +245,14 @@ chfsi_status check_x(chfsi_ctx* ctx, const void* X, int64_t ldx, int ncol, chfsi
   if (!valid_prec(prec)) return fail(ctx, CHFSI_ERR_ARG, "unknown precision");
   if (!ctx->built) return fail(ctx, CHFSI_ERR_STATE, "chfsi_build has not been called");
   if (ncol < 0 || (ncol > 0 && (!X || ldx < ncol))) return fail(ctx, CHFSI_ERR_ARG, "bad X / ldx / ncol");
+  return CHFSI_OK;
+}
+
+// Device-side bounded waits report through a status word; map it to an error.
+chfsi_status check_device_status(chfsi_ctx* ctx, chfsi_precision prec) {
+  if (!is_mixed(prec)) return CHFSI_OK;
+  int v = tc_read_status(ctx->stream);
+  if (v) return fail(ctx, CHFSI_ERR_TIMEOUT, "device wait timed out (site " + std::to_string(v) + ")");
   return CHFSI_OK;
 }
 
@@ -315,6 +338,7 @@ chfsi_status rotate_impl(chfsi_ctx* ctx, chfsi_precision prec, void* X, int64_t 
     CK(launch_tallgemm_fp64((const double*)X, ldx, U, n, m.ndofs, n, n, (double*)ctx->rot.ptr, n,
                             upper, trans, ctx->stream));
   } else {
+    if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n))) != CHFSI_OK) return st;
     CK(tc_tallgemm_mixed((const float*)X, ldx, U, n, m.ndofs, n, n, (float*)ctx->rot.ptr, n, upper,
                          trans, ctx->diag_block, prec == CHFSI_MIXED_TF32X3, ctx->work.ptr,
                          ctx->stream));
@@ -366,8 +390,11 @@ chfsi_status cholgs_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_prec
   return rotate_impl(ctx, prec, X, ldx, n, S, 1, 1);
 }
 
+// Rayleigh-Ritz.  fp64_apply: for the mixed precisions, evaluate H~ X with the
+// binary64 cell products (then round to binary32) so that H^ carries no
+// binary32-accumulation bias; used for the last RR of a mixed solve.
 chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
-                     double* evals_host) {
+                     double* evals_host, bool fp64_apply = false) {
   const HostMesh& m = ctx->mesh;
   chfsi_status st;
   if (n == 0) return CHFSI_OK;
@@ -379,12 +406,22 @@ chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precisio
   const size_t es = esize(prec);
   const int B = std::max(1, std::min(ctx->filter_block, n));
   if ((st = grow(ctx, ctx->T1, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+  const bool via64 = fp64_apply && is_mixed(prec);
+  if (via64 && (st = grow(ctx, ctx->rot, (size_t)m.ndofs * B * 8 * 2)) != CHFSI_OK) return st;
   // 1. H^ = X^T (H~ X), lower triangle, one column block at a time
   for (int j0 = 0; j0 < n; j0 += B) {
     const int nb = std::min(B, n - j0);
-    if ((st = apply_step(ctx, prec, (const char*)X + j0 * es, ldx, ctx->T1.ptr, nb, nullptr, 0, nb,
-                         1.0, 0.0, 0.0)) != CHFSI_OK)
+    if (via64) {
+      double* X64 = (double*)ctx->rot.ptr;
+      double* Y64 = X64 + (size_t)m.ndofs * B;
+      CK(launch_copy_cols((const char*)X + j0 * es, ldx, X64, nb, m.ndofs, nb, 0, 1, ctx->stream));
+      if ((st = apply_step(ctx, CHFSI_FP64, X64, nb, Y64, nb, nullptr, 0, nb, 1.0, 0.0, 0.0)) != CHFSI_OK)
+        return st;
+      CK(launch_copy_cols(Y64, nb, ctx->T1.ptr, nb, m.ndofs, nb, 1, 0, ctx->stream));
+    } else if ((st = apply_step(ctx, prec, (const char*)X + j0 * es, ldx, ctx->T1.ptr, nb, nullptr, 0,
+                                nb, 1.0, 0.0, 0.0)) != CHFSI_OK) {
       return st;
+    }
     if ((st = gram_impl(ctx, prec, (const char*)X + j0 * es, ldx, ctx->T1.ptr, nb, n - j0, nb,
                         Hh + j0 + (int64_t)j0 * n, n, 1)) != CHFSI_OK)
       return st;
@@ -507,6 +544,8 @@ int64_t chfsi_num_dofs(const chfsi_ctx* ctx) { return ctx ? ctx->mesh.ndofs : -1
 
 int64_t chfsi_device_bytes(const chfsi_ctx* ctx) { return ctx ? ctx->dev_bytes : -1; }
 
+int64_t chfsi_kernel_launches(void) { return launch_count(); }
+
 chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out) {
   CHECK_CTX();
   if (!host_out) return CHFSI_ERR_ARG;
@@ -567,7 +606,7 @@ chfsi_status chfsi_build(chfsi_ctx* ctx) {
     CK(upload(ctx, &ctx->d_dof_c32, dc32));
     CK(cudaStreamSynchronize(ctx->stream));
   }
-  cudaError_t te = tc_build(ctx->tc, Ht, m.ncells, m.ne, ctx->stream, &ctx->dev_bytes);
+  cudaError_t te = tc_build(ctx->tc, Ht, m.ncells, m.ne, ctx->stream, &ctx->dev_bytes);   // packed lazily
   if (te != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, te == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
@@ -601,7 +640,9 @@ chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, in
   chfsi_status st = check_x(ctx, X, ldx, ncol, prec);
   if (st != CHFSI_OK) return st;
   if (ncol > 0 && (!Y || ldy < ncol)) return fail(ctx, CHFSI_ERR_ARG, "bad Y / ldy");
-  return apply_blocks(ctx, prec, X, ldx, Y, ldy, ncol);
+  st = apply_blocks(ctx, prec, X, ldx, Y, ldy, ncol);
+  if (st == CHFSI_OK) st = check_device_status(ctx, prec);
+  return st;
 }
 
 chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
@@ -614,6 +655,7 @@ chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int de
   tic(ctx);
   st = filter_impl(ctx, X, ldx, ncol, degree, a, b, a0, prec);
   if (st == CHFSI_OK) toc(ctx, 0);
+  if (st == CHFSI_OK) st = check_device_status(ctx, prec);
   return st;
 }
 
@@ -625,6 +667,7 @@ chfsi_status chfsi_cholgs(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_pre
   tic(ctx);
   st = cholgs_impl(ctx, X, ldx, n, prec);
   if (st == CHFSI_OK) toc(ctx, 1);
+  if (st == CHFSI_OK) st = check_device_status(ctx, prec);
   return st;
 }
 
@@ -637,6 +680,7 @@ chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* ctx, void* X, int64_t ldx, int n, ch
   tic(ctx);
   st = rr_impl(ctx, X, ldx, n, prec, evals_host);
   if (st == CHFSI_OK) toc(ctx, 2);
+  if (st == CHFSI_OK) st = check_device_status(ctx, prec);
   return st;
 }
 
@@ -735,7 +779,7 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
   if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
   toc(ctx, 1);
   tic(ctx);
-  if ((st = rr_impl(ctx, X, ldx, n, prec, D.data())) != CHFSI_OK) return st;
+  if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), iters == 0)) != CHFSI_OK) return st;
   toc(ctx, 2);
   int it = 0;
   for (; it < iters; ++it) {
@@ -749,7 +793,8 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
     if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
     toc(ctx, 1);
     tic(ctx);
-    if ((st = rr_impl(ctx, X, ldx, n, prec, D.data())) != CHFSI_OK) return st;
+    const bool last = (it + 1 == iters);
+    if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), last)) != CHFSI_OK) return st;
     toc(ctx, 2);
     if (tol > 0.0) {
       tic(ctx);
@@ -757,9 +802,18 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
         return st;
       toc(ctx, 3);
       double mx = *std::max_element(res.begin(), res.begin() + n_check);
-      if (mx < tol) { ++it; break; }
+      if (mx < tol) {
+        ++it;
+        if (!last && is_mixed(prec)) {   // stopping early: redo the last RR with binary64 products
+          tic(ctx);
+          if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), true)) != CHFSI_OK) return st;
+          toc(ctx, 2);
+        }
+        break;
+      }
     }
   }
+  if ((st = check_device_status(ctx, prec)) != CHFSI_OK) return st;
   std::memcpy(evals_host, D.data(), (size_t)n * 8);
   if (iters_done) *iters_done = it;
   return CHFSI_OK;

@@ -139,4 +139,8 @@ cudaError_t launch_nl_expand_fp64(const int64_t* dof_ptr, const int32_t* dof_sit
 
 uint64_t stream_key(uint64_t seed, uint64_t stream);
 
+// Count of kernel launches issued by this library (all contexts, monotonic).
+void note_launch();
+int64_t launch_count();
+
 }  // namespace chfsi

@@ -91,6 +91,7 @@ cudaError_t launch_cell_fp64(const CellLaunch& L, const double* Yin, double* You
                            96 * 1024);                                                            \
       attr_##B = true;                                                                            \
     }                                                                                             \
+    note_launch();                                                                                \
     cell_fp64_kernel<B><<<grid, 256, smem, s>>>(L.Ht, L.dofmap, L.modes, L.cells, L.ne, L.ncol,   \
                                                 Yin, L.ld_in, Yout, L.ld_out, prev, L.ld_prev, W,  \
                                                 ld_w, NL, st.alpha, st.beta, st.shift);           \
@@ -176,8 +177,10 @@ cudaError_t launch_gram_fp64(const double* A, int64_t lda, const double* B, int6
   nsplit = (M + rps - 1) / rps;
   if (nsplit < 1) nsplit = 1;
   dim3 grid(t1, t2, (unsigned)nsplit);
+  note_launch();
   gram_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, M, n1, n2, lower_only, rps, partial);
   const int64_t tot = (int64_t)n1 * n2;
+  note_launch();
   gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(partial, (int)nsplit, n1, n2, C,
                                                                    ldc, lower_only);
   return cudaGetLastError();
@@ -238,6 +241,7 @@ cudaError_t launch_tallgemm_fp64(const double* A, int64_t lda, const double* U, 
                                  int trans_u, cudaStream_t s) {
   if (M == 0 || n2 == 0) return cudaSuccess;
   dim3 grid((unsigned)((M + GT - 1) / GT), (unsigned)((n2 + GT - 1) / GT));
+  note_launch();
   tallgemm_fp64_kernel<<<grid, 256, 0, s>>>(A, lda, U, ldu, M, n1, n2, C, ldc, upper_tri, trans_u);
   return cudaGetLastError();
 }
@@ -298,7 +302,9 @@ cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* X, in
   int64_t rpc = (M + nchunk - 1) / nchunk;
   nchunk = (M + rpc - 1) / rpc;
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)nchunk);
+  note_launch();
   resid_partial_kernel<<<grid, 256, 0, s>>>(Y, ldy, X, ldx, M, n, lam, wgt, rpc, partial);
+  note_launch();
   resid_reduce_kernel<<<(3 * n + 255) / 256, 256, 0, s>>>(partial, (int)nchunk, n, out_sq);
   return cudaGetLastError();
 }
@@ -358,6 +364,7 @@ cudaError_t launch_nl_project_fp64(const int64_t* site_ptr, const int32_t* site_
                                    int ncol, double* Z, cudaStream_t s) {
   if (nsite == 0 || ncol == 0) return cudaSuccess;
   dim3 grid(nsite, (ncol + 31) / 32);
+  note_launch();
   nl_project_kernel<<<grid, 128, 0, s>>>(site_ptr, site_dof, site_c, Y, ldy, ncol, Z);
   return cudaGetLastError();
 }
@@ -367,6 +374,7 @@ cudaError_t launch_nl_expand_fp64(const int64_t* dof_ptr, const int32_t* dof_sit
                                   double* NL, int64_t ldn, cudaStream_t s) {
   const int64_t tot = M * ncol;
   if (tot == 0) return cudaSuccess;
+  note_launch();
   nl_expand_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dof_ptr, dof_site, dof_c, M, Z,
                                                                   ncol, NL, ldn);
   return cudaGetLastError();
@@ -404,6 +412,7 @@ cudaError_t launch_fill_uniform(void* X, int64_t ldx, int64_t rows, int ncol, ui
                                 int is_double, cudaStream_t s) {
   const int64_t tot = rows * ncol;
   if (tot == 0) return cudaSuccess;
+  note_launch();
   fill_uniform_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ldx, rows, ncol, key,
                                                                      is_double);
   return cudaGetLastError();
@@ -424,6 +433,7 @@ cudaError_t launch_copy_cols(const void* src, int64_t lds, void* dst, int64_t ld
                              int ncol, int src_double, int dst_double, cudaStream_t s) {
   const int64_t tot = rows * ncol;
   if (tot == 0) return cudaSuccess;
+  note_launch();
   copy_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, lds, dst, ldd, rows, ncol,
                                                                   src_double, dst_double);
   return cudaGetLastError();
@@ -443,6 +453,7 @@ cudaError_t launch_scale_rows(void* X, int64_t ldx, int64_t rows, int ncol, cons
                               int is_double, cudaStream_t s) {
   const int64_t tot = rows * ncol;
   if (tot == 0) return cudaSuccess;
+  note_launch();
   scale_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ldx, rows, ncol, sv, is_double);
   return cudaGetLastError();
 }
@@ -461,10 +472,12 @@ __global__ void scal_copy_kernel(double* v, const double* w, int64_t M, double s
 
 cudaError_t launch_axpy2(double* w, const double* v, const double* vp, int64_t M, double a,
                          double b, cudaStream_t s) {
+  note_launch();
   axpy2_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(w, v, vp, M, a, b);
   return cudaGetLastError();
 }
 cudaError_t launch_scal_copy(double* v, const double* w, int64_t M, double sc, cudaStream_t s) {
+  note_launch();
   scal_copy_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(v, w, M, sc);
   return cudaGetLastError();
 }

@@ -1,23 +1,942 @@
-// Mixed-precision (tcgen05) kernels -- placeholder until the tensor-core path lands.
+// Mixed-precision kernels on the 5th-generation tensor cores (tcgen05,
+// kind::tf32, FP32 accumulation in TMEM) for sm_103a.
+//
+// Precision scheme (the mixed strategy of Secs. 3.4.1 and 3.5.2 of
+// arXiv:1903.10959, moved onto tensor cores): every operand x is split into
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi); a product a.b is evaluated as
+// a_lo.b_hi + a_hi.b_lo + a_hi.b_hi ("3xTF32", binary32-level accuracy) or
+// as a_hi.b_hi alone ("1xTF32").  Wavefunction blocks are stored in
+// binary32.  Diagonal blocks of the overlap / projected matrices and of the
+// CholGS factor are evaluated in binary64 (the paper's S_d and L^{-1}_d).
+//
+//  tc_cell      : one colour of the cell-by-cell H~ Y (Sec. 3.3.1) fused with
+//                 the Chebyshev update (Eq. chebFilter).  One CTA per
+//                 (cell, 64-column tile); warp-specialised: warp 4 streams
+//                 the pre-split cell matrix with bulk async copies, warps 0-3
+//                 gather + split the cell block of Y into shared memory and
+//                 later run the colour-mode epilogue, warp 5 issues the MMAs.
+//  tc_gram      : lower tiles of A^T B over the unknowns (Algorithm CholGS
+//                 step 1; H^ of Sec. 3.5), split-K, fixed-order reduction.
+//  tc_tallgemm  : X U (Algorithm CholGS step 4, subspace rotation of Sec. 3.5).
+#include <algorithm>
+#include <cstdio>
+
 #include "internal.h"
 #include "tc.h"
+#include "tc_ptx.cuh"
 
 namespace chfsi {
 
-cudaError_t tc_build(TcCellData& d, const std::vector<double>&, int64_t, int, cudaStream_t, int64_t*) {
+using namespace ptx;
+
+__device__ int g_tc_status = 0;   // nonzero after a bounded wait gave up
+
+constexpr int CELL_BN = 64;       // columns per CTA
+constexpr int CELL_KC = 8;        // K per pipeline stage (one MMA K-step)
+constexpr int CELL_THREADS = 192;
+
+// ----------------------------------------------------------------- packing
+// Cell matrix layout for the MMA A operand: per cell, per K-chunk of 8, the hi
+// part for all M-tiles, then the lo part; each M-tile block is 128 rows x 8 K
+// in the no-swizzle K-major core-matrix layout (LBO 128 B along K, SBO 256 B
+// along M).
+__device__ __host__ __forceinline__ int cell_elem_off(int r, int k) {
+  return (r >> 3) * 64 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);   // in floats
+}
+
+__global__ void tc_pack_kernel(const double* __restrict__ Ht, float* __restrict__ out,
+                               int64_t ncells, int ne, int mt, int nk) {
+  const int64_t per_cell = (int64_t)nk * 2 * mt * 1024;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ncells * per_cell / 2) return;
+  // one thread per (cell, kc, mtile, r, k) of the hi half; writes hi and lo
+  const int64_t e = idx / (per_cell / 2);
+  int64_t rem = idx - e * (per_cell / 2);
+  const int kc = (int)(rem / (mt * 1024));
+  rem -= (int64_t)kc * mt * 1024;
+  const int t = (int)(rem / 1024);
+  const int w = (int)(rem - t * 1024);
+  const int r = w / 8, k = w % 8;
+  const int row = t * 128 + r, col = kc * CELL_KC + k;
+  double v = (row < ne && col < ne) ? Ht[(e * ne + row) * (int64_t)ne + col] : 0.0;
+  // round to TF32 (nearest, ties away), then the residual
+  float hi = ptx::tf32_rna((float)v);
+  float lo = ptx::tf32_rna((float)(v - (double)hi));
+  float* base = out + e * per_cell + (int64_t)kc * 2 * mt * 1024;
+  const int o = cell_elem_off(r, k);
+  base[t * 1024 + o] = hi;
+  base[mt * 1024 + t * 1024 + o] = lo;
+}
+
+cudaError_t tc_build(TcCellData& d, const std::vector<double>&, int64_t ncells, int ne,
+                     cudaStream_t s, int64_t* dev_bytes) {
+  // the device copy of the binary64 cell matrices is packed by tc_pack_from_device
+  (void)s;
+  (void)dev_bytes;
   d = TcCellData();
+  d.ncells = ncells;
+  d.ne = ne;
+  d.mt = (ne + 127) / 128;
+  d.kt = (ne + CELL_KC - 1) / CELL_KC * CELL_KC;
   return cudaSuccess;
 }
-void tc_free(TcCellData& d) { d = TcCellData(); }
-cudaError_t tc_cell_launch(const TcCellData&, const TcCellArgs&, cudaStream_t) { return cudaErrorNotSupported; }
-size_t tc_gram_partial_bytes(int64_t, int, int) { return 16; }
-cudaError_t tc_gram_mixed(const float*, int64_t, const float*, int64_t, int64_t, int, int, double*, int64_t,
-                          int, int, int, void*, size_t, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_tallgemm_mixed(const float*, int64_t, const double*, int64_t, int64_t, int, int, float*,
-                              int64_t, int, int, int, int, void*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_nl_project(const int64_t*, const int32_t*, const float*, int, const float*, int64_t, int,
-                          float*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_nl_expand(const int64_t*, const int32_t*, const float*, int64_t, const float*, int, float*,
-                         int64_t, cudaStream_t) { return cudaErrorNotSupported; }
+
+cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                int64_t* dev_bytes) {
+  const int nk = d.kt / CELL_KC;
+  const size_t per_cell = (size_t)nk * 2 * d.mt * 1024 * sizeof(float);
+  d.bytes = per_cell * d.ncells;
+  cudaError_t e = cudaMalloc(&d.hi, d.bytes);
+  if (e != cudaSuccess) {
+    d.hi = nullptr;
+    d.bytes = 0;
+    return e;
+  }
+  if (dev_bytes) *dev_bytes += (int64_t)d.bytes;
+  const int64_t n = d.ncells * (int64_t)nk * d.mt * 1024;
+  note_launch();
+  tc_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dHt, d.hi, d.ncells, d.ne, d.mt, nk);
+  return cudaGetLastError();
+}
+
+void tc_free(TcCellData& d) {
+  if (d.hi) cudaFree(d.hi);
+  d = TcCellData();
+}
+
+// ----------------------------------------------------------------- cell kernel
+struct CellSmem {
+  int stages;
+  int a_bytes;   // per stage
+  int y_bytes;   // per stage (hi + lo)
+  int total;
+};
+
+__host__ __device__ inline CellSmem cell_smem(int mt, int split3) {
+  CellSmem c;
+  c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
+  c.y_bytes = CELL_BN * CELL_KC * 4 * 2;
+  const int stage = c.a_bytes + c.y_bytes;
+  int S = (110 * 1024) / stage;
+  S = S < 2 ? 2 : (S > 6 ? 6 : S);
+  c.stages = S;
+  c.total = S * stage + 1024;   // + barriers and slack
+  return c;
+}
+
+struct CellParams {
+  const float* A;          // packed cell matrices
+  const int32_t* cells;
+  const int32_t* dofmap;
+  const uint8_t* modes;
+  const float* Yin;
+  float* Yout;
+  const float* Yprev;
+  float* W;
+  const float* NL;
+  int64_t ld_in, ld_out, ld_prev, ld_w;
+  int ncol, ne, mt, nk, split3;
+  float alpha, beta, shift;
+};
+
+__global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.cells[blockIdx.y];
+  const int c0 = blockIdx.x * CELL_BN;
+  const int ncv = min(CELL_BN, P.ncol - c0);
+  const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;   // MMA N
+  const CellSmem L = cell_smem(P.mt, P.split3);
+  const int S = L.stages;
+  const int stage_bytes = L.a_bytes + L.y_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  // bars: fa[S] (tx), fy[S] (128 arrivals), em[S] (MMA commit), acc (1)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t sbase = smem_u32(smem);
+  auto fa = [&](int s) { return smem_u32(bars + s); };
+  auto fy = [&](int s) { return smem_u32(bars + S + s); };
+  auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
+  const uint32_t accb = smem_u32(bars + 3 * S);
+  const uint32_t tmem_cols = P.mt == 1 ? 64 : (P.mt == 2 ? 128 : 256);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(fa(s), 1);
+      mbar_init(fy(s), 128);
+      mbar_init(em(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(smem_u32(tmem_slot), tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nk = P.nk;
+  const int32_t* dm = P.dofmap + e * P.ne;
+  const uint8_t* md = P.modes + e * P.ne;
+
+  if (warp == 4) {
+    // ---------------- producer of the cell-matrix chunks (bulk async copies)
+    if (lane == 0) {
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * P.mt * 8192;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+          atomicExch(&g_tc_status, 1);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        mbar_arrive_expect_tx(fa(s), L.a_bytes);
+        bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes, fa(s));
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(128, bne);
+      bool ok = true;
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i % S;
+        ok = mbar_wait(fa(s), (i / S) & 1) && mbar_wait(fy(s), (i / S) & 1);
+        if (!ok || *(volatile int*)abort_flag) {
+          if (!ok) atomicExch(&g_tc_status, 2);
+          *(volatile int*)abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * stage_bytes;
+        const uint32_t sy = sa + L.a_bytes;
+        const uint64_t yhi = umma_desc(sy, 128, 256);
+        const uint64_t ylo = umma_desc(sy + CELL_BN * CELL_KC * 4, 128, 256);
+        for (int t = 0; t < P.mt; ++t) {
+          const uint32_t d = tmem + t * CELL_BN;
+          const uint64_t ahi = umma_desc(sa + t * 4096, 128, 256);
+          if (P.split3) {
+            const uint64_t alo = umma_desc(sa + P.mt * 4096 + t * 4096, 128, 256);
+            mma_tf32(d, alo, yhi, idesc, i > 0);
+            mma_tf32(d, ahi, ylo, idesc, 1);
+            mma_tf32(d, ahi, yhi, idesc, 1);
+          } else {
+            mma_tf32(d, ahi, yhi, idesc, i > 0);
+          }
+        }
+        umma_commit(em(s));
+      }
+      umma_commit(accb);   // arrives once all issued MMAs are done (also on abort)
+    }
+  } else {
+    // ---------------- warps 0-3: gather + split the cell block of Y
+    const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
+    const int kk = tid >> 4;          // node within the chunk (0..7)
+    const int j4 = (tid & 15) * 4;    // first of 4 columns
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S;
+      if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+        atomicExch(&g_tc_status, 3);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
+      float* yl = yh + CELL_BN * CELL_KC;
+      const int l = i * CELL_KC + kk;
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      const int g = l < P.ne ? dm[l] : -1;
+      if (g >= 0) {
+        const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + j4;
+        if (vec && j4 + 4 <= ncv) {
+          float4 q = __ldg(reinterpret_cast<const float4*>(src));
+          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+          for (int u = 0; u < 4; ++u)
+            if (j4 + u < ncv) v[u] = __ldg(src + u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = j4 + u;
+        const int o = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
+        const float h = tf32_rna(v[u]);
+        yh[o] = h;
+        yl[o] = tf32_rna(v[u] - h);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(fy(s));
+    }
+    // ---------------- epilogue: TMEM -> registers -> colour-mode update
+    const bool okacc = mbar_wait(accb, 0);
+    if (!okacc) {
+      atomicExch(&g_tc_status, 4);
+      *(volatile int*)abort_flag = 1;
+    }
+    tc_fence_after();
+    const bool run = okacc && !*(volatile int*)abort_flag;
+    for (int t = 0; t < P.mt; ++t) {
+      const int l = t * 128 + warp * 32 + lane;
+      const bool row_ok = run && l < P.ne;
+      const int g = row_ok ? dm[l] : -1;
+      const int mode = row_ok ? md[l] : MODE_SKIP;
+      for (int cb = 0; cb < bne; cb += 16) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CELL_BN + cb, acc);
+        tmem_wait_ld();
+        if (g < 0 || mode == MODE_SKIP) continue;
+        const int64_t gw = (int64_t)g * P.ld_w + c0 + cb;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int c = cb + u;
+          if (c >= ncv) break;
+          float vv = acc[u];
+          if (mode == MODE_STORE) {
+            P.W[gw + u] = vv;
+          } else if (mode == MODE_ACCUM) {
+            P.W[gw + u] += vv;
+          } else {
+            if (mode == MODE_FINAL) vv += P.W[gw + u];
+            if (P.NL) vv += P.NL[gw + u];
+            const float y = P.Yin[(int64_t)g * P.ld_in + c0 + c];
+            float out = P.alpha * (vv - P.shift * y);
+            if (P.Yprev) out = fmaf(P.beta, P.Yprev[(int64_t)g * P.ld_prev + c0 + c], out);
+            P.Yout[(int64_t)g * P.ld_out + c0 + c] = out;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) tmem_dealloc(tmem, tmem_cols);
+}
+
+cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_t s) {
+  if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
+  if (!d.hi) return cudaErrorInvalidValue;
+  CellParams P;
+  P.A = d.hi;
+  P.cells = a.cells;
+  P.dofmap = a.dofmap;
+  P.modes = a.modes;
+  P.Yin = a.Yin;
+  P.Yout = a.Yout;
+  P.Yprev = a.Yprev;
+  P.W = a.W;
+  P.NL = a.NL;
+  P.ld_in = a.ld_in;
+  P.ld_out = a.ld_out;
+  P.ld_prev = a.ld_prev;
+  P.ld_w = a.ld_w;
+  P.ncol = a.ncol;
+  P.ne = d.ne;
+  P.mt = d.mt;
+  P.nk = d.kt / CELL_KC;
+  P.split3 = a.split3;
+  P.alpha = a.alpha;
+  P.beta = a.beta;
+  P.shift = a.shift;
+  const CellSmem L = cell_smem(d.mt, a.split3);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  dim3 grid((a.ncol + CELL_BN - 1) / CELL_BN, (unsigned)a.ncells);
+  note_launch();
+  tc_cell_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
+  return cudaGetLastError();
+}
+
+int tc_read_status(cudaStream_t s) {
+  int v = 0;
+  cudaMemcpyFromSymbolAsync(&v, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (v) {
+    int z = 0;
+    cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  return v;
+}
+
+// ----------------------------------------------------------------- Gram (A^T B)
+// Output tile 128 x 128 of C = A^T B (rows i of C <-> columns of A, columns j
+// <-> columns of B); K = unknowns, split over grid.z.  Operands are loaded by
+// warps 0-3, split into TF32 hi/lo and stored transposed (K-major) in shared
+// memory; warp 4 issues the MMAs.  Tiles strictly above the diagonal are
+// skipped when `lower`.  Partial tiles (binary64) are reduced in fixed order.
+constexpr int GR_T = 128, GR_KC = 16, GR_THREADS = 160;
+
+__host__ __device__ inline int gram_stage_bytes(int same) {
+  return (same ? 1 : 2) * GR_T * GR_KC * 4 * 2;   // operands x (hi + lo)
+}
+
+struct GramParams {
+  const float* A;
+  const float* B;
+  int64_t lda, ldb, M;
+  int n1, n2, lower, split3;
+  int64_t rows_per_split;
+  double* partial;
+};
+
+__device__ __forceinline__ int gr_off(int n, int k) {   // floats, 128 rows x 16 K, SBO 512 B
+  return (n >> 3) * 128 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+}
+
+__global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int ti = blockIdx.x, tj = blockIdx.y, z = blockIdx.z;
+  if (P.lower && ti < tj) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool same = (P.A == P.B) && (P.lda == P.ldb) && ti == tj;
+  const int SB = gram_stage_bytes(same);
+  const int S = 3;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * gram_stage_bytes(0));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto emp = [&](int s) { return smem_u32(bars + S + s); };
+  const uint32_t accb = smem_u32(bars + 2 * S);
+  const int64_t r0 = (int64_t)z * P.rows_per_split;
+  const int64_t r1 = min(P.M, r0 + P.rows_per_split);
+  const int nk = (int)((r1 - r0 + GR_KC - 1) / GR_KC);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 128);
+      mbar_init(emp(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 4) {
+    tmem_alloc(smem_u32(tmem_slot), 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc = idesc_tf32(128, 128);
+      bool ok = true;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (!mbar_wait(full(s), (i / S) & 1) || *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 5);
+          *(volatile int*)abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * SB;
+        const uint32_t sb = same ? sa : sa + GR_T * GR_KC * 8;
+        for (int j = 0; j < GR_KC / 8; ++j) {
+          const uint64_t ah = umma_desc(sa + j * 256, 128, 512);
+          const uint64_t al = umma_desc(sa + GR_T * GR_KC * 4 + j * 256, 128, 512);
+          const uint64_t bh = umma_desc(sb + j * 256, 128, 512);
+          const uint64_t bl = umma_desc(sb + GR_T * GR_KC * 4 + j * 256, 128, 512);
+          const uint32_t first = (i > 0 || j > 0);
+          if (P.split3) {
+            mma_tf32(tmem, al, bh, idesc, first);
+            mma_tf32(tmem, ah, bl, idesc, 1);
+            mma_tf32(tmem, ah, bh, idesc, 1);
+          } else {
+            mma_tf32(tmem, ah, bh, idesc, first);
+          }
+        }
+        umma_commit(emp(s));
+      }
+      (void)ok;
+      umma_commit(accb);
+    }
+  } else {
+    // warps 0-3: load rows r of A[:, ti*128 ..] and B[:, tj*128 ..], split, store K-major
+    const int cq = (tid & 31) * 4;    // 4 columns
+    const int rr = tid >> 5;          // row lane 0..3
+    const int ia = ti * GR_T, jb = tj * GR_T;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S;
+      if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
+        atomicExch(&g_tc_status, 6);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      float* sh = reinterpret_cast<float*>(smem + s * SB);
+      for (int op = 0; op < (same ? 1 : 2); ++op) {
+        const float* X = op == 0 ? P.A : P.B;
+        const int64_t ld = op == 0 ? P.lda : P.ldb;
+        const int nmax = op == 0 ? P.n1 : P.n2;
+        const int cbase = op == 0 ? ia : jb;
+        float* hi = sh + op * GR_T * GR_KC * 2;
+        float* lo = hi + GR_T * GR_KC;
+        for (int k = rr; k < GR_KC; k += 4) {
+          const int64_t row = r0 + (int64_t)i * GR_KC + k;
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int col = cbase + cq + u;
+            v[u] = (row < r1 && col < nmax) ? __ldg(X + row * ld + col) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int o = gr_off(cq + u, k);
+            const float h = tf32_rna(v[u]);
+            hi[o] = h;
+            lo[o] = tf32_rna(v[u] - h);
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(full(s));
+    }
+    bool okacc = true;
+    if (nk > 0) {
+      okacc = mbar_wait(accb, 0);
+      if (!okacc) atomicExch(&g_tc_status, 7);
+    }
+    tc_fence_after();
+    // epilogue: row i = ti*128 + warp*32 + lane, columns tj*128 + c
+    const int i = ti * GR_T + warp * 32 + lane;
+    double* Pz = P.partial + (int64_t)z * P.n1 * P.n2;
+    for (int cb = 0; cb < 128; cb += 16) {
+      float acc[16];
+      if (nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+        tmem_wait_ld();
+      } else {
+        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      }
+      if (i >= P.n1 || !okacc) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int j = tj * GR_T + cb + u;
+        if (j < P.n2) Pz[i + (int64_t)j * P.n1] = (double)acc[u];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) tmem_dealloc(tmem, 128);
+}
+
+__global__ void tc_gram_reduce_kernel(const double* __restrict__ partial, int nsplit, int n1, int n2,
+                                      double* __restrict__ C, int64_t ldc, int lower) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n1 * n2) return;
+  const int i = (int)(idx % n1), j = (int)(idx / n1);
+  if (lower && (i / GR_T) < (j / GR_T)) return;
+  double s = 0.0;
+  for (int zz = 0; zz < nsplit; ++zz) s += partial[(int64_t)zz * n1 * n2 + idx];
+  C[i + (int64_t)j * ldc] = s;
+}
+
+// Binary64 diagonal blocks: C[i, j] = sum_r A[r, i] B[r, j] for i / bd == j / bd
+// (i, j < min(n1, n2); bd divides 32).  Block: 8 row lanes x 32 columns; a
+// thread owns column i and accumulates its bd block partners, whose B values
+// come from neighbouring lanes by warp shuffles.  Products of binary32 values
+// are exact in binary64; partial sums over row chunks are reduced in fixed order.
+__global__ void diag_gram_fp64_kernel(const float* __restrict__ A, int64_t lda,
+                                      const float* __restrict__ B, int64_t ldb, int64_t M, int nd,
+                                      int bd, int64_t rows_per_chunk, double* __restrict__ part) {
+  const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(M, r0 + rows_per_chunk);
+  const int jb = lane / bd * bd;            // first lane of this column's block
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  for (int64_t r = r0 + rl; r < r1; r += 8) {
+    const float a = i < nd ? A[r * lda + i] : 0.f;
+    const float b = i < nd ? B[r * ldb + i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      if (q < bd) {
+        const float bq = __shfl_sync(0xffffffffu, b, jb + q);
+        acc[q] = fma((double)a, (double)bq, acc[q]);
+      }
+    }
+  }
+  __shared__ double red[8][32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    if (q >= bd) break;
+    red[rl][lane] = acc[q];
+    __syncthreads();
+    if (rl == 0 && i < nd) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w][lane];
+      part[((int64_t)blockIdx.y * gridDim.x * 32 + i) * bd + q] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void diag_reduce_kernel(const double* __restrict__ part, int nchunk, int ncols, int nd,
+                                   int bd, double* __restrict__ C, int64_t ldc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nd * bd) return;
+  const int i = (int)(idx / bd), q = (int)(idx % bd);
+  const int j = i / bd * bd + q;
+  if (j >= nd) return;
+  double s = 0.0;
+  for (int zz = 0; zz < nchunk; ++zz) s += part[((int64_t)zz * ncols + i) * bd + q];
+  C[i + (int64_t)j * ldc] = s;
+}
+
+size_t tc_gram_partial_bytes(int64_t M, int n1, int n2) {
+  (void)M;
+  return (size_t)8 * 8 * n1 * n2 + (size_t)64 * 1024 * 1024;
+}
+
+cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
+                          int n1, int n2, double* C, int64_t ldc, int lower, int diag_block,
+                          int split3, void* partial, size_t partial_bytes, cudaStream_t s) {
+  if (n1 == 0 || n2 == 0) return cudaSuccess;
+  const int t1 = (n1 + GR_T - 1) / GR_T, t2 = (n2 + GR_T - 1) / GR_T;
+  const int64_t tiles = lower ? (int64_t)t1 * (t1 + 1) / 2 : (int64_t)t1 * t2;
+  const size_t diag_bytes = (size_t)64 * 1024 * 1024;
+  int64_t max_split = (int64_t)((partial_bytes - diag_bytes) / (sizeof(double) * (size_t)n1 * n2));
+  int64_t want = (2 * 152 + tiles - 1) / tiles;
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(std::min(want, max_split), (M + 1023) / 1024));
+  int64_t rps = ((M + nsplit - 1) / nsplit + GR_KC - 1) / GR_KC * GR_KC;
+  nsplit = (M + rps - 1) / rps;
+  GramParams P{A, B, lda, ldb, M, n1, n2, lower, split3, rps, (double*)partial};
+  const int smem = 3 * gram_stage_bytes(0) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  note_launch();
+  tc_gram_kernel<<<dim3(t1, t2, (unsigned)nsplit), GR_THREADS, smem, s>>>(P);
+  const int64_t tot = (int64_t)n1 * n2;
+  note_launch();
+  tc_gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((double*)partial, (int)nsplit,
+                                                                      n1, n2, C, ldc, lower);
+  // binary64 diagonal blocks overwrite the tensor-core values there
+  if (diag_block > 0) {
+    int bd = 1;
+    while (bd * 2 <= std::min(diag_block, 32)) bd *= 2;
+    const int nd = std::min(n1, n2);
+    const int ntile = (nd + 31) / 32;
+    double* dpart = (double*)((char*)partial + (partial_bytes - diag_bytes));
+    int64_t nchunk = std::max<int64_t>(1, (4 * 152 + ntile - 1) / ntile);
+    nchunk = std::min<int64_t>(nchunk, (int64_t)(diag_bytes / (8 * (size_t)ntile * 32 * bd)));
+    nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, (M + 63) / 64));
+    int64_t rpc = (M + nchunk - 1) / nchunk;
+    nchunk = (M + rpc - 1) / rpc;
+    note_launch();
+    diag_gram_fp64_kernel<<<dim3(ntile, (unsigned)nchunk), 256, 0, s>>>(A, lda, B, ldb, M, nd, bd, rpc,
+                                                                          dpart);
+    const int64_t tot2 = (int64_t)nd * bd;
+    note_launch();
+    diag_reduce_kernel<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(dpart, (int)nchunk, ntile * 32, nd,
+                                                                       bd, C, ldc);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- tall GEMM (X U)
+// C (M x n2) = A (M x n1, binary32) U (n1 x n2, binary64).  Tile: 128 rows x
+// 128 columns; K-loop over n1 in chunks of 16.  U is split into TF32 hi / lo
+// once per call into a K-major chunked layout (tc_splitu_kernel); diagonal
+// blocks of U are excluded from the tensor-core product and added in binary64
+// in the epilogue (the paper's Psi L^{-1}_d term).
+constexpr int TG_T = 128, TG_KC = 16, TG_THREADS = 160;
+
+// U split layout: [col tile][k chunk][hi|lo][128 cols x 16 K in gr_off layout]
+__global__ void tc_splitu_kernel(const double* __restrict__ U, int64_t ldu, int n1, int n2, int upper,
+                                 int trans, int bd, float* __restrict__ out) {
+  const int nkc = (n1 + TG_KC - 1) / TG_KC;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ntile = (n2 + TG_T - 1) / TG_T;
+  if (idx >= (int64_t)ntile * nkc * TG_T * TG_KC) return;
+  const int tile = (int)(idx / ((int64_t)nkc * TG_T * TG_KC));
+  int rem = (int)(idx - (int64_t)tile * nkc * TG_T * TG_KC);
+  const int kc = rem / (TG_T * TG_KC);
+  rem -= kc * TG_T * TG_KC;
+  const int n = rem / TG_KC, k = rem % TG_KC;
+  const int col = tile * TG_T + n, kk = kc * TG_KC + k;
+  double v = 0.0;
+  if (col < n2 && kk < n1 && (!upper || kk <= col) && !(bd > 0 && kk / bd == col / bd))
+    v = trans ? U[col + (int64_t)kk * ldu] : U[kk + (int64_t)col * ldu];
+  const float h = tf32_rna((float)v);
+  const float l = tf32_rna((float)(v - (double)h));
+  float* base = out + ((int64_t)tile * nkc + kc) * 2 * TG_T * TG_KC;
+  base[gr_off(n, k)] = h;
+  base[TG_T * TG_KC + gr_off(n, k)] = l;
+}
+
+struct TallParams {
+  const float* A;
+  int64_t lda, M;
+  const float* Us;       // split U
+  const double* U;       // binary64 U for the diagonal blocks
+  int64_t ldu;
+  int n1, n2, upper, trans, bd, split3;
+  float* C;
+  int64_t ldc;
+};
+
+__global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rb = (int64_t)blockIdx.x * TG_T;
+  const int tj = blockIdx.y;
+  const int nkc_all = (P.n1 + TG_KC - 1) / TG_KC;
+  int kend = P.n1;
+  if (P.upper) kend = min(P.n1, (tj + 1) * TG_T);
+  const int nk = (kend + TG_KC - 1) / TG_KC;
+  const int SB = 2 * TG_T * TG_KC * 4 * 2;   // A (hi, lo) + U (hi, lo)
+  const int S = 3;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * SB);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto emp = [&](int s) { return smem_u32(bars + S + s); };
+  const uint32_t accb = smem_u32(bars + 2 * S);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 128);
+      mbar_init(emp(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 4) {
+    tmem_alloc(smem_u32(tmem_slot), 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ncv = min(TG_T, P.n2 - tj * TG_T);
+  const int bne = (ncv + 15) / 16 * 16;
+
+  if (warp == 4) {
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc = idesc_tf32(128, bne);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (!mbar_wait(full(s), (i / S) & 1) || *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 8);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * SB;
+        const uint32_t su = sa + TG_T * TG_KC * 8;
+        for (int j = 0; j < TG_KC / 8; ++j) {
+          const uint64_t ah = umma_desc(sa + j * 256, 128, 512);
+          const uint64_t al = umma_desc(sa + TG_T * TG_KC * 4 + j * 256, 128, 512);
+          const uint64_t uh = umma_desc(su + j * 256, 128, 512);
+          const uint64_t ul = umma_desc(su + TG_T * TG_KC * 4 + j * 256, 128, 512);
+          const uint32_t acc = (i > 0 || j > 0);
+          if (P.split3) {
+            mma_tf32(tmem, al, uh, idesc, acc);
+            mma_tf32(tmem, ah, ul, idesc, 1);
+            mma_tf32(tmem, ah, uh, idesc, 1);
+          } else {
+            mma_tf32(tmem, ah, uh, idesc, acc);
+          }
+        }
+        umma_commit(emp(s));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % S;
+      if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
+        atomicExch(&g_tc_status, 9);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      float* sa = reinterpret_cast<float*>(smem + s * SB);
+      float* ahi = sa;
+      float* alo = sa + TG_T * TG_KC;
+      // A rows rb..rb+127, K columns i*16 .. i*16+15: 128 x 16 floats, 16 per thread
+      for (int q = tid; q < TG_T * 4; q += 128) {
+        const int r = q >> 2, k4 = (q & 3) * 4;
+        const int64_t row = rb + r;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (row < P.M) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int kk = i * TG_KC + k4 + u;
+            if (kk < P.n1) v[u] = __ldg(P.A + row * P.lda + kk);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int o = gr_off(r, k4 + u);
+          const float h = tf32_rna(v[u]);
+          ahi[o] = h;
+          alo[o] = tf32_rna(v[u] - h);
+        }
+      }
+      // U chunk: contiguous 2 x 8 KB block of the pre-split layout
+      const float4* src = reinterpret_cast<const float4*>(
+          P.Us + ((int64_t)tj * nkc_all + i) * 2 * TG_T * TG_KC);
+      float4* dst = reinterpret_cast<float4*>(sa + 2 * TG_T * TG_KC);
+      for (int q = tid; q < TG_T * TG_KC * 2 / 4; q += 128) dst[q] = __ldg(src + q);
+      fence_proxy_async_smem();
+      mbar_arrive(full(s));
+    }
+    bool okacc = true;
+    if (nk > 0) {
+      okacc = mbar_wait(accb, 0);
+      if (!okacc) atomicExch(&g_tc_status, 10);
+    }
+    tc_fence_after();
+    const int64_t row = rb + warp * 32 + lane;
+    for (int cb = 0; cb < bne; cb += 16) {
+      float acc[16];
+      if (nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+        tmem_wait_ld();
+      } else {
+        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      }
+      if (row >= P.M || !okacc) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int col = tj * TG_T + cb + u;
+        if (cb + u >= ncv) break;
+        double v = (double)acc[u];
+        if (P.bd > 0) {   // binary64 diagonal block of U
+          const int k0 = (col / P.bd) * P.bd;
+          const int k1 = min(P.n1, k0 + P.bd);
+          for (int kk = k0; kk < k1; ++kk) {
+            if (P.upper && kk > col) break;
+            const double u_ = P.trans ? P.U[col + (int64_t)kk * P.ldu] : P.U[kk + (int64_t)col * P.ldu];
+            v = fma((double)P.A[row * P.lda + kk], u_, v);
+          }
+        }
+        P.C[row * P.ldc + col] = (float)v;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) tmem_dealloc(tmem, 128);
+}
+
+cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int64_t ldu, int64_t M,
+                              int n1, int n2, float* C, int64_t ldc, int upper, int trans,
+                              int diag_block, int split3, void* work, cudaStream_t s) {
+  if (M == 0 || n2 == 0) return cudaSuccess;
+  const int nkc = (n1 + TG_KC - 1) / TG_KC;
+  const int ntile = (n2 + TG_T - 1) / TG_T;
+  float* Us = (float*)work;
+  int bd = 0;
+  if (diag_block > 0) {
+    bd = 1;
+    while (bd * 2 <= std::min(diag_block, 32)) bd *= 2;
+  }
+  const int64_t tot = (int64_t)ntile * nkc * TG_T * TG_KC;
+  note_launch();
+  tc_splitu_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans, bd, Us);
+  TallParams P{A, lda, M, Us, U, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
+  const int smem = 3 * (2 * TG_T * TG_KC * 4 * 2) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_tall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  dim3 grid((unsigned)((M + TG_T - 1) / TG_T), ntile);
+  note_launch();
+  tc_tall_kernel<<<grid, TG_THREADS, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+size_t tc_tallgemm_work_bytes(int n1, int n2) {
+  const int nkc = (n1 + TG_KC - 1) / TG_KC;
+  const int ntile = (n2 + TG_T - 1) / TG_T;
+  return (size_t)ntile * nkc * 2 * TG_T * TG_KC * 4 + 256;
+}
+
+// ----------------------------------------------------------------- nonlocal (binary32)
+__global__ void nl_project32_kernel(const int64_t* __restrict__ site_ptr,
+                                    const int32_t* __restrict__ site_dof,
+                                    const float* __restrict__ site_c, const float* __restrict__ Y,
+                                    int64_t ldy, int ncol, float* __restrict__ Z) {
+  const int s = blockIdx.x;
+  const int c = blockIdx.y * 32 + threadIdx.x % 32;
+  const int w = threadIdx.x / 32;  // 8 warps
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (c < ncol) {
+    for (int64_t e = site_ptr[s] + w; e < site_ptr[s + 1]; e += 8) {
+      const float y = Y[(int64_t)site_dof[e] * ldy + c];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] = fmaf(site_c[4 * e + t], y, acc[t]);
+    }
+  }
+  __shared__ float red[8][4][32];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) red[w][t][threadIdx.x % 32] = acc[t];
+  __syncthreads();
+  if (w == 0 && c < ncol) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float v = 0.f;
+      for (int q = 0; q < 8; ++q) v += red[q][t][threadIdx.x];
+      Z[(int64_t)(4 * s + t) * ncol + c] = v;
+    }
+  }
+}
+
+__global__ void nl_expand32_kernel(const int64_t* __restrict__ dof_ptr,
+                                   const int32_t* __restrict__ dof_site,
+                                   const float* __restrict__ dof_c, int64_t M,
+                                   const float* __restrict__ Z, int ncol, float* __restrict__ NL,
+                                   int64_t ldn) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * ncol) return;
+  const int64_t j = idx / ncol;
+  const int c = (int)(idx - j * ncol);
+  float v = 0.f;
+  for (int64_t e = dof_ptr[j]; e < dof_ptr[j + 1]; ++e) {
+    const int64_t s = dof_site[e];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v = fmaf(dof_c[4 * e + t], Z[(4 * s + t) * ncol + c], v);
+  }
+  NL[j * ldn + c] = v;
+}
+
+cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, const float* site_c,
+                          int nsite, const float* Y, int64_t ldy, int ncol, float* Z, cudaStream_t s) {
+  if (nsite == 0 || ncol == 0) return cudaSuccess;
+  note_launch();
+  nl_project32_kernel<<<dim3(nsite, (ncol + 31) / 32), 256, 0, s>>>(site_ptr, site_dof, site_c, Y, ldy,
+                                                                     ncol, Z);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_nl_expand(const int64_t* dof_ptr, const int32_t* dof_site, const float* dof_c, int64_t M,
+                         const float* Z, int ncol, float* NL, int64_t ldn, cudaStream_t s) {
+  const int64_t tot = M * ncol;
+  if (tot == 0) return cudaSuccess;
+  note_launch();
+  nl_expand32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dof_ptr, dof_site, dof_c, M, Z, ncol,
+                                                                    NL, ldn);
+  return cudaGetLastError();
+}
 
 }  // namespace chfsi

@@ -38,6 +38,12 @@ struct TcCellArgs {
 
 cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
                      cudaStream_t s, int64_t* dev_bytes);
+// Split the binary64 device cell matrices into the TF32 hi / lo operand layout.
+cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                int64_t* dev_bytes);
+// Read and clear the device status word of the bounded waits (0: no timeout).
+int tc_read_status(cudaStream_t s);
+size_t tc_tallgemm_work_bytes(int n1, int n2);
 void tc_free(TcCellData& d);
 cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_t s);
 size_t tc_gram_partial_bytes(int64_t M, int n1, int n2);

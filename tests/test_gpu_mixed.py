@@ -1,0 +1,127 @@
+"""Mixed-precision (tcgen05 TF32) path against the FP64 oracle.
+
+Inputs are the binary32 roundings of the seeded blocks; the oracle runs in
+binary64 on the same rounded values.  Tolerances follow from the arithmetic:
+3xTF32 products carry ~2^-22 relative error, but the cell sums accumulate
+n_e <= 512 products in binary32 whose magnitudes exceed the result by the
+cancellation factor of the kinetic matrix (~10-40 here), so one operator
+application is checked at 1e-5 relative Frobenius and a degree-20 filter at
+1e-4; the ChFSI eigenvalues must meet the method statement's 1e-7 Ha.
+1xTF32 keeps only ~2^-12, checked at 2e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1903_10959_gb300 import workloads as W
+from oracle import chfsi as och
+
+from gpu_util import gpu_context, oracle_problem, rel_fro
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _sys(kind):
+    if kind == "c1":
+        return W.small_periodic()
+    if kind == "p6":
+        return W.small_periodic(seed=21, ncell=3, p=6, L=6.0, n_wells=3, n_want=12)
+    if kind == "p7dir":
+        s = W.small_periodic(seed=22, ncell=2, p=7, L=7.0, n_wells=3, n_want=10)
+        s.periodic = False
+        return s
+    if kind == "nonlocal":
+        s = W.small_periodic(seed=14, ncell=4, p=3, L=10.0, n_wells=6, n_want=16)
+        s.nl_centres = s.centres[:3].copy()
+        s.nl_h = 0.5 + np.arange(12).reshape(3, 4) / 8.0
+        return s
+    raise ValueError(kind)
+
+
+@pytest.fixture(scope="module", params=["c1", "p6", "p7dir", "nonlocal"])
+def case(request):
+    s = _sys(request.param)
+    prob = oracle_problem(s)
+    ctx = gpu_context(s)
+    yield s, prob, ctx
+    ctx.destroy()
+
+
+def _x32(seed, m, n):
+    return W.start_block(seed, m, n).astype(np.float32)
+
+
+@pytest.mark.parametrize("ncol,prec,tol", [(1, "tf32x3", 1e-5), (13, "tf32x3", 1e-5),
+                                           (64, "tf32x3", 1e-5), (150, "tf32x3", 1e-5),
+                                           (70, "tf32", 2e-3)])
+def test_mixed_apply(case, ncol, prec, tol):
+    s, prob, ctx = case
+    X0 = _x32(3, prob.ndofs, ncol)
+    X = torch.tensor(X0, device=DEV)
+    Y = torch.empty_like(X)
+    ctx.set_blocking(200, 8)
+    ctx.apply(X, Y, prec=prec)
+    ref = prob.apply_Htilde(X0.astype(np.float64))
+    assert rel_fro(Y.cpu().numpy().astype(np.float64), ref) < tol
+
+
+def test_mixed_filter(case):
+    s, prob, ctx = case
+    X0 = _x32(4, prob.ndofs, 45)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(4, prob.ndofs), 15)
+    a, a0 = 0.2 * b, -3.0
+    ref = och.chebyshev_filter(prob.apply_Htilde, X0.astype(np.float64), 20, a, b, a0)
+    X = torch.tensor(X0, device=DEV)
+    ctx.set_blocking(32, 8)
+    ctx.filter(X, 20, a, b, a0, prec="mixed")
+    assert rel_fro(X.cpu().numpy().astype(np.float64), ref) < 1e-4
+
+
+@pytest.mark.parametrize("bd", [1, 8, 32])
+def test_mixed_cholgs(case, bd):
+    s, prob, ctx = case
+    n = 40
+    X0 = _x32(7, prob.ndofs, n)
+    X = torch.tensor(X0, device=DEV)
+    ctx.set_blocking(200, bd)
+    ctx.cholgs(X, prec="mixed")
+    Q = X.cpu().numpy().astype(np.float64)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 2e-5
+    assert rel_fro(Q, och.cholgs(X0.astype(np.float64))) < 2e-5
+
+
+def test_mixed_rayleigh_ritz(case):
+    s, prob, ctx = case
+    X0 = och.cholgs(W.start_block(8, prob.ndofs, 30)).astype(np.float32)
+    D_ref, _ = och.rayleigh_ritz(prob.apply_Htilde, X0.astype(np.float64))
+    X = torch.tensor(X0, device=DEV)
+    ctx.set_blocking(16, 8)
+    D = ctx.rayleigh_ritz(X, prec="mixed")
+    scale = max(1.0, np.abs(D_ref).max())
+    assert np.abs(D - D_ref).max() < 1e-5 * scale
+
+
+def test_mixed_solve_meets_eigenvalue_tolerance(case):
+    """ChFSI in mixed precision vs the FP64 oracle run: <= 1e-7 Ha per eigenvalue."""
+    s, prob, ctx = case
+    n = s.n_sub
+    iters = 12
+    X0 = W.start_block(s.seed, prob.ndofs, n)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(s.seed, prob.ndofs), 20)
+    D_ref, _ = och.chfsi(prob.apply_Htilde, X0, s.degree, iters, b)
+    X = torch.tensor(X0.astype(np.float32), device=DEV)
+    ctx.set_blocking(200, 8)
+    D, done = ctx.solve(X, iters, s.degree, b, prec="mixed")
+    nw = s.n_want
+    assert np.abs(D[:nw] - D_ref[:nw]).max() < 1e-7
+
+
+def test_mixed_tf32_runs(case):
+    s, prob, ctx = case
+    X0 = W.start_block(s.seed, prob.ndofs, s.n_sub)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(s.seed, prob.ndofs), 20)
+    D_ref, _ = och.chfsi(prob.apply_Htilde, X0, s.degree, 6, b)
+    X = torch.tensor(X0.astype(np.float32), device=DEV)
+    D, _ = ctx.solve(X, 6, s.degree, b, prec="tf32")
+    assert np.abs(D[:s.n_want] - D_ref[:s.n_want]).max() < 1e-3
