@@ -126,6 +126,27 @@ chfsi_status chfsi_fill_uniform(chfsi_ctx* ctx, void* X, int64_t ldx, int64_t ro
 chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy,
                          int ncol, chfsi_precision prec);
 
+/* Y = H~ X in binary64 like chfsi_apply, but without allocating any device
+ * memory.  The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc from inside their step -- for example host frameworks whose
+ * own pool allocator owns the GPU's memory (a library allocation would fail
+ * or escape their accounting), or latency-critical loops where cudaMalloc /
+ * cudaFree would synchronise the device.  The caller passes X and Y (device,
+ * M x ncol, not overlapping); the assembly scratch (the partial-sum buffer,
+ * plus the projector buffers when projectors are set) lives in one fixed
+ * file-scope device array of 64 MiB that every GPU loading the library keeps
+ * until the process exits.  Limit: M * ncol * 8 bytes (twice that plus
+ * 4 * nsite * ncol * 8 with projectors) must fit in 64 MiB; larger requests
+ * return CHFSI_ERR_ARG with the sizes in chfsi_last_error, so split the
+ * columns over several calls.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and nothing in it needs to
+ * start at zero (each call writes every scratch entry it reads); calls whose
+ * work overlaps on the GPU (other streams, other contexts on the device)
+ * race on it, so serialise them.  Asynchronous on the context's stream. */
+chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, double* Y,
+                                 int64_t ldy, int ncol);
+
 /* Degree-m Chebyshev filter (Eq. chebFilter) in the scaled form of Zhou &
  * Saad, in place on X (M x ncol): X <- T_m((H~ - c)/e) X / T_m((a0 - c)/e),
  * c = (a + b)/2, e = (b - a)/2; [a, b] is the damped interval, a0 < a the

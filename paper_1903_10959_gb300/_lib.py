@@ -52,6 +52,7 @@ _SIGS = {
     "chfsi_set_blocking": (C.c_int, [_vp, C.c_int, C.c_int]),
     "chfsi_fill_uniform": (C.c_int, [_vp, _vp, _i64, _i64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]),
     "chfsi_apply": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int, C.c_int]),
+    "chfsi_apply_noalloc": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int]),
     "chfsi_filter": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_double, C.c_double,
                                C.c_double, C.c_int]),
     "chfsi_cholgs": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
@@ -204,6 +205,13 @@ class Context:
         px, ldx, n = _dev(X, pr)
         py, ldy, _ = _dev(Y, pr)
         self._check(self._lib.chfsi_apply(self._h, px, ldx, py, ldy, n, pr))
+
+    def apply_noalloc(self, X, Y):
+        """Y = H~ X in binary64 through chfsi_apply_noalloc (no device allocation:
+        the assembly scratch is the library's fixed 64 MiB device array)."""
+        px, ldx, n = _dev(X, FP64)
+        py, ldy, _ = _dev(Y, FP64)
+        self._check(self._lib.chfsi_apply_noalloc(self._h, px, ldx, py, ldy, n))
 
     def filter(self, X, degree, a, b, a0, prec="fp64"):
         pr = _prec(prec)

@@ -16,6 +16,7 @@
 using namespace chfsi;
 
 #include <atomic>
+#include <mutex>
 namespace chfsi {
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -482,6 +483,38 @@ chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, ch
 
 }  // namespace
 
+// ================================================== apply without device allocation
+// Fixed device scratch for chfsi_apply_noalloc: the partial-sum buffer of the
+// colour-ordered assembly and, with projectors, the projected coefficients and
+// their expansion.  It is a file-scope device array, so every GPU that loads
+// the library holds these bytes until the process exits.
+constexpr size_t kNoallocScratchBytes = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};   // device address of the scratch, per device ordinal
+
+// Device address of the scratch on the current device.  The first call on a
+// device resolves it with cudaGetSymbolAddress (the array's host-side name is
+// only a stand-in and must never be handed to a kernel).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 // ===================================================================== C ABI
 extern "C" {
 
@@ -643,6 +676,54 @@ chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, in
   st = apply_blocks(ctx, prec, X, ldx, Y, ldy, ncol);
   if (st == CHFSI_OK) st = check_device_status(ctx, prec);
   return st;
+}
+
+chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, double* Y,
+                                 int64_t ldy, int ncol) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, ncol, CHFSI_FP64);
+  if (st != CHFSI_OK) return st;
+  if (ncol > 0 && (!Y || ldy < ncol)) return fail(ctx, CHFSI_ERR_ARG, "bad Y / ldy");
+  if (ncol == 0) return CHFSI_OK;
+  const HostMesh& m = ctx->mesh;
+  const int nsite = ctx->hproj.nsite;
+  const size_t w_bytes = (size_t)m.ndofs * ncol * sizeof(double);
+  const size_t z_bytes = (size_t)4 * nsite * ncol * sizeof(double);
+  const size_t need = w_bytes + (nsite > 0 ? w_bytes + z_bytes : 0);
+  if (need > kNoallocScratchBytes)
+    return fail(ctx, CHFSI_ERR_ARG,
+                "chfsi_apply_noalloc: needs " + std::to_string(need) + " bytes of scratch for " +
+                    std::to_string(ncol) + " columns, more than the fixed " +
+                    std::to_string(kNoallocScratchBytes) + " bytes; use fewer columns per call");
+  void* scratch = nullptr;
+  cudaError_t se = noalloc_scratch(&scratch);
+  if (se != cudaSuccess)
+    return fail(ctx, CHFSI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(se));
+  double* W = (double*)scratch;                       // written before read (MODE_STORE first)
+  double* NL = nsite > 0 ? W + (size_t)m.ndofs * ncol : nullptr;
+  double* Z = nsite > 0 ? NL + (size_t)m.ndofs * ncol : nullptr;
+  if (nsite > 0) {
+    CK(launch_nl_project_fp64(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c, nsite, X, ldx, ncol,
+                              Z, ctx->stream));
+    CK(launch_nl_expand_fp64(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c, m.ndofs, Z, ncol, NL,
+                             ncol, ctx->stream));
+  }
+  const int ncolour = (int)m.colour_offsets.size() - 1;
+  for (int c = 0; c < ncolour; ++c) {
+    CellLaunch L{};
+    L.Ht = ctx->d_Ht;
+    L.dofmap = ctx->d_dofmap;
+    L.modes = ctx->d_modes;
+    L.cells = ctx->d_cells + m.colour_offsets[c];
+    L.ncells_colour = m.colour_offsets[c + 1] - m.colour_offsets[c];
+    L.ne = m.ne;
+    L.ncol = ncol;
+    L.ld_in = ldx;
+    L.ld_out = ldy;
+    L.ld_prev = 0;
+    CK(launch_cell_fp64(L, X, Y, nullptr, W, NL, ncol, FilterStep{1.0, 0.0, 0.0}, ctx->stream));
+  }
+  return CHFSI_OK;
 }
 
 chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
