@@ -112,7 +112,8 @@ chfsi_status chfsi_build(chfsi_ctx* ctx);
 
 /* Column block size of the filter (Sec. 3.3.1 "B^f"; default 200 or ncol if
  * smaller) and diagonal block size of the mixed overlap/projection products
- * (default 8, a power of two <= 32).  Takes effect on the next call. */
+ * (default 1: the diagonal entries, as in the paper; a power of two <= 32).
+ * Takes effect on the next call. */
 chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block);
 
 /* Fill rows x ncol of X (device, leading dimension ldx) with the seeded

@@ -192,7 +192,7 @@ class Context:
     def build(self):
         self._check(self._lib.chfsi_build(self._h))
 
-    def set_blocking(self, filter_block=200, diag_block=8):
+    def set_blocking(self, filter_block=200, diag_block=1):
         self._check(self._lib.chfsi_set_blocking(self._h, int(filter_block), int(diag_block)))
 
     def fill_uniform(self, X, seed, stream=1, prec="fp64"):

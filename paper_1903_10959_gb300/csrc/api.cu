@@ -33,7 +33,7 @@ struct chfsi_ctx {
   bool built = false;
   chfsi_status latched = CHFSI_OK;
   std::string err;
-  int filter_block = 200, diag_block = 8;
+  int filter_block = 200, diag_block = 1;
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices

@@ -117,10 +117,10 @@ __host__ __device__ inline CellSmem cell_smem(int mt, int split3) {
   c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
   c.y_bytes = CELL_BN * CELL_KC * 4 * 2;
   const int stage = c.a_bytes + c.y_bytes;
-  int S = (110 * 1024) / stage;
+  int S = (110 * 1024 - 3072) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
   c.stages = S;
-  c.total = S * stage + 1024;   // + barriers and slack
+  c.total = S * stage + 3072;   // + barriers, the cell's dof map (<= 512) and modes
   return c;
 }
 
@@ -136,9 +136,15 @@ struct CellParams {
   const float* NL;
   int64_t ld_in, ld_out, ld_prev, ld_w;
   int ncol, ne, mt, nk, split3;
+  int cl;                  // thread-block cluster size along the column tiles (1, 2 or 4)
   float alpha, beta, shift;
 };
 
+// With cl > 1 the cl CTAs of one cell (consecutive column tiles) form a
+// cluster: the leader (rank 0) streams each cell-matrix chunk once and the
+// bulk copy is multicast into every member's stage buffer; each member's MMA
+// commit arrives on the empty barrier of every member, so a stage is reused
+// only after the whole cluster has consumed it.
 __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -150,21 +156,25 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) 
   const int S = L.stages;
   const int stage_bytes = L.a_bytes + L.y_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
-  // bars: fa[S] (tx), fy[S] (128 arrivals), em[S] (MMA commit), acc (1)
+  // bars: fa[S] (tx), fy[S] (32 arrivals: one gather warp), em[S] (MMA commit), acc (1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(smem + S * stage_bytes + 256);
+  uint8_t* md = reinterpret_cast<uint8_t*>(dm + 512);
   const uint32_t sbase = smem_u32(smem);
   auto fa = [&](int s) { return smem_u32(bars + s); };
   auto fy = [&](int s) { return smem_u32(bars + S + s); };
   auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
   const uint32_t accb = smem_u32(bars + 3 * S);
   const uint32_t tmem_cols = P.mt == 1 ? 64 : (P.mt == 2 ? 128 : 256);
+  const uint32_t crank = P.cl > 1 ? cluster_ctarank() : 0;
+  const uint16_t cmask = (uint16_t)((1u << P.cl) - 1u);
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(fa(s), 1);
-      mbar_init(fy(s), 128);
-      mbar_init(em(s), 1);
+      mbar_init(fy(s), 32);
+      mbar_init(em(s), P.cl);
     }
     mbar_init(accb, 1);
     *abort_flag = 0;
@@ -174,18 +184,23 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) 
     tmem_alloc(smem_u32(tmem_slot), tmem_cols);
     tmem_relinquish();
   }
+  for (int l = tid; l < P.ne; l += CELL_THREADS) {
+    dm[l] = P.dofmap[e * P.ne + l];
+    md[l] = P.modes[e * P.ne + l];
+  }
   tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  if (P.cl > 1) cluster_sync();   // every member's barriers exist before the first multicast
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int nk = P.nk;
-  const int32_t* dm = P.dofmap + e * P.ne;
-  const uint8_t* md = P.modes + e * P.ne;
 
   if (warp == 4) {
     // ---------------- producer of the cell-matrix chunks (bulk async copies)
     if (lane == 0) {
       const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * P.mt * 8192;
+      int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
         if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
@@ -195,7 +210,19 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) 
         }
         if (*(volatile int*)abort_flag) break;
         mbar_arrive_expect_tx(fa(s), L.a_bytes);
-        bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes, fa(s));
+        if (P.cl == 1)
+          bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes, fa(s));
+        else if (crank == 0)
+          bulk_g2s_multicast(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes,
+                             fa(s), cmask);
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag) {   // let the copies still in flight land before exit
+        for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(fa(i % S), (i / S) & 1);
+      } else if (P.cl > 1) {
+        // the peers' commits of the last chunks arrive on this CTA's empty
+        // barriers: see them all before the CTA may leave the cluster
+        for (int i = max(0, nk - S); i < nk; ++i) mbar_wait(em(i % S), (i / S) & 1);
       }
     }
   } else if (warp == 5) {
@@ -229,17 +256,45 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) 
             mma_tf32(d, ahi, yhi, idesc, i > 0);
           }
         }
-        umma_commit(em(s));
+        if (P.cl > 1) umma_commit_multicast(em(s), cmask);
+        else umma_commit(em(s));
       }
       umma_commit(accb);   // arrives once all issued MMAs are done (also on abort)
     }
   } else {
     // ---------------- warps 0-3: gather + split the cell block of Y
+    // Warp w produces the chunks i = w, w + G, ... (G = min(4, S)) so up to four
+    // chunks are in flight per CTA.  Lane (q, cq) loads 4 nodes (4q..4q+3) x 4 columns (4cq..4cq+3)
+    // with 16-byte loads and writes, per column, the 4 consecutive K values as
+    // one 16-byte store of hi and one of lo (K-major core-matrix layout).
+    // hi = tf32(x) (nearest); lo = x - hi is exact and the MMA truncates it.
+    // A warp waits on the empty barrier of chunk i - S after having seen chunk
+    // i - G - S consumed on its previous turn; a parity wait is only sound when
+    // the barrier is at most one phase behind, i.e. when G <= S.
     const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
-    const int kk = tid >> 4;          // node within the chunk (0..7)
-    const int j4 = (tid & 15) * 4;    // first of 4 columns
-    for (int i = 0; i < nk; ++i) {
+    const int q = lane >> 4;           // node quad within the chunk (0..1)
+    const int cq = (lane & 15) * 4;    // first of 4 columns
+    const int G = S < 4 ? S : 4;       // gather warps in use
+    for (int i = warp; i < nk && warp < G; i += G) {
       const int s = i % S;
+      float v[4][4];                   // [node][column]
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int l = i * CELL_KC + q * 4 + a;
+        const int g = l < P.ne ? dm[l] : -1;
+        v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
+        if (g >= 0) {
+          const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
+          if (vec && cq + 4 <= ncv) {
+            const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
+            v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (cq + u < ncv) v[a][u] = __ldg(src + u);
+          }
+        }
+      }
       if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 3);
         *(volatile int*)abort_flag = 1;
@@ -247,72 +302,106 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) 
       if (*(volatile int*)abort_flag) break;
       float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
       float* yl = yh + CELL_BN * CELL_KC;
-      const int l = i * CELL_KC + kk;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      const int g = l < P.ne ? dm[l] : -1;
-      if (g >= 0) {
-        const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + j4;
-        if (vec && j4 + 4 <= ncv) {
-          float4 q = __ldg(reinterpret_cast<const float4*>(src));
-          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-        } else {
-          for (int u = 0; u < 4; ++u)
-            if (j4 + u < ncv) v[u] = __ldg(src + u);
-        }
-      }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int n = j4 + u;
-        const int o = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
-        const float h = tf32_rna(v[u]);
-        yh[o] = h;
-        yl[o] = tf32_rna(v[u] - h);
+        const int n = cq + u;
+        const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
+        float4 h, lo;
+        h.x = tf32_rna(v[0][u]); lo.x = v[0][u] - h.x;
+        h.y = tf32_rna(v[1][u]); lo.y = v[1][u] - h.y;
+        h.z = tf32_rna(v[2][u]); lo.z = v[2][u] - h.z;
+        h.w = tf32_rna(v[3][u]); lo.w = v[3][u] - h.w;
+        *reinterpret_cast<float4*>(yh + o) = h;
+        *reinterpret_cast<float4*>(yl + o) = lo;
       }
       fence_proxy_async_smem();
       mbar_arrive(fy(s));
     }
-    // ---------------- epilogue: TMEM -> registers -> colour-mode update
+    // ---------------- epilogue: TMEM -> shared tile -> row-wise colour-mode update
+    // The stage buffers are free once every MMA has completed; a 128 x 64 tile
+    // of the result is staged there so that each warp then walks whole rows
+    // (one unknown, warp-uniform mode) with lanes over consecutive columns.
     const bool okacc = mbar_wait(accb, 0);
     if (!okacc) {
       atomicExch(&g_tc_status, 4);
       *(volatile int*)abort_flag = 1;
     }
     tc_fence_after();
-    const bool run = okacc && !*(volatile int*)abort_flag;
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    float* E = reinterpret_cast<float*>(smem);
+    constexpr int EP = CELL_BN + 1;
     for (int t = 0; t < P.mt; ++t) {
-      const int l = t * 128 + warp * 32 + lane;
-      const bool row_ok = run && l < P.ne;
-      const int g = row_ok ? dm[l] : -1;
-      const int mode = row_ok ? md[l] : MODE_SKIP;
-      for (int cb = 0; cb < bne; cb += 16) {
-        float acc[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CELL_BN + cb, acc);
-        tmem_wait_ld();
-        if (g < 0 || mode == MODE_SKIP) continue;
-        const int64_t gw = (int64_t)g * P.ld_w + c0 + cb;
+      __syncwarp();   // tcgen05.ld and bar.sync are warp-aligned: reconverge first
+      if (run) {
+        for (int cb = 0; cb < bne; cb += 16) {
+          float acc[16];
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CELL_BN + cb, acc);
+          tmem_wait_ld();
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int c = cb + u;
-          if (c >= ncv) break;
-          float vv = acc[u];
-          if (mode == MODE_STORE) {
-            P.W[gw + u] = vv;
-          } else if (mode == MODE_ACCUM) {
-            P.W[gw + u] += vv;
-          } else {
-            if (mode == MODE_FINAL) vv += P.W[gw + u];
-            if (P.NL) vv += P.NL[gw + u];
-            const float y = P.Yin[(int64_t)g * P.ld_in + c0 + c];
-            float out = P.alpha * (vv - P.shift * y);
-            if (P.Yprev) out = fmaf(P.beta, P.Yprev[(int64_t)g * P.ld_prev + c0 + c], out);
-            P.Yout[(int64_t)g * P.ld_out + c0 + c] = out;
+          for (int u = 0; u < 16; ++u) E[(warp * 32 + lane) * EP + cb + u] = acc[u];
+        }
+      }
+      __syncwarp();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (run) {
+        // rows r = warp + 4 j; batches of RB rows: every global load of the
+        // batch is issued before any is used (memory-level parallelism)
+        constexpr int RB = 8;
+        for (int j0 = 0; j0 < 32; j0 += RB) {
+          float wv[RB][2], yv[RB][2], pv[RB][2], nv[RB][2];
+          int gg[RB], mm[RB];
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const int r = warp + 4 * (j0 + b);
+            const int l = t * 128 + r;
+            gg[b] = l < P.ne ? dm[l] : -1;
+            mm[b] = l < P.ne ? md[l] : MODE_SKIP;
+            if (gg[b] < 0) mm[b] = MODE_SKIP;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c = lane + 32 * h;
+              wv[b][h] = yv[b][h] = pv[b][h] = nv[b][h] = 0.f;
+              if (mm[b] == MODE_SKIP || c >= ncv) continue;
+              const int64_t g = gg[b];
+              if (mm[b] == MODE_ACCUM || mm[b] == MODE_FINAL) wv[b][h] = P.W[g * P.ld_w + c0 + c];
+              if (mm[b] == MODE_FINAL || mm[b] == MODE_FINAL_DIRECT) {
+                yv[b][h] = P.Yin[g * P.ld_in + c0 + c];
+                if (P.Yprev) pv[b][h] = P.Yprev[g * P.ld_prev + c0 + c];
+                if (P.NL) nv[b][h] = P.NL[g * P.ld_w + c0 + c];
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < RB; ++b) {
+            const int r = warp + 4 * (j0 + b);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c = lane + 32 * h;
+              if (mm[b] == MODE_SKIP || c >= ncv) continue;
+              const int64_t g = gg[b];
+              const float vv = E[r * EP + c];
+              if (mm[b] == MODE_STORE) {
+                P.W[g * P.ld_w + c0 + c] = vv;
+              } else if (mm[b] == MODE_ACCUM) {
+                P.W[g * P.ld_w + c0 + c] = wv[b][h] + vv;
+              } else {
+                const float tot = (mm[b] == MODE_FINAL ? wv[b][h] + vv : vv) + nv[b][h];
+                float out = P.alpha * (tot - P.shift * yv[b][h]);
+                if (P.Yprev) out = fmaf(P.beta, pv[b][h], out);
+                P.Yout[g * P.ld_out + c0 + c] = out;
+              }
+            }
           }
         }
       }
+      __syncwarp();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   }
   tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  if (P.cl > 1) cluster_sync();   // no member leaves while peers may still signal it
+  else __syncthreads();
   if (warp == 5) tmem_dealloc(tmem, tmem_cols);
 }
 
@@ -347,10 +436,23 @@ cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_
     cudaFuncSetAttribute(tc_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  dim3 grid((a.ncol + CELL_BN - 1) / CELL_BN, (unsigned)a.ncells);
+  const int tiles = (a.ncol + CELL_BN - 1) / CELL_BN;
+  int cl = tiles >= 4 ? 4 : (tiles >= 2 ? 2 : 1);
+  P.cl = cl;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((tiles + cl - 1) / cl * cl, (unsigned)a.ncells);
+  cfg.blockDim = dim3(CELL_THREADS);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = s;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = cl;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
   note_launch();
-  tc_cell_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, tc_cell_kernel, P);
 }
 
 int tc_read_status(cudaStream_t s) {
@@ -366,12 +468,8 @@ int tc_read_status(cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- Gram (A^T B)
-// Output tile 128 x 128 of C = A^T B (rows i of C <-> columns of A, columns j
-// <-> columns of B); K = unknowns, split over grid.z.  Operands are loaded by
-// warps 0-3, split into TF32 hi/lo and stored transposed (K-major) in shared
-// memory; warp 4 issues the MMAs.  Tiles strictly above the diagonal are
-// skipped when `lower`.  Partial tiles (binary64) are reduced in fixed order.
-constexpr int GR_T = 128, GR_KC = 16, GR_THREADS = 160;
+constexpr int GR_T = 128, GR_KC = 8, GR_THREADS = 160, GR_S = 6;
+static_assert(GR_S >= 4, "parity waits of the 4 producer warps need at least 4 stages");
 
 __host__ __device__ inline int gram_stage_bytes(int same) {
   return (same ? 1 : 2) * GR_T * GR_KC * 4 * 2;   // operands x (hi + lo)
@@ -386,10 +484,53 @@ struct GramParams {
   double* partial;
 };
 
-__device__ __forceinline__ int gr_off(int n, int k) {   // floats, 128 rows x 16 K, SBO 512 B
-  return (n >> 3) * 128 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+// (row n, K index k) of a 128 x 8 operand block, K-major core matrices:
+// LBO 128 B along K, SBO 256 B along the 128 rows.
+__device__ __forceinline__ int k8_off(int n, int k) {
+  return (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
 }
 
+// Load 4 rows x 4 columns (row-major source, column offset col0) and store the
+// TF32 hi / lo split transposed: per column, 4 consecutive K values as one
+// 16-byte store (K-major layout).  Rows >= r1 or columns >= nmax read as 0.
+__device__ __forceinline__ void load4x4(const float* __restrict__ X, int64_t ld, int64_t row0,
+                                        int64_t r1, int col0, int nmax, bool vec, float v[4][4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t row = row0 + a;
+    v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
+    if (row < r1) {
+      const float* src = X + row * ld + col0;
+      if (vec && col0 + 4 <= nmax) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(src));
+        v[a][0] = t.x; v[a][1] = t.y; v[a][2] = t.z; v[a][3] = t.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (col0 + u < nmax) v[a][u] = __ldg(src + u);
+      }
+    }
+  }
+}
+__device__ __forceinline__ void store_split_t(float* hi, float* lo, int nbase, int kq, const float v[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int o = k8_off(nbase + u, kq * 4);
+    float4 h, l;
+    h.x = tf32_rna(v[0][u]); l.x = v[0][u] - h.x;
+    h.y = tf32_rna(v[1][u]); l.y = v[1][u] - h.y;
+    h.z = tf32_rna(v[2][u]); l.z = v[2][u] - h.z;
+    h.w = tf32_rna(v[3][u]); l.w = v[3][u] - h.w;
+    *reinterpret_cast<float4*>(hi + o) = h;
+    *reinterpret_cast<float4*>(lo + o) = l;
+  }
+}
+
+// Output tile 128 x 128 of C = A^T B (rows i of C <-> columns of A, columns j
+// <-> columns of B); K = unknowns, split over grid.z.  Warps 0-3 produce the
+// K-chunks (warp w: chunks w, w+4, ...; registers prefetched before the stage
+// is free), warp 4 issues the MMAs.  Tiles strictly above the diagonal are
+// skipped when `lower`; partial tiles (binary64) are reduced in fixed order.
 __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int ti = blockIdx.x, tj = blockIdx.y, z = blockIdx.z;
@@ -397,7 +538,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool same = (P.A == P.B) && (P.lda == P.ldb) && ti == tj;
   const int SB = gram_stage_bytes(same);
-  const int S = 3;
+  const int S = GR_S;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * gram_stage_bytes(0));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -407,11 +548,11 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
   const uint32_t accb = smem_u32(bars + 2 * S);
   const int64_t r0 = (int64_t)z * P.rows_per_split;
   const int64_t r1 = min(P.M, r0 + P.rows_per_split);
-  const int nk = (int)((r1 - r0 + GR_KC - 1) / GR_KC);
+  const int nk = r1 > r0 ? (int)((r1 - r0 + GR_KC - 1) / GR_KC) : 0;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full(s), 128);
+      mbar_init(full(s), 32);
       mbar_init(emp(s), 1);
     }
     mbar_init(accb, 1);
@@ -430,73 +571,54 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
   if (warp == 4) {
     if (lane == 0 && nk > 0) {
       const uint32_t idesc = idesc_tf32(128, 128);
-      bool ok = true;
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
         if (!mbar_wait(full(s), (i / S) & 1) || *(volatile int*)abort_flag) {
           atomicExch(&g_tc_status, 5);
           *(volatile int*)abort_flag = 1;
-          ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t sa = sbase + s * SB;
         const uint32_t sb = same ? sa : sa + GR_T * GR_KC * 8;
-        for (int j = 0; j < GR_KC / 8; ++j) {
-          const uint64_t ah = umma_desc(sa + j * 256, 128, 512);
-          const uint64_t al = umma_desc(sa + GR_T * GR_KC * 4 + j * 256, 128, 512);
-          const uint64_t bh = umma_desc(sb + j * 256, 128, 512);
-          const uint64_t bl = umma_desc(sb + GR_T * GR_KC * 4 + j * 256, 128, 512);
-          const uint32_t first = (i > 0 || j > 0);
-          if (P.split3) {
-            mma_tf32(tmem, al, bh, idesc, first);
-            mma_tf32(tmem, ah, bl, idesc, 1);
-            mma_tf32(tmem, ah, bh, idesc, 1);
-          } else {
-            mma_tf32(tmem, ah, bh, idesc, first);
-          }
+        const uint64_t ah = umma_desc(sa, 128, 256);
+        const uint64_t al = umma_desc(sa + GR_T * GR_KC * 4, 128, 256);
+        const uint64_t bh = umma_desc(sb, 128, 256);
+        const uint64_t bl = umma_desc(sb + GR_T * GR_KC * 4, 128, 256);
+        if (P.split3) {
+          mma_tf32(tmem, al, bh, idesc, i > 0);
+          mma_tf32(tmem, ah, bl, idesc, 1);
+          mma_tf32(tmem, ah, bh, idesc, 1);
+        } else {
+          mma_tf32(tmem, ah, bh, idesc, i > 0);
         }
         umma_commit(emp(s));
       }
-      (void)ok;
       umma_commit(accb);
     }
   } else {
-    // warps 0-3: load rows r of A[:, ti*128 ..] and B[:, tj*128 ..], split, store K-major
-    const int cq = (tid & 31) * 4;    // 4 columns
-    const int rr = tid >> 5;          // row lane 0..3
-    const int ia = ti * GR_T, jb = tj * GR_T;
-    for (int i = 0; i < nk; ++i) {
+    const bool vecA = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+    const bool vecB = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0);
+    const int ia = ti * GR_T + lane * 4, jb = tj * GR_T + lane * 4;
+    for (int i = warp; i < nk; i += 4) {
       const int s = i % S;
+      const int64_t row0 = r0 + (int64_t)i * GR_KC;
+      float va[2][4][4], vb[2][4][4];
+#pragma unroll
+      for (int kq = 0; kq < 2; ++kq) {
+        load4x4(P.A, P.lda, row0 + kq * 4, r1, ia, P.n1, vecA, va[kq]);
+        if (!same) load4x4(P.B, P.ldb, row0 + kq * 4, r1, jb, P.n2, vecB, vb[kq]);
+      }
       if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 6);
         *(volatile int*)abort_flag = 1;
       }
       if (*(volatile int*)abort_flag) break;
       float* sh = reinterpret_cast<float*>(smem + s * SB);
-      for (int op = 0; op < (same ? 1 : 2); ++op) {
-        const float* X = op == 0 ? P.A : P.B;
-        const int64_t ld = op == 0 ? P.lda : P.ldb;
-        const int nmax = op == 0 ? P.n1 : P.n2;
-        const int cbase = op == 0 ? ia : jb;
-        float* hi = sh + op * GR_T * GR_KC * 2;
-        float* lo = hi + GR_T * GR_KC;
-        for (int k = rr; k < GR_KC; k += 4) {
-          const int64_t row = r0 + (int64_t)i * GR_KC + k;
-          float v[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int col = cbase + cq + u;
-            v[u] = (row < r1 && col < nmax) ? __ldg(X + row * ld + col) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int o = gr_off(cq + u, k);
-            const float h = tf32_rna(v[u]);
-            hi[o] = h;
-            lo[o] = tf32_rna(v[u] - h);
-          }
-        }
+      for (int kq = 0; kq < 2; ++kq) {
+        store_split_t(sh, sh + GR_T * GR_KC, lane * 4, kq, va[kq]);
+        if (!same) store_split_t(sh + GR_T * GR_KC * 2, sh + GR_T * GR_KC * 3, lane * 4, kq, vb[kq]);
       }
       fence_proxy_async_smem();
       mbar_arrive(full(s));
@@ -507,11 +629,14 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
       if (!okacc) atomicExch(&g_tc_status, 7);
     }
     tc_fence_after();
-    // epilogue: row i = ti*128 + warp*32 + lane, columns tj*128 + c
+    // epilogue: thread row i = ti*128 + warp*32 + lane; consecutive lanes write
+    // consecutive i of a column-major partial tile (coalesced)
+    __syncwarp();   // tcgen05.ld is warp-aligned: reconverge after the polling above
     const int i = ti * GR_T + warp * 32 + lane;
     double* Pz = P.partial + (int64_t)z * P.n1 * P.n2;
     for (int cb = 0; cb < 128; cb += 16) {
       float acc[16];
+      __syncwarp();
       if (nk > 0) {
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
         tmem_wait_ld();
@@ -614,7 +739,7 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
   int64_t rps = ((M + nsplit - 1) / nsplit + GR_KC - 1) / GR_KC * GR_KC;
   nsplit = (M + rps - 1) / rps;
   GramParams P{A, B, lda, ldb, M, n1, n2, lower, split3, rps, (double*)partial};
-  const int smem = 3 * gram_stage_bytes(0) + 1024;
+  const int smem = GR_S * gram_stage_bytes(0) + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -651,13 +776,16 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
 
 // ----------------------------------------------------------------- tall GEMM (X U)
 // C (M x n2) = A (M x n1, binary32) U (n1 x n2, binary64).  Tile: 128 rows x
-// 128 columns; K-loop over n1 in chunks of 16.  U is split into TF32 hi / lo
-// once per call into a K-major chunked layout (tc_splitu_kernel); diagonal
+// 128 columns; K-loop over n1 in chunks of 8.  U is split into TF32 hi / lo
+// once per call into a chunked K-major layout (tc_splitu_kernel); diagonal
 // blocks of U are excluded from the tensor-core product and added in binary64
-// in the epilogue (the paper's Psi L^{-1}_d term).
-constexpr int TG_T = 128, TG_KC = 16, TG_THREADS = 160;
+// in the epilogue (the paper's Psi L^{-1}_d term).  Grid x runs over column
+// tiles so the CTAs sharing a row block of A run together (A read once from
+// HBM).  The epilogue stages the tile in shared memory and writes whole rows.
+constexpr int TG_T = 128, TG_KC = 8, TG_THREADS = 160, TG_S = 6;
+static_assert(TG_S >= 4, "parity waits of the 4 producer warps need at least 4 stages");
 
-// U split layout: [col tile][k chunk][hi|lo][128 cols x 16 K in gr_off layout]
+// U split layout: [col tile][k chunk][hi|lo][128 cols x 8 K in k8_off layout]
 __global__ void tc_splitu_kernel(const double* __restrict__ U, int64_t ldu, int n1, int n2, int upper,
                                  int trans, int bd, float* __restrict__ out) {
   const int nkc = (n1 + TG_KC - 1) / TG_KC;
@@ -676,8 +804,8 @@ __global__ void tc_splitu_kernel(const double* __restrict__ U, int64_t ldu, int 
   const float h = tf32_rna((float)v);
   const float l = tf32_rna((float)(v - (double)h));
   float* base = out + ((int64_t)tile * nkc + kc) * 2 * TG_T * TG_KC;
-  base[gr_off(n, k)] = h;
-  base[TG_T * TG_KC + gr_off(n, k)] = l;
+  base[k8_off(n, k)] = h;
+  base[TG_T * TG_KC + k8_off(n, k)] = l;
 }
 
 struct TallParams {
@@ -694,14 +822,14 @@ struct TallParams {
 __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t rb = (int64_t)blockIdx.x * TG_T;
-  const int tj = blockIdx.y;
+  const int tj = blockIdx.x;
+  const int64_t rb = (int64_t)blockIdx.y * TG_T;
   const int nkc_all = (P.n1 + TG_KC - 1) / TG_KC;
   int kend = P.n1;
   if (P.upper) kend = min(P.n1, (tj + 1) * TG_T);
   const int nk = (kend + TG_KC - 1) / TG_KC;
   const int SB = 2 * TG_T * TG_KC * 4 * 2;   // A (hi, lo) + U (hi, lo)
-  const int S = 3;
+  const int S = TG_S;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * SB);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -711,7 +839,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
   const uint32_t accb = smem_u32(bars + 2 * S);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full(s), 128);
+      mbar_init(full(s), 32);
       mbar_init(emp(s), 1);
     }
     mbar_init(accb, 1);
@@ -742,60 +870,78 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
         tc_fence_after();
         const uint32_t sa = sbase + s * SB;
         const uint32_t su = sa + TG_T * TG_KC * 8;
-        for (int j = 0; j < TG_KC / 8; ++j) {
-          const uint64_t ah = umma_desc(sa + j * 256, 128, 512);
-          const uint64_t al = umma_desc(sa + TG_T * TG_KC * 4 + j * 256, 128, 512);
-          const uint64_t uh = umma_desc(su + j * 256, 128, 512);
-          const uint64_t ul = umma_desc(su + TG_T * TG_KC * 4 + j * 256, 128, 512);
-          const uint32_t acc = (i > 0 || j > 0);
-          if (P.split3) {
-            mma_tf32(tmem, al, uh, idesc, acc);
-            mma_tf32(tmem, ah, ul, idesc, 1);
-            mma_tf32(tmem, ah, uh, idesc, 1);
-          } else {
-            mma_tf32(tmem, ah, uh, idesc, acc);
-          }
+        const uint64_t ah = umma_desc(sa, 128, 256);
+        const uint64_t al = umma_desc(sa + TG_T * TG_KC * 4, 128, 256);
+        const uint64_t uh = umma_desc(su, 128, 256);
+        const uint64_t ul = umma_desc(su + TG_T * TG_KC * 4, 128, 256);
+        if (P.split3) {
+          mma_tf32(tmem, al, uh, idesc, i > 0);
+          mma_tf32(tmem, ah, ul, idesc, 1);
+          mma_tf32(tmem, ah, uh, idesc, 1);
+        } else {
+          mma_tf32(tmem, ah, uh, idesc, i > 0);
         }
         umma_commit(emp(s));
       }
       umma_commit(accb);
     }
   } else {
-    for (int i = 0; i < nk; ++i) {
+    const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+    for (int i = warp; i < nk; i += 4) {
       const int s = i % S;
+      // A: rows rb + lane + 32 j, K quads kq: 4 consecutive K values (already K-major)
+      float4 av[4][2];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t row = rb + lane + 32 * j;
+#pragma unroll
+        for (int kq = 0; kq < 2; ++kq) {
+          const int k0 = i * TG_KC + kq * 4;
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < P.M) {
+            const float* src = P.A + row * P.lda + k0;
+            if (vec && k0 + 4 <= P.n1) {
+              t = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+              if (k0 + 0 < P.n1) t.x = __ldg(src + 0);
+              if (k0 + 1 < P.n1) t.y = __ldg(src + 1);
+              if (k0 + 2 < P.n1) t.z = __ldg(src + 2);
+              if (k0 + 3 < P.n1) t.w = __ldg(src + 3);
+            }
+          }
+          av[j][kq] = t;
+        }
+      }
+      const float4* usrc = reinterpret_cast<const float4*>(
+          P.Us + ((int64_t)tj * nkc_all + i) * 2 * TG_T * TG_KC);
+      float4 uv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) uv[q] = __ldg(usrc + lane + 32 * q);
       if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 9);
         *(volatile int*)abort_flag = 1;
       }
       if (*(volatile int*)abort_flag) break;
       float* sa = reinterpret_cast<float*>(smem + s * SB);
-      float* ahi = sa;
-      float* alo = sa + TG_T * TG_KC;
-      // A rows rb..rb+127, K columns i*16 .. i*16+15: 128 x 16 floats, 16 per thread
-      for (int q = tid; q < TG_T * 4; q += 128) {
-        const int r = q >> 2, k4 = (q & 3) * 4;
-        const int64_t row = rb + r;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (row < P.M) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int kk = i * TG_KC + k4 + u;
-            if (kk < P.n1) v[u] = __ldg(P.A + row * P.lda + kk);
-          }
-        }
+      for (int j = 0; j < 4; ++j) {
+        const int r = lane + 32 * j;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int o = gr_off(r, k4 + u);
-          const float h = tf32_rna(v[u]);
-          ahi[o] = h;
-          alo[o] = tf32_rna(v[u] - h);
+        for (int kq = 0; kq < 2; ++kq) {
+          const float4 t = av[j][kq];
+          float4 h, l;
+          h.x = tf32_rna(t.x); l.x = t.x - h.x;
+          h.y = tf32_rna(t.y); l.y = t.y - h.y;
+          h.z = tf32_rna(t.z); l.z = t.z - h.z;
+          h.w = tf32_rna(t.w); l.w = t.w - h.w;
+          const int o = k8_off(r, kq * 4);
+          *reinterpret_cast<float4*>(sa + o) = h;
+          *reinterpret_cast<float4*>(sa + TG_T * TG_KC + o) = l;
         }
       }
-      // U chunk: contiguous 2 x 8 KB block of the pre-split layout
-      const float4* src = reinterpret_cast<const float4*>(
-          P.Us + ((int64_t)tj * nkc_all + i) * 2 * TG_T * TG_KC);
-      float4* dst = reinterpret_cast<float4*>(sa + 2 * TG_T * TG_KC);
-      for (int q = tid; q < TG_T * TG_KC * 2 / 4; q += 128) dst[q] = __ldg(src + q);
+      float4* udst = reinterpret_cast<float4*>(sa + 2 * TG_T * TG_KC);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) udst[lane + 32 * q] = uv[q];
       fence_proxy_async_smem();
       mbar_arrive(full(s));
     }
@@ -805,31 +951,46 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
       if (!okacc) atomicExch(&g_tc_status, 10);
     }
     tc_fence_after();
-    const int64_t row = rb + warp * 32 + lane;
-    for (int cb = 0; cb < bne; cb += 16) {
-      float acc[16];
-      if (nk > 0) {
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
-        tmem_wait_ld();
-      } else {
-        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
-      }
-      if (row >= P.M || !okacc) continue;
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    // stage the 128 x 128 tile in shared memory (stage buffers are free), then
+    // each warp writes whole rows with lanes over consecutive columns
+    float* E = reinterpret_cast<float*>(smem);
+    constexpr int EP = TG_T + 1;
+    if (run) {
+      for (int cb = 0; cb < bne; cb += 16) {
+        float acc[16];
+        __syncwarp();
+        if (nk > 0) {
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+          tmem_wait_ld();
+        } else {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int col = tj * TG_T + cb + u;
-        if (cb + u >= ncv) break;
-        double v = (double)acc[u];
-        if (P.bd > 0) {   // binary64 diagonal block of U
-          const int k0 = (col / P.bd) * P.bd;
-          const int k1 = min(P.n1, k0 + P.bd);
-          for (int kk = k0; kk < k1; ++kk) {
-            if (P.upper && kk > col) break;
-            const double u_ = P.trans ? P.U[col + (int64_t)kk * P.ldu] : P.U[kk + (int64_t)col * P.ldu];
-            v = fma((double)P.A[row * P.lda + kk], u_, v);
-          }
+          for (int u = 0; u < 16; ++u) acc[u] = 0.f;
         }
-        P.C[row * P.ldc + col] = (float)v;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) E[(warp * 32 + lane) * EP + cb + u] = acc[u];
+      }
+    }
+    __syncwarp();
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (run) {
+      for (int r = warp; r < TG_T; r += 4) {
+        const int64_t row = rb + r;
+        if (row >= P.M) break;
+        for (int c = lane; c < ncv; c += 32) {
+          const int col = tj * TG_T + c;
+          double v = (double)E[r * EP + c];
+          if (P.bd > 0) {   // binary64 diagonal block of U
+            const int k0 = (col / P.bd) * P.bd;
+            const int k1 = min(P.n1, k0 + P.bd);
+            for (int kk = k0; kk < k1; ++kk) {
+              if (P.upper && kk > col) break;
+              const double u_ = P.trans ? P.U[col + (int64_t)kk * P.ldu] : P.U[kk + (int64_t)col * P.ldu];
+              v = fma((double)P.A[row * P.lda + kk], u_, v);
+            }
+          }
+          P.C[row * P.ldc + col] = (float)v;
+        }
       }
     }
   }
@@ -854,13 +1015,13 @@ cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int6
   note_launch();
   tc_splitu_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans, bd, Us);
   TallParams P{A, lda, M, Us, U, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
-  const int smem = 3 * (2 * TG_T * TG_KC * 4 * 2) + 1024;
+  const int smem = TG_S * (2 * TG_T * TG_KC * 4 * 2) + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc_tall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  dim3 grid((unsigned)((M + TG_T - 1) / TG_T), ntile);
+  dim3 grid(ntile, (unsigned)((M + TG_T - 1) / TG_T));
   note_launch();
   tc_tall_kernel<<<grid, TG_THREADS, smem, s>>>(P);
   return cudaGetLastError();
