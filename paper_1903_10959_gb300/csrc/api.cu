@@ -42,6 +42,8 @@ struct chfsi_ctx {
   uint8_t* d_modes = nullptr;
   int32_t* d_cells = nullptr;
   double* d_mass = nullptr;
+  int32_t* d_node_ptr = nullptr;
+  int32_t* d_node_ent = nullptr;
   int64_t* d_site_ptr = nullptr;
   int32_t* d_site_dof = nullptr;
   double* d_site_c = nullptr;
@@ -51,7 +53,7 @@ struct chfsi_ctx {
   float* d_site_c32 = nullptr;
   float* d_dof_c32 = nullptr;
   // grown scratch
-  DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam;
+  DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double times[4] = {0, 0, 0, 0};
@@ -156,7 +158,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   const int B = std::max(ncol, 1);
   const size_t es = esize(prec);
   chfsi_status st;
-  if ((st = grow(ctx, ctx->Wb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+  if (prec == CHFSI_FP64 && (st = grow(ctx, ctx->Wb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
   const bool nl = ctx->hproj.nsite > 0;
   if (nl) {
     if ((st = grow(ctx, ctx->NLb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
@@ -203,28 +205,23 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     CK(tc_nl_expand(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c32, m.ndofs,
                     (const float*)ctx->Zb.ptr, ncol, (float*)ctx->NLb.ptr, B, ctx->stream));
   }
-  for (int c = 0; c < ncolour; ++c) {
-    TcCellArgs a{};
-    a.cells = ctx->d_cells + m.colour_offsets[c];
-    a.ncells = m.colour_offsets[c + 1] - m.colour_offsets[c];
-    a.dofmap = ctx->d_dofmap;
-    a.modes = ctx->d_modes;
-    a.ncol = ncol;
-    a.Yin = (const float*)Yin;
-    a.ld_in = ld_in;
-    a.Yout = (float*)Yout;
-    a.ld_out = ld_out;
-    a.Yprev = beta != 0.0 ? (const float*)Yprev : nullptr;
-    a.ld_prev = ld_prev;
-    a.W = (float*)ctx->Wb.ptr;
-    a.NL = nl ? (const float*)ctx->NLb.ptr : nullptr;
-    a.ld_w = B;
-    a.alpha = (float)alpha;
-    a.beta = (float)beta;
-    a.shift = (float)shift;
-    a.split3 = prec == CHFSI_MIXED_TF32X3;
-    CK(tc_cell_launch(ctx->tc, a, ctx->stream));
-  }
+  // owner-computes: dense cell blocks R_e (one launch over all cells), then the
+  // fixed-order assembly fused with the Chebyshev update
+  if ((st = grow(ctx, ctx->Rb, (size_t)m.ncells * m.ne * ncol * sizeof(float))) != CHFSI_OK) return st;
+  TcApplyArgs ra{};
+  ra.dofmap = ctx->d_dofmap;
+  ra.ncells = m.ncells;
+  ra.ncol = ncol;
+  ra.Yin = (const float*)Yin;
+  ra.ld_in = ld_in;
+  ra.R = (float*)ctx->Rb.ptr;
+  ra.split3 = prec == CHFSI_MIXED_TF32X3;
+  CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
+  CK(tc_assemble_launch(ctx->d_node_ptr, ctx->d_node_ent, m.ndofs, ncol, (const float*)ctx->Rb.ptr,
+                        (const float*)Yin, ld_in, (float*)Yout, ld_out,
+                        beta != 0.0 ? (const float*)Yprev : nullptr, ld_prev,
+                        nl ? (const float*)ctx->NLb.ptr : nullptr, B, (float)alpha, (float)beta,
+                        (float)shift, ctx->stream));
   return CHFSI_OK;
 }
 
@@ -542,6 +539,8 @@ chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx**
       (e = upload(ctx, &ctx->d_modes, m.modes)) != cudaSuccess ||
       (e = upload(ctx, &ctx->d_cells, m.colour_cells)) != cudaSuccess ||
       (e = upload(ctx, &ctx->d_mass, m.mass)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_node_ptr, m.node_ptr)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_node_ent, m.node_ent)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev[0])) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev[1])) != cudaSuccess ||
       (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
@@ -561,8 +560,10 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_modes, m.modes.size());
   release(ctx, ctx->d_cells, m.colour_cells.size() * 4);
   release(ctx, ctx->d_mass, m.mass.size() * 8);
+  release(ctx, ctx->d_node_ptr, m.node_ptr.size() * 4);
+  release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
-                    &ctx->part, &ctx->vec, &ctx->lam})
+                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb})
     dfree(ctx, b->ptr, b->bytes);
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)

@@ -39,6 +39,9 @@ struct HostMesh {
   std::vector<int32_t> colour_cells;   // cells ordered by colour
   std::vector<int64_t> colour_offsets; // ncolours + 1
   std::vector<double> mass;    // ndofs
+  // owner-computes assembly: the cell-local rows (e * ne + l) holding each
+  // unknown, in ascending cell order (fixed summation order)
+  std::vector<int32_t> node_ptr, node_ent;
   // 1-D rules
   std::vector<double> gll_x, gll_w, gq_x, gq_w;
   std::vector<double> B, D;    // (q x n1) basis values / d/dxi at Gauss points

@@ -219,6 +219,22 @@ void build_mesh(const chfsi_mesh_desc& d, HostMesh& m) {
     }
   }
 
+  // unknown -> (cell, local node) rows for the owner-computes assembly
+  m.node_ptr.assign(m.ndofs + 1, 0);
+  for (int64_t e = 0; e < m.ncells; ++e)
+    for (int l = 0; l < ne; ++l)
+      if (m.dofmap[e * ne + l] >= 0) m.node_ptr[m.dofmap[e * ne + l] + 1]++;
+  for (int64_t j = 0; j < m.ndofs; ++j) m.node_ptr[j + 1] += m.node_ptr[j];
+  m.node_ent.assign(m.node_ptr[m.ndofs], 0);
+  {
+    std::vector<int32_t> pos(m.node_ptr.begin(), m.node_ptr.end() - 1);
+    for (int64_t e = 0; e < m.ncells; ++e)     // ascending e: fixed summation order
+      for (int l = 0; l < ne; ++l) {
+        const int32_t g = m.dofmap[e * ne + l];
+        if (g >= 0) m.node_ent[pos[g]++] = (int32_t)(e * ne + l);
+      }
+  }
+
   // diagonal mass by GLL quadrature: node weight w_i w_j w_k hx hy hz / 8
   m.mass.assign(m.ndofs, 0.0);
   const double jac = m.h[0] * m.h[1] * m.h[2] / 8.0;

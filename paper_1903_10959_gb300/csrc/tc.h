@@ -36,6 +36,26 @@ struct TcCellArgs {
   int split3;
 };
 
+// Owner-computes form of one H~ Y step (no colouring): every cell writes its
+// dense block R_e = H~_e Y_e (ne x ncol rows at R[(e * ne + l) * ncol]) with
+// plain stores, then each unknown sums its 1..8 cell rows in ascending cell
+// order and applies Y_out = alpha (sum + NL - shift Y_in) + beta Y_prev.
+struct TcApplyArgs {
+  const int32_t* dofmap;
+  int64_t ncells;
+  int ncol;
+  const float* Yin;
+  int64_t ld_in;
+  float* R;                 // ncells * ne * ncol scratch
+  int split3;
+};
+cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
+cudaError_t tc_assemble_launch(const int32_t* node_ptr, const int32_t* node_ent, int64_t M,
+                               int ncol, const float* R, const float* Yin, int64_t ld_in,
+                               float* Yout, int64_t ld_out, const float* Yprev, int64_t ld_prev,
+                               const float* NL, int64_t ld_nl, float alpha, float beta,
+                               float shift, cudaStream_t s);
+
 cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
                      cudaStream_t s, int64_t* dev_bytes);
 // Split the binary64 device cell matrices into the TF32 hi / lo operand layout.
