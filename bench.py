@@ -252,6 +252,8 @@ def run_ours(args):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    ctx.set_kernel_timing(True)
+    ctx.kernel_timings()
     l0 = _lib.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -261,6 +263,8 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = _lib.kernel_launches() - l0
+    kt = ctx.kernel_timings()          # [cell ms, assembly ms, cell launches, assembly launches]
+    ctx.set_kernel_timing(False)
     clk = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
     if dist:
@@ -270,30 +274,51 @@ def run_ours(args):
         dist.barrier()
     value = t / (args.steps * world)
 
-    # roofline of the dominant kernel (the tensor-core / binary64 cell kernel of the filter)
-    ncolour = 8
+    # Roofline of the dominant kernel, the tensor-core cell-product kernel
+    # (per-launch CUDA events on the context stream).  Its algorithmic bytes per
+    # launch (one filter block of nb columns): the split cell matrices
+    # (N_c n_e^2 x 8 B), the block of Y read once (M nb x s_X) and the dense
+    # cell blocks written (N_c n_e nb x s_X).  The whole filter step (cell +
+    # assembly kernels) is also reported against the fused-recurrence minimum
+    # 3 s_X per unknown and vector plus the cell matrices.
     nblocks = -(-n // s.block)
-    launches_filter = args.steps * s.degree * nblocks * ncolour
-    filter_s = phase[0] / 1e3
     ne = (s.p + 1) ** 3
+    ncells = s.ncell ** 3
     sx = 8 if prec == "fp64" else 4
-    sh = 8
-    alg_bytes = args.steps * s.degree * (3 * sx * M * n + nblocks * s.ncell ** 3 * ne * ne * sh)
-    alg_flops = args.steps * s.degree * n * (s.ncell ** 3) * 2 * ne * ne
+    filter_s = phase[0] / 1e3
+    # cell launches in the timed region: every filter degree step and the RR
+    # application, each over one column block
+    steps_blocks = args.steps * (s.degree + 1)
+    col_steps = steps_blocks * n                  # (vector, application) units
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    achieved = alg_bytes / filter_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "kernel": "tc_cell_kernel" if prec != "fp64" else "cell_fp64_kernel",
-            "launches": launches_filter, "avg_launch_ms": phase[0] / launches_filter,
-            "bytes_per_launch": alg_bytes / launches_filter,
-            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    cell_ms, asm_ms, cell_n, asm_n = [float(v) for v in kt]
+    alg_flops = col_steps * ncells * 2 * ne * ne          # dense cell products, one per vector
     if prec == "fp64":
-        roof.update({"bound": "alu", "achieved": alg_flops / filter_s / 1e12, "peak": 1.0,
-                     "unit": "TFLOP/s", "frac": alg_flops / filter_s / 1e12 / 1.0,
-                     "peak_note": "binary64 DFMA peak 1.0 TFLOP/s measured by a DFMA probe"})
-
+        roof = {"bound": "alu", "achieved": alg_flops / (cell_ms / 1e3) / 1e12, "peak": 1.0,
+                "unit": "TFLOP/s", "kernel": "cell_fp64_kernel", "launches": int(cell_n),
+                "avg_launch_ms": cell_ms / max(cell_n, 1),
+                "peak_note": "binary64 DFMA peak 1.0 TFLOP/s measured by a DFMA probe on this GB300"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        step_roof = None
+    else:
+        cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * 8
+                      + col_steps * M * sx + col_steps * ncells * ne * sx)
+        per_launch = cell_bytes / cell_n
+        achieved = cell_bytes / (cell_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "tc_cell_r_kernel",
+                "launches": int(cell_n), "avg_launch_ms": cell_ms / cell_n,
+                "bytes_per_launch": per_launch,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
+        step_bytes = col_steps * 3 * sx * M + steps_blocks * nblocks * ncells * ne * ne * 8
+        step_roof = {"bound": "hbm", "achieved": step_bytes / ((cell_ms + asm_ms) / 1e3) / 1e9,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "kernels": "tc_cell_r_kernel + tc_assemble_kernel",
+                     "assemble_avg_launch_ms": asm_ms / max(asm_n, 1)}
+        step_roof["frac"] = step_roof["achieved"] / peaks["hbm_gbs"]
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1672.5) * 1.1 / 2.25
     phase_timed = phase.copy()
     # end to end through host buffers: H2D of X, one iteration, D2H of X and the Ritz values
     e2e = None
@@ -331,10 +356,12 @@ def run_ours(args):
         "phases_ms_per_step": {"filter": phase_timed[0] / args.steps,
                                "cholgs": phase_timed[1] / args.steps,
                                "rr": phase_timed[2] / args.steps},
-        "filter_tflops": {"algorithmic": alg_flops / filter_s / 1e12,
-                          "executed_tensor": (3 if prec == "mixed" else 1) * alg_flops / filter_s / 1e12
-                          if prec != "fp64" else None},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "filter_tflops": {"algorithmic_per_filter_time": alg_flops / filter_s / 1e12,
+                          "cell_kernel_executed_tensor": (3 if prec == "mixed" else 1) * alg_flops
+                          / (cell_ms / 1e3) / 1e12 if prec != "fp64" else None,
+                          "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
+        "roofline": roof, "roofline_filter_step": step_roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches,
         "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
     }
     print(json.dumps(line), flush=True)

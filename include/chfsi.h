@@ -203,9 +203,66 @@ chfsi_status chfsi_last_timings(chfsi_ctx* ctx, double* out4);
 /* Bytes of device memory the context currently holds. */
 int64_t      chfsi_device_bytes(const chfsi_ctx* ctx);
 
+/* Event timing of the filter kernels (on != 0: every cell-product and
+ * assembly launch of this context is bracketed by CUDA events on its stream;
+ * for measurement runs, the events cost a few microseconds per launch). */
+chfsi_status chfsi_set_kernel_timing(chfsi_ctx* ctx, int on);
+
+/* Accumulated device times since the last call, then reset:
+ * out4[0] cell-product kernel ms, out4[1] assembly kernel ms, out4[2] and
+ * out4[3] the numbers of launches timed.  Synchronises the stream. */
+chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out4);
+
 /* Number of kernels this library has launched so far (all contexts; a
  * monotonic counter for accounting, e.g. launches per ChFSI iteration). */
 int64_t      chfsi_kernel_launches(void);
+
+/* ---------------------------------------------------------------- batching
+ * Many independent systems of the same FE degree (typically small and of
+ * uneven size) filtered together on the tensor cores.  Per Chebyshev degree
+ * step one persistent launch of the cell kernel covers the (system, cell,
+ * column-tile) items of every system and one launch of the assembly kernel
+ * covers every unknown of every system; the whole degree-m filter is
+ * captured once into a CUDA graph and replayed while the buffers, widths,
+ * degree and tile choice stay the same (the recurrence scalars live in device
+ * memory and are refreshed by the graph).  Contexts must be built, share the
+ * device, have no projectors and p <= 7. */
+typedef struct chfsi_batch chfsi_batch;
+
+chfsi_status chfsi_batch_create(int n, chfsi_ctx* const* ctxs, void* stream, chfsi_batch** out);
+chfsi_status chfsi_batch_destroy(chfsi_batch* b);
+const char*  chfsi_batch_last_error(const chfsi_batch* b);
+
+/* Filter X[s] (device, binary32, M_s x ncol[s], leading dimension ldx[s]) of
+ * every system in place with degree `degree` and bounds a[s] < b[s],
+ * a0[s] < a[s] (scaled Eq. chebFilter), precision MIXED_TF32X3 or MIXED_TF32.
+ * Synchronises the batch stream. */
+chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* ldx,
+                                const int* ncol, int degree, const double* a,
+                                const double* bnd, const double* a0, chfsi_precision prec);
+
+/* Autotuner of the batched cell kernel: times every candidate (column tile
+ * width x pipeline depth, see chfsi_batch_candidates) on two degree steps of
+ * this batch and keeps the fastest for later filter calls.  X is used as
+ * scratch and overwritten.  choice (may be NULL) receives the winning index,
+ * ms_out (may be NULL, one entry per candidate) the measured times. */
+chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t* ldx,
+                                  const int* ncol, chfsi_precision prec, int* choice,
+                                  double* ms_out);
+
+/* Candidate tile configurations: fills up to max (column tile, stages) pairs,
+ * returns their number. */
+int          chfsi_batch_candidates(const chfsi_batch* b, int* bn_out, int* stages_out, int max);
+
+/* ChFSI on every system: X[s] (device, binary64, M_s x n[s], in/out start
+ * block), bnd[s] the upper bound of spec(H~_s); per iteration the batched
+ * binary32 filter (filter_prec) followed, per system and concurrently, by
+ * CholGS and Rayleigh-Ritz in binary64 (orth_prec must be CHFSI_FP64).
+ * evals[s][n[s]] (host) receive the Ritz values. */
+chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* ldx, const int* n,
+                               int iters, int degree, const double* bnd,
+                               chfsi_precision filter_prec, chfsi_precision orth_prec,
+                               double* const* evals);
 
 #ifdef __cplusplus
 }

@@ -64,6 +64,18 @@ _SIGS = {
     "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
     "chfsi_last_timings": (C.c_int, [_vp, _dp]),
     "chfsi_kernel_launches": (_i64, []),
+    "chfsi_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp), _vp, C.POINTER(_vp)]),
+    "chfsi_batch_destroy": (C.c_int, [_vp]),
+    "chfsi_batch_last_error": (C.c_char_p, [_vp]),
+    "chfsi_batch_filter": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int), C.c_int,
+                                     _dp, _dp, _dp, C.c_int]),
+    "chfsi_batch_autotune": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int),
+                                       C.c_int, C.POINTER(C.c_int), _dp]),
+    "chfsi_batch_candidates": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    "chfsi_batch_solve": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int), C.c_int,
+                                    C.c_int, _dp, C.c_int, C.c_int, C.POINTER(_dp)]),
+    "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_kernel_timings": (C.c_int, [_vp, _dp]),
 }
 
 
@@ -257,7 +269,89 @@ class Context:
         px, ldx, n = _dev(X, pr)
         self._check(self._lib.chfsi_unscale(self._h, px, ldx, n, pr))
 
+    def set_kernel_timing(self, on=True):
+        self._check(self._lib.chfsi_set_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_timings(self) -> np.ndarray:
+        """[cell-product ms, assembly ms, cell launches, assembly launches] since the last call."""
+        out = np.zeros(4)
+        self._check(self._lib.chfsi_kernel_timings(self._h, _ptr(out)))
+        return out
+
     def last_timings(self) -> np.ndarray:
         out = np.zeros(4)
         self._check(self._lib.chfsi_last_timings(self._h, _ptr(out)))
         return out
+
+
+class Batch:
+    """Batched filtering / ChFSI of several built Contexts (chfsi_batch_*)."""
+
+    def __init__(self, contexts, stream=None):
+        lib = load()
+        self._lib = lib
+        self.contexts = list(contexts)
+        arr = (_vp * len(self.contexts))(*[c._h for c in self.contexts])
+        h = _vp()
+        s = _vp(stream.cuda_stream) if stream is not None else _vp(None)
+        st = lib.chfsi_batch_create(len(self.contexts), arr, s, C.byref(h))
+        if st != 0:
+            raise ChfsiError(st, "chfsi_batch_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise ChfsiError(st, self._lib.chfsi_batch_last_error(self._h).decode())
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.chfsi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _blocks(X, prec):
+        ptrs, lds, ncols = [], [], []
+        for x in X:
+            p, ld, n = _dev(x, prec)
+            ptrs.append(p)
+            lds.append(ld)
+            ncols.append(n)
+        k = len(X)
+        return (_vp * k)(*ptrs), (_i64 * k)(*lds), (C.c_int * k)(*ncols)
+
+    def filter(self, X, degree, a, b, a0, prec="mixed"):
+        pr = _prec(prec)
+        p, ld, n = self._blocks(X, pr)
+        a, b, a0 = _host(a), _host(b), _host(a0)
+        self._check(self._lib.chfsi_batch_filter(self._h, p, ld, n, int(degree), _ptr(a), _ptr(b),
+                                                 _ptr(a0), pr))
+
+    def candidates(self):
+        k = self._lib.chfsi_batch_candidates(self._h, None, None, 0)
+        bn, st = (C.c_int * k)(), (C.c_int * k)()
+        self._lib.chfsi_batch_candidates(self._h, bn, st, k)
+        return list(zip(list(bn), list(st)))
+
+    def autotune(self, X, prec="mixed"):
+        pr = _prec(prec)
+        p, ld, n = self._blocks(X, pr)
+        k = len(self.candidates())
+        ms = np.zeros(k)
+        choice = C.c_int(-1)
+        self._check(self._lib.chfsi_batch_autotune(self._h, p, ld, n, pr, C.byref(choice), _ptr(ms)))
+        return choice.value, ms
+
+    def solve(self, X, iters, degree, bounds, filter_prec="mixed"):
+        p, ld, n = self._blocks(X, FP64)
+        bnd = _host(bounds)
+        evs = [np.empty(x.shape[1]) for x in X]
+        earr = (_dp * len(X))(*[_ptr(e) for e in evs])
+        self._check(self._lib.chfsi_batch_solve(self._h, p, ld, n, int(iters), int(degree), _ptr(bnd),
+                                                _prec(filter_prec), FP64, earr))
+        return evs

@@ -2,6 +2,8 @@
 // device-memory management, the filter / CholGS / Rayleigh-Ritz drivers and
 // the ChFSI loop (step 7 of Algorithm scf in arXiv:1903.10959).
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,56 +12,49 @@
 
 #include <cusolverDn.h>
 
-#include "internal.h"
-#include "tc.h"
+#include "ctx.h"
 
 using namespace chfsi;
 
-#include <atomic>
-#include <mutex>
 namespace chfsi {
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace chfsi
 
-struct chfsi_ctx {
-  HostMesh mesh;
-  Wells wells;
-  Projectors proj;
-  HostProjectors hproj;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  bool built = false;
-  chfsi_status latched = CHFSI_OK;
-  std::string err;
-  int filter_block = 200, diag_block = 1;
-  int64_t dev_bytes = 0;
-  // resident device data
-  double* d_Ht = nullptr;          // binary64 cell matrices
-  TcCellData tc;                   // tensor-core copies (mixed precisions)
-  int32_t* d_dofmap = nullptr;
-  uint8_t* d_modes = nullptr;
-  int32_t* d_cells = nullptr;
-  double* d_mass = nullptr;
-  int32_t* d_node_ptr = nullptr;
-  int32_t* d_node_ent = nullptr;
-  int64_t* d_site_ptr = nullptr;
-  int32_t* d_site_dof = nullptr;
-  double* d_site_c = nullptr;
-  int64_t* d_dof_ptr = nullptr;
-  int32_t* d_dof_site = nullptr;
-  double* d_dof_c = nullptr;
-  float* d_site_c32 = nullptr;
-  float* d_dof_c32 = nullptr;
-  // grown scratch
-  DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
-  cusolverDnHandle_t sol = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  double times[4] = {0, 0, 0, 0};
-};
+
 
 namespace {
+
+cudaEvent_t kev_get(chfsi_ctx* ctx) {
+  if (!ctx->kev_free.empty()) {
+    cudaEvent_t e = ctx->kev_free.back();
+    ctx->kev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+// Event pair around one kernel launch (kind 0: cell products, 1: assembly).
+struct KTimer {
+  chfsi_ctx* ctx;
+  int kind;
+  cudaEvent_t a = nullptr;
+  KTimer(chfsi_ctx* c, int k) : ctx(c), kind(k) {
+    if (ctx->ktiming) {
+      a = kev_get(ctx);
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~KTimer() {
+    if (a) {
+      cudaEvent_t b = kev_get(ctx);
+      cudaEventRecord(b, ctx->stream);
+      ctx->krec.push_back({kind, a, b});
+    }
+  }
+};
 
 chfsi_status fail(chfsi_ctx* c, chfsi_status st, const std::string& msg) {
   if (c) {
@@ -184,6 +179,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
       L.ld_in = ld_in;
       L.ld_out = ld_out;
       L.ld_prev = ld_prev;
+      KTimer kt(ctx, 0);
       CK(launch_cell_fp64(L, (const double*)Yin, (double*)Yout, (const double*)Yprev,
                           (double*)ctx->Wb.ptr, nl ? (const double*)ctx->NLb.ptr : nullptr, B,
                           FilterStep{alpha, beta, shift}, ctx->stream));
@@ -216,7 +212,11 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.ld_in = ld_in;
   ra.R = (float*)ctx->Rb.ptr;
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
-  CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
+  {
+    KTimer kt(ctx, 0);
+    CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
+  }
+  KTimer kt(ctx, 1);
   CK(tc_assemble_launch(ctx->d_node_ptr, ctx->d_node_ent, m.ndofs, ncol, (const float*)ctx->Rb.ptr,
                         (const float*)Yin, ld_in, (float*)Yout, ld_out,
                         beta != 0.0 ? (const float*)Yprev : nullptr, ld_prev,
@@ -568,6 +568,11 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& r : ctx->krec) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->kev_free) cudaEventDestroy(e);
   delete ctx;
   return CHFSI_OK;
 }
@@ -579,6 +584,34 @@ int64_t chfsi_num_dofs(const chfsi_ctx* ctx) { return ctx ? ctx->mesh.ndofs : -1
 int64_t chfsi_device_bytes(const chfsi_ctx* ctx) { return ctx ? ctx->dev_bytes : -1; }
 
 int64_t chfsi_kernel_launches(void) { return launch_count(); }
+
+chfsi_status chfsi_set_kernel_timing(chfsi_ctx* ctx, int on) {
+  CHECK_CTX();
+  ctx->ktiming = on != 0;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out4) {
+  CHECK_CTX();
+  if (!out4) return CHFSI_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& r : ctx->krec) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    ctx->kms[r.kind] += ms;
+    ctx->kcount[r.kind] += 1;
+    ctx->kev_free.push_back(r.a);
+    ctx->kev_free.push_back(r.b);
+  }
+  ctx->krec.clear();
+  out4[0] = ctx->kms[0];
+  out4[1] = ctx->kms[1];
+  out4[2] = (double)ctx->kcount[0];
+  out4[3] = (double)ctx->kcount[1];
+  ctx->kms[0] = ctx->kms[1] = 0.0;
+  ctx->kcount[0] = ctx->kcount[1] = 0;
+  return CHFSI_OK;
+}
 
 chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out) {
   CHECK_CTX();

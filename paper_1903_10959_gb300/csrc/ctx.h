@@ -1,0 +1,56 @@
+// Private definition of the library context (shared by api.cu and batch.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cusolverDn.h>
+
+#include "internal.h"
+#include "tc.h"
+
+struct chfsi_ctx {
+  chfsi::HostMesh mesh;
+  chfsi::Wells wells;
+  chfsi::Projectors proj;
+  chfsi::HostProjectors hproj;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool built = false;
+  chfsi_status latched = CHFSI_OK;
+  std::string err;
+  int filter_block = 200, diag_block = 1;
+  int64_t dev_bytes = 0;
+  // resident device data
+  double* d_Ht = nullptr;          // binary64 cell matrices
+  chfsi::TcCellData tc;                   // tensor-core copies (mixed precisions)
+  int32_t* d_dofmap = nullptr;
+  uint8_t* d_modes = nullptr;
+  int32_t* d_cells = nullptr;
+  double* d_mass = nullptr;
+  int32_t* d_node_ptr = nullptr;
+  int32_t* d_node_ent = nullptr;
+  int64_t* d_site_ptr = nullptr;
+  int32_t* d_site_dof = nullptr;
+  double* d_site_c = nullptr;
+  int64_t* d_dof_ptr = nullptr;
+  int32_t* d_dof_site = nullptr;
+  double* d_dof_c = nullptr;
+  float* d_site_c32 = nullptr;
+  float* d_dof_c32 = nullptr;
+  // grown scratch
+  chfsi::DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
+  cusolverDnHandle_t sol = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double times[4] = {0, 0, 0, 0};
+  // optional per-launch event timing of the filter kernels
+  bool ktiming = false;
+  std::vector<cudaEvent_t> kev_free;
+  struct KRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<KRec> krec;
+  double kms[2] = {0, 0};
+  int64_t kcount[2] = {0, 0};
+};

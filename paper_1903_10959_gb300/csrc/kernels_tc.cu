@@ -9,12 +9,14 @@
 // binary32.  Diagonal blocks of the overlap / projected matrices and of the
 // CholGS factor are evaluated in binary64 (the paper's S_d and L^{-1}_d).
 //
-//  tc_cell      : one colour of the cell-by-cell H~ Y (Sec. 3.3.1) fused with
-//                 the Chebyshev update (Eq. chebFilter).  One CTA per
-//                 (cell, 64-column tile); warp-specialised: warp 4 streams
-//                 the pre-split cell matrix with bulk async copies, warps 0-3
-//                 gather + split the cell block of Y into shared memory and
-//                 later run the colour-mode epilogue, warp 5 issues the MMAs.
+//  tc_cell_r    : the cell-by-cell products H~_e Y_e of Sec. 3.3.1 for all
+//                 cells in one launch, one CTA per (cell, 64-column tile);
+//                 warp-specialised: warp 4 streams the pre-split cell matrix
+//                 with bulk async copies, warps 0-3 gather + split the cell
+//                 block of Y into shared memory and later store the result
+//                 block, warp 5 issues the MMAs.
+//  tc_assemble  : owner-computes sum of the cell blocks per unknown fused with
+//                 the Chebyshev three-term update (Eq. chebFilter).
 //  tc_gram      : lower tiles of A^T B over the unknowns (Algorithm CholGS
 //                 step 1; H^ of Sec. 3.5), split-K, fixed-order reduction.
 //  tc_tallgemm  : X U (Algorithm CholGS step 4, subspace rotation of Sec. 3.5).
@@ -124,295 +126,14 @@ __host__ __device__ inline CellSmem cell_smem(int mt, int split3) {
   return c;
 }
 
-struct CellParams {
-  const float* A;          // packed cell matrices
-  const int32_t* cells;
-  const int32_t* dofmap;
-  const uint8_t* modes;
-  const float* Yin;
-  float* Yout;
-  const float* Yprev;
-  float* W;
-  const float* NL;
-  int64_t ld_in, ld_out, ld_prev, ld_w;
-  int ncol, ne, mt, nk, split3;
-  int cl;                  // thread-block cluster size along the column tiles (1, 2 or 4)
-  int64_t ncells;          // cells of this colour (persistent kernel)
-  float alpha, beta, shift;
-};
-
-// With cl > 1 the cl CTAs of one cell (consecutive column tiles) form a
-// cluster: the leader (rank 0) streams each cell-matrix chunk once and the
-// bulk copy is multicast into every member's stage buffer; each member's MMA
-// commit arrives on the empty barrier of every member, so a stage is reused
-// only after the whole cluster has consumed it.
-__global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_kernel(CellParams P) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t e = P.cells[blockIdx.y];
-  const int c0 = blockIdx.x * CELL_BN;
-  const int ncv = min(CELL_BN, P.ncol - c0);
-  const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;   // MMA N
-  const CellSmem L = cell_smem(P.mt, P.split3);
-  const int S = L.stages;
-  const int stage_bytes = L.a_bytes + L.y_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
-  // bars: fa[S] (tx), fy[S] (32 arrivals: one gather warp), em[S] (MMA commit), acc (1)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  int32_t* dm = reinterpret_cast<int32_t*>(smem + S * stage_bytes + 256);
-  uint8_t* md = reinterpret_cast<uint8_t*>(dm + 512);
-  const uint32_t sbase = smem_u32(smem);
-  auto fa = [&](int s) { return smem_u32(bars + s); };
-  auto fy = [&](int s) { return smem_u32(bars + S + s); };
-  auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
-  const uint32_t accb = smem_u32(bars + 3 * S);
-  const uint32_t tmem_cols = P.mt == 1 ? 64 : (P.mt == 2 ? 128 : 256);
-  const uint32_t crank = P.cl > 1 ? cluster_ctarank() : 0;
-  const uint16_t cmask = (uint16_t)((1u << P.cl) - 1u);
-
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(fa(s), 1);
-      mbar_init(fy(s), 32);
-      mbar_init(em(s), P.cl);
-    }
-    mbar_init(accb, 1);
-    *abort_flag = 0;
-    fence_mbar_init();
-  }
-  if (warp == 5) {
-    tmem_alloc(smem_u32(tmem_slot), tmem_cols);
-    tmem_relinquish();
-  }
-  for (int l = tid; l < P.ne; l += CELL_THREADS) {
-    dm[l] = P.dofmap[e * P.ne + l];
-    md[l] = P.modes[e * P.ne + l];
-  }
-  tc_fence_before();
-  __syncwarp();
-  if (P.cl > 1) cluster_sync();   // every member's barriers exist before the first multicast
-  else __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const int nk = P.nk;
-
-  if (warp == 4) {
-    // ---------------- producer of the cell-matrix chunks (bulk async copies)
-    if (lane == 0) {
-      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * P.mt * 8192;
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % S;
-        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
-          atomicExch(&g_tc_status, 1);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        if (*(volatile int*)abort_flag) break;
-        mbar_arrive_expect_tx(fa(s), L.a_bytes);
-        if (P.cl == 1)
-          bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes, fa(s));
-        else if (crank == 0)
-          bulk_g2s_multicast(sbase + s * stage_bytes, Ae + (int64_t)i * P.mt * 8192, L.a_bytes,
-                             fa(s), cmask);
-        ++issued;
-      }
-      if (*(volatile int*)abort_flag) {   // let the copies still in flight land before exit
-        for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(fa(i % S), (i / S) & 1);
-      } else if (P.cl > 1) {
-        // the peers' commits of the last chunks arrive on this CTA's empty
-        // barriers: see them all before the CTA may leave the cluster
-        for (int i = max(0, nk - S); i < nk; ++i) mbar_wait(em(i % S), (i / S) & 1);
-      }
-    }
-  } else if (warp == 5) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(128, bne);
-      bool ok = true;
-      for (int i = 0; i < nk && ok; ++i) {
-        const int s = i % S;
-        ok = mbar_wait(fa(s), (i / S) & 1) && mbar_wait(fy(s), (i / S) & 1);
-        if (!ok || *(volatile int*)abort_flag) {
-          if (!ok) atomicExch(&g_tc_status, 2);
-          *(volatile int*)abort_flag = 1;
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t sa = sbase + s * stage_bytes;
-        const uint32_t sy = sa + L.a_bytes;
-        const uint64_t yhi = umma_desc(sy, 128, 256);
-        const uint64_t ylo = umma_desc(sy + CELL_BN * CELL_KC * 4, 128, 256);
-        for (int t = 0; t < P.mt; ++t) {
-          const uint32_t d = tmem + t * CELL_BN;
-          const uint64_t ahi = umma_desc(sa + t * 4096, 128, 256);
-          if (P.split3) {
-            const uint64_t alo = umma_desc(sa + P.mt * 4096 + t * 4096, 128, 256);
-            mma_tf32(d, alo, yhi, idesc, i > 0);
-            mma_tf32(d, ahi, ylo, idesc, 1);
-            mma_tf32(d, ahi, yhi, idesc, 1);
-          } else {
-            mma_tf32(d, ahi, yhi, idesc, i > 0);
-          }
-        }
-        if (P.cl > 1) umma_commit_multicast(em(s), cmask);
-        else umma_commit(em(s));
-      }
-      umma_commit(accb);   // arrives once all issued MMAs are done (also on abort)
-    }
-  } else {
-    // ---------------- warps 0-3: gather + split the cell block of Y
-    // Warp w produces the chunks i = w, w + G, ... (G = min(4, S)) so up to four
-    // chunks are in flight per CTA.  Lane (q, cq) loads 4 nodes (4q..4q+3) x 4 columns (4cq..4cq+3)
-    // with 16-byte loads and writes, per column, the 4 consecutive K values as
-    // one 16-byte store of hi and one of lo (K-major core-matrix layout).
-    // hi = tf32(x) (nearest); lo = x - hi is exact and the MMA truncates it.
-    // A warp waits on the empty barrier of chunk i - S after having seen chunk
-    // i - G - S consumed on its previous turn; a parity wait is only sound when
-    // the barrier is at most one phase behind, i.e. when G <= S.
-    const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
-    const int q = lane >> 4;           // node quad within the chunk (0..1)
-    const int cq = (lane & 15) * 4;    // first of 4 columns
-    const int G = S < 4 ? S : 4;       // gather warps in use
-    for (int i = warp; i < nk && warp < G; i += G) {
-      const int s = i % S;
-      float v[4][4];                   // [node][column]
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int l = i * CELL_KC + q * 4 + a;
-        const int g = l < P.ne ? dm[l] : -1;
-        v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
-        if (g >= 0) {
-          const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
-          if (vec && cq + 4 <= ncv) {
-            const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
-            v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (cq + u < ncv) v[a][u] = __ldg(src + u);
-          }
-        }
-      }
-      if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
-        atomicExch(&g_tc_status, 3);
-        *(volatile int*)abort_flag = 1;
-      }
-      if (*(volatile int*)abort_flag) break;
-      float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
-      float* yl = yh + CELL_BN * CELL_KC;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int n = cq + u;
-        const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
-        float4 h, lo;
-        h.x = tf32_rna(v[0][u]); lo.x = v[0][u] - h.x;
-        h.y = tf32_rna(v[1][u]); lo.y = v[1][u] - h.y;
-        h.z = tf32_rna(v[2][u]); lo.z = v[2][u] - h.z;
-        h.w = tf32_rna(v[3][u]); lo.w = v[3][u] - h.w;
-        *reinterpret_cast<float4*>(yh + o) = h;
-        *reinterpret_cast<float4*>(yl + o) = lo;
-      }
-      fence_proxy_async_smem();
-      mbar_arrive(fy(s));
-    }
-    // ---------------- epilogue: TMEM -> shared tile -> row-wise colour-mode update
-    // The stage buffers are free once every MMA has completed; a 128 x 64 tile
-    // of the result is staged there so that each warp then walks whole rows
-    // (one unknown, warp-uniform mode) with lanes over consecutive columns.
-    const bool okacc = mbar_wait(accb, 0);
-    if (!okacc) {
-      atomicExch(&g_tc_status, 4);
-      *(volatile int*)abort_flag = 1;
-    }
-    tc_fence_after();
-    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
-    float* E = reinterpret_cast<float*>(smem);
-    constexpr int EP = CELL_BN + 1;
-    for (int t = 0; t < P.mt; ++t) {
-      __syncwarp();   // tcgen05.ld and bar.sync are warp-aligned: reconverge first
-      if (run) {
-        for (int cb = 0; cb < bne; cb += 16) {
-          float acc[16];
-          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CELL_BN + cb, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int u = 0; u < 16; ++u) E[(warp * 32 + lane) * EP + cb + u] = acc[u];
-        }
-      }
-      __syncwarp();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (run) {
-        // rows r = warp + 4 j; batches of RB rows: every global load of the
-        // batch is issued before any is used (memory-level parallelism)
-        constexpr int RB = 8;
-        for (int j0 = 0; j0 < 32; j0 += RB) {
-          float wv[RB][2], yv[RB][2], pv[RB][2], nv[RB][2];
-          int gg[RB], mm[RB];
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int r = warp + 4 * (j0 + b);
-            const int l = t * 128 + r;
-            gg[b] = l < P.ne ? dm[l] : -1;
-            mm[b] = l < P.ne ? md[l] : MODE_SKIP;
-            if (gg[b] < 0) mm[b] = MODE_SKIP;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int c = lane + 32 * h;
-              wv[b][h] = yv[b][h] = pv[b][h] = nv[b][h] = 0.f;
-              if (mm[b] == MODE_SKIP || c >= ncv) continue;
-              const int64_t g = gg[b];
-              if (mm[b] == MODE_ACCUM || mm[b] == MODE_FINAL) wv[b][h] = P.W[g * P.ld_w + c0 + c];
-              if (mm[b] == MODE_FINAL || mm[b] == MODE_FINAL_DIRECT) {
-                yv[b][h] = P.Yin[g * P.ld_in + c0 + c];
-                if (P.Yprev) pv[b][h] = P.Yprev[g * P.ld_prev + c0 + c];
-                if (P.NL) nv[b][h] = P.NL[g * P.ld_w + c0 + c];
-              }
-            }
-          }
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const int r = warp + 4 * (j0 + b);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int c = lane + 32 * h;
-              if (mm[b] == MODE_SKIP || c >= ncv) continue;
-              const int64_t g = gg[b];
-              const float vv = E[r * EP + c];
-              if (mm[b] == MODE_STORE) {
-                P.W[g * P.ld_w + c0 + c] = vv;
-              } else if (mm[b] == MODE_ACCUM) {
-                P.W[g * P.ld_w + c0 + c] = wv[b][h] + vv;
-              } else {
-                const float tot = (mm[b] == MODE_FINAL ? wv[b][h] + vv : vv) + nv[b][h];
-                float out = P.alpha * (tot - P.shift * yv[b][h]);
-                if (P.Yprev) out = fmaf(P.beta, pv[b][h], out);
-                P.Yout[g * P.ld_out + c0 + c] = out;
-              }
-            }
-          }
-        }
-      }
-      __syncwarp();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-    }
-  }
-  tc_fence_before();
-  __syncwarp();
-  if (P.cl > 1) cluster_sync();   // no member leaves while peers may still signal it
-  else __syncthreads();
-  if (warp == 5) tmem_dealloc(tmem, tmem_cols);
-}
-
 // ----------------------------------------------------------------- owner-computes cell kernel
-// One CTA per (cell, 64-column tile) over ALL cells (no colour phases): the
-// same warp-specialised mainloop as tc_cell_kernel (warp 4 streams the split
-// cell matrix, warps 0-3 gather + split Y, warp 5 issues the MMAs), but the
-// epilogue only stores the dense cell block R_e = H~_e Y_e with 16-byte
-// stores (no loads), so it never stalls on memory latency.  The assembly over
-// cells and the Chebyshev update follow in tc_assemble_kernel.
+// One CTA per (cell, 64-column tile) over ALL cells (no colour phases).
+// Warp 4 streams the split cell matrix in K-chunks of 8 with bulk async
+// copies, warps 0-3 gather + split the cell block of Y, warp 5 issues the
+// MMAs into TMEM (one 64-column accumulator per 128-row tile); the epilogue
+// only stores the dense cell block R_e = H~_e Y_e with 16-byte stores (no
+// loads), so it never stalls on memory latency.  The assembly over cells and
+// the Chebyshev update follow in tc_assemble_kernel.
 struct RParams {
   const float* A;
   const int32_t* dofmap;
@@ -667,391 +388,6 @@ cudaError_t tc_assemble_launch(const int32_t* node_ptr, const int32_t* node_ent,
       node_ptr, node_ent, M, ncol, R, Yin, ld_in, Yout, ld_out, Yprev, ld_prev, NL, ld_nl, alpha,
       beta, shift, vec);
   return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------- persistent cell kernel
-// One CTA per SM loops over the (cell, 64-column tile) items of a colour.
-// Warp roles: 0 streams the cell-matrix chunks (bulk async copies), 1 issues
-// the MMAs and owns TMEM, 2-5 gather + split the cell blocks of Y (two-deep
-// register prefetch), 6-9 run the epilogue.  The accumulator is double
-// buffered in TMEM, so the epilogue of item k overlaps the MMAs of item k+1.
-constexpr int PC_THREADS = 320;
-
-struct PcSmem {
-  int S, a_bytes, y_bytes, stage, e_off, dm_off, bar_off, total;
-};
-
-__host__ __device__ inline PcSmem pc_smem(int mt, int split3) {
-  PcSmem c;
-  c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
-  c.y_bytes = CELL_BN * CELL_KC * 4 * 2;
-  c.stage = c.a_bytes + c.y_bytes;
-  const int e_bytes = 128 * (CELL_BN + 1) * 4;
-  int S = (226 * 1024 - e_bytes - 2560 - 512) / c.stage;
-  S = S < 4 ? 4 : (S > 8 ? 8 : S);   // >= 4: the four gather warps' parity waits
-  c.S = S;
-  c.e_off = S * c.stage;
-  c.dm_off = c.e_off + e_bytes;
-  c.bar_off = c.dm_off + 2560;
-  c.total = c.bar_off + 512;
-  return c;
-}
-
-__global__ void __launch_bounds__(PC_THREADS, 1) tc_cell_persistent_kernel(CellParams P) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const PcSmem L = pc_smem(P.mt, P.split3);
-  const int S = L.S;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* E = reinterpret_cast<float*>(smem + L.e_off);
-  int32_t* dms = reinterpret_cast<int32_t*>(smem + L.dm_off);
-  uint8_t* mds = reinterpret_cast<uint8_t*>(dms + 512);
-  const uint32_t sbase = smem_u32(smem);
-  auto fa = [&](int s) { return smem_u32(bars + s); };
-  auto fy = [&](int s) { return smem_u32(bars + S + s); };
-  auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
-  auto accf = [&](int b) { return smem_u32(bars + 3 * S + b); };
-  auto acce = [&](int b) { return smem_u32(bars + 3 * S + 2 + b); };
-  const int mt = P.mt, nk = P.nk, ne = P.ne;
-  const uint32_t acc_cols = (uint32_t)(mt * CELL_BN);          // one accumulator buffer
-  const uint32_t tmem_cols = 2 * acc_cols <= 128 ? 128 : (2 * acc_cols <= 256 ? 256 : 512);
-  const int ntiles = (P.ncol + CELL_BN - 1) / CELL_BN;
-  const int64_t nitems = P.ncells * ntiles;
-  const int64_t my_items = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(fa(s), 1);
-      mbar_init(fy(s), 32);
-      mbar_init(em(s), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(accf(b), 1);
-      mbar_init(acce(b), 128);
-    }
-    *abort_flag = 0;
-    fence_mbar_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), tmem_cols);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  auto item_of = [&](int64_t it) { return (int64_t)blockIdx.x + it * gridDim.x; };
-
-  if (warp == 0) {
-    // ---------------- cell-matrix chunks
-    if (lane == 0) {
-      int64_t gi = 0, issued = 0;
-      for (int64_t it = 0; it < my_items && !*(volatile int*)abort_flag; ++it) {
-        const int64_t e = P.cells[item_of(it) / ntiles];
-        const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * mt * 8192;
-        for (int i = 0; i < nk; ++i, ++gi) {
-          const int s = (int)(gi % S);
-          if (gi >= S && !mbar_wait(em(s), (uint32_t)((gi / S) - 1) & 1)) {
-            atomicExch(&g_tc_status, 11);
-            *(volatile int*)abort_flag = 1;
-            break;
-          }
-          mbar_arrive_expect_tx(fa(s), L.a_bytes);
-          bulk_g2s(sbase + s * L.stage, Ae + (int64_t)i * mt * 8192, L.a_bytes, fa(s));
-          ++issued;
-        }
-      }
-      if (*(volatile int*)abort_flag)
-        for (int64_t i = issued > S ? issued - S : 0; i < issued; ++i)
-          mbar_wait(fa((int)(i % S)), (uint32_t)(i / S) & 1);
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      int64_t gi = 0;
-      bool ok = true;
-      for (int64_t it = 0; it < my_items && ok; ++it) {
-        const int b = (int)(it & 1);
-        if (it >= 2 && !mbar_wait(acce(b), (uint32_t)((it / 2) - 1) & 1)) {
-          atomicExch(&g_tc_status, 12);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        tc_fence_after();
-        const int c0 = (int)(item_of(it) % ntiles) * CELL_BN;
-        const int ncv = min(CELL_BN, P.ncol - c0);
-        const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
-        const uint32_t idesc = idesc_tf32(128, bne);
-        const uint32_t dbase = tmem + b * acc_cols;
-        for (int i = 0; i < nk; ++i, ++gi) {
-          const int s = (int)(gi % S);
-          const uint32_t par = (uint32_t)(gi / S) & 1;
-          if (!mbar_wait(fa(s), par) || !mbar_wait(fy(s), par) || *(volatile int*)abort_flag) {
-            atomicExch(&g_tc_status, 13);
-            *(volatile int*)abort_flag = 1;
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = sbase + s * L.stage;
-          const uint32_t sy = sa + L.a_bytes;
-          const uint64_t yhi = umma_desc(sy, 128, 256);
-          const uint64_t ylo = umma_desc(sy + CELL_BN * CELL_KC * 4, 128, 256);
-          for (int t = 0; t < mt; ++t) {
-            const uint32_t d = dbase + t * CELL_BN;
-            const uint64_t ahi = umma_desc(sa + t * 4096, 128, 256);
-            if (P.split3) {
-              const uint64_t alo = umma_desc(sa + mt * 4096 + t * 4096, 128, 256);
-              mma_tf32(d, alo, yhi, idesc, i > 0);
-              mma_tf32(d, ahi, ylo, idesc, 1);
-              mma_tf32(d, ahi, yhi, idesc, 1);
-            } else {
-              mma_tf32(d, ahi, yhi, idesc, i > 0);
-            }
-          }
-          umma_commit(em(s));
-        }
-        umma_commit(accf(b));
-      }
-    }
-  } else if (warp <= 5) {
-    // ---------------- gather + split of the cell blocks of Y
-    // Warp g takes global chunk indices g, g + 4, ...; the loads of its next
-    // chunk are issued before the current one is stored (two chunks in flight).
-    const int gw = warp - 2;
-    const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
-    const int q = lane >> 4;
-    const int cq = (lane & 15) * 4;
-    const int64_t total = my_items * nk;
-    auto load_chunk = [&](int64_t gi, float v[4][4]) {
-      const int64_t it = gi / nk;
-      const int i = (int)(gi - it * nk);
-      const int64_t item = item_of(it);
-      const int64_t e = P.cells[item / ntiles];
-      const int c0 = (int)(item % ntiles) * CELL_BN;
-      const int ncv = min(CELL_BN, P.ncol - c0);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int l = i * CELL_KC + q * 4 + a;
-        const int g = l < ne ? P.dofmap[e * ne + l] : -1;
-        v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
-        if (g >= 0) {
-          const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
-          if (vec && cq + 4 <= ncv) {
-            const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
-            v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (cq + u < ncv) v[a][u] = __ldg(src + u);
-          }
-        }
-      }
-    };
-    float va[4][4], vb[4][4];
-    if (gw < total) load_chunk(gw, va);
-    for (int64_t gi = gw; gi < total; gi += 4) {
-      const bool more = gi + 4 < total;
-      if (more) load_chunk(gi + 4, vb);
-      const int s = (int)(gi % S);
-      if (gi >= S && !mbar_wait(em(s), (uint32_t)((gi / S) - 1) & 1)) {
-        atomicExch(&g_tc_status, 14);
-        *(volatile int*)abort_flag = 1;
-      }
-      if (*(volatile int*)abort_flag) break;
-      float* yh = reinterpret_cast<float*>(smem + s * L.stage + L.a_bytes);
-      float* yl = yh + CELL_BN * CELL_KC;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int n = cq + u;
-        const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
-        float4 h, lo;
-        h.x = tf32_rna(va[0][u]); lo.x = va[0][u] - h.x;
-        h.y = tf32_rna(va[1][u]); lo.y = va[1][u] - h.y;
-        h.z = tf32_rna(va[2][u]); lo.z = va[2][u] - h.z;
-        h.w = tf32_rna(va[3][u]); lo.w = va[3][u] - h.w;
-        *reinterpret_cast<float4*>(yh + o) = h;
-        *reinterpret_cast<float4*>(yl + o) = lo;
-      }
-      fence_proxy_async_smem();
-      mbar_arrive(fy(s));
-      if (more) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) va[a][u] = vb[a][u];
-      }
-    }
-  } else {
-    // ---------------- epilogue (warps 6-9; TMEM lane quadrant = warp % 4)
-    const int qd = warp & 3;
-    const int ew = warp - 6;
-    const int et = tid - 6 * 32;           // 0..127
-    constexpr int EP = CELL_BN + 1;
-    for (int64_t it = 0; it < my_items; ++it) {
-      const int b = (int)(it & 1);
-      const int64_t item = item_of(it);
-      const int64_t e = P.cells[item / ntiles];
-      const int c0 = (int)(item % ntiles) * CELL_BN;
-      const int ncv = min(CELL_BN, P.ncol - c0);
-      const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
-      for (int l = et; l < ne; l += 128) {   // dof map and modes of this cell
-        dms[l] = P.dofmap[e * ne + l];
-        mds[l] = P.modes[e * ne + l];
-      }
-      const bool okw = !*(volatile int*)abort_flag && mbar_wait(accf(b), (uint32_t)(it / 2) & 1);
-      if (!okw) {
-        atomicExch(&g_tc_status, 15);
-        *(volatile int*)abort_flag = 1;
-      }
-      tc_fence_after();
-      const bool run = __all_sync(0xffffffffu, okw);
-      for (int t = 0; t < mt; ++t) {
-        __syncwarp();
-        if (run) {
-          for (int cb = 0; cb < bne; cb += 16) {
-            float acc[16];
-            tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + b * acc_cols + t * CELL_BN + cb, acc);
-            tmem_wait_ld();
-#pragma unroll
-            for (int u = 0; u < 16; ++u) E[(qd * 32 + lane) * EP + cb + u] = acc[u];
-          }
-        }
-        if (t == mt - 1) {   // all TMEM reads of this item done: free the buffer
-          tc_fence_before();
-          mbar_arrive(acce(b));
-        }
-        __syncwarp();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (run) {
-          constexpr int RB = 8;
-          for (int j0 = 0; j0 < 32; j0 += RB) {
-            float wv[RB][2], yv[RB][2], pv[RB][2], nv[RB][2];
-            int gg[RB], mm[RB];
-#pragma unroll
-            for (int bb = 0; bb < RB; ++bb) {
-              const int r = ew + 4 * (j0 + bb);
-              const int l = t * 128 + r;
-              gg[bb] = l < ne ? dms[l] : -1;
-              mm[bb] = l < ne ? mds[l] : MODE_SKIP;
-              if (gg[bb] < 0) mm[bb] = MODE_SKIP;
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;
-                wv[bb][h] = yv[bb][h] = pv[bb][h] = nv[bb][h] = 0.f;
-                if (mm[bb] == MODE_SKIP || c >= ncv) continue;
-                const int64_t g = gg[bb];
-                if (mm[bb] == MODE_ACCUM || mm[bb] == MODE_FINAL) wv[bb][h] = P.W[g * P.ld_w + c0 + c];
-                if (mm[bb] == MODE_FINAL || mm[bb] == MODE_FINAL_DIRECT) {
-                  yv[bb][h] = P.Yin[g * P.ld_in + c0 + c];
-                  if (P.Yprev) pv[bb][h] = P.Yprev[g * P.ld_prev + c0 + c];
-                  if (P.NL) nv[bb][h] = P.NL[g * P.ld_w + c0 + c];
-                }
-              }
-            }
-#pragma unroll
-            for (int bb = 0; bb < RB; ++bb) {
-              const int r = ew + 4 * (j0 + bb);
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;
-                if (mm[bb] == MODE_SKIP || c >= ncv) continue;
-                const int64_t g = gg[bb];
-                const float vv = E[r * EP + c];
-                if (mm[bb] == MODE_STORE) {
-                  P.W[g * P.ld_w + c0 + c] = vv;
-                } else if (mm[bb] == MODE_ACCUM) {
-                  P.W[g * P.ld_w + c0 + c] = wv[bb][h] + vv;
-                } else {
-                  const float tot = (mm[bb] == MODE_FINAL ? wv[bb][h] + vv : vv) + nv[bb][h];
-                  float out = P.alpha * (tot - P.shift * yv[bb][h]);
-                  if (P.Yprev) out = fmaf(P.beta, pv[bb][h], out);
-                  P.Yout[g * P.ld_out + c0 + c] = out;
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, tmem_cols);
-}
-
-cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_t s) {
-  if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
-  if (!d.hi) return cudaErrorInvalidValue;
-  CellParams P;
-  P.A = d.hi;
-  P.cells = a.cells;
-  P.dofmap = a.dofmap;
-  P.modes = a.modes;
-  P.Yin = a.Yin;
-  P.Yout = a.Yout;
-  P.Yprev = a.Yprev;
-  P.W = a.W;
-  P.NL = a.NL;
-  P.ld_in = a.ld_in;
-  P.ld_out = a.ld_out;
-  P.ld_prev = a.ld_prev;
-  P.ld_w = a.ld_w;
-  P.ncol = a.ncol;
-  P.ne = d.ne;
-  P.mt = d.mt;
-  P.nk = d.kt / CELL_KC;
-  P.split3 = a.split3;
-  P.alpha = a.alpha;
-  P.beta = a.beta;
-  P.shift = a.shift;
-  const CellSmem L = cell_smem(d.mt, a.split3);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  const int tiles = (a.ncol + CELL_BN - 1) / CELL_BN;
-  P.ncells = a.ncells;
-  const PcSmem Q = pc_smem(d.mt, a.split3);
-  if (d.mt <= 4 && Q.total <= 227 * 1024 && !getenv("CHFSI_CELL_NONPERSISTENT")) {
-    static bool pattr = false;
-    static int nsm = 0;
-    if (!pattr) {
-      cudaFuncSetAttribute(tc_cell_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024);
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      pattr = true;
-    }
-    P.cl = 1;
-    const int64_t nitems = a.ncells * tiles;
-    const int grid = (int)std::min<int64_t>(nitems, nsm);
-    note_launch();
-    tc_cell_persistent_kernel<<<grid, PC_THREADS, Q.total, s>>>(P);
-    return cudaGetLastError();
-  }
-  int cl = tiles >= 4 ? 4 : (tiles >= 2 ? 2 : 1);
-  P.cl = cl;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((tiles + cl - 1) / cl * cl, (unsigned)a.ncells);
-  cfg.blockDim = dim3(CELL_THREADS);
-  cfg.dynamicSmemBytes = L.total;
-  cfg.stream = s;
-  cudaLaunchAttribute attrs[1];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = cl;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
-  cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  note_launch();
-  return cudaLaunchKernelEx(&cfg, tc_cell_kernel, P);
 }
 
 int tc_read_status(cudaStream_t s) {

@@ -17,25 +17,6 @@ struct TcCellData {
   int ne = 0, mt = 0, kt = 0;   // ne, row tiles of 128, K padded to a multiple of 8
 };
 
-struct TcCellArgs {
-  const int32_t* cells;
-  int64_t ncells;
-  const int32_t* dofmap;
-  const uint8_t* modes;
-  int ncol;
-  const float* Yin;
-  int64_t ld_in;
-  float* Yout;
-  int64_t ld_out;
-  const float* Yprev;
-  int64_t ld_prev;
-  float* W;
-  const float* NL;
-  int64_t ld_w;
-  float alpha, beta, shift;
-  int split3;
-};
-
 // Owner-computes form of one H~ Y step (no colouring): every cell writes its
 // dense block R_e = H~_e Y_e (ne x ncol rows at R[(e * ne + l) * ncol]) with
 // plain stores, then each unknown sums its 1..8 cell rows in ascending cell
@@ -65,7 +46,6 @@ cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s
 int tc_read_status(cudaStream_t s);
 size_t tc_tallgemm_work_bytes(int n1, int n2);
 void tc_free(TcCellData& d);
-cudaError_t tc_cell_launch(const TcCellData& d, const TcCellArgs& a, cudaStream_t s);
 size_t tc_gram_partial_bytes(int64_t M, int n1, int n2);
 cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
                           int n1, int n2, double* C, int64_t ldc, int lower, int diag_block,
