@@ -44,6 +44,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
+    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "serving"],
+                    help="serving: request stream through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=12, help="serving: number of requests")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrently admitted requests")
+    ap.add_argument("--dof-max", type=float, default=2.0e6, help="serving: largest request (unknowns)")
+    ap.add_argument("--fp64-requests", type=int, default=4,
+                    help="serving: requests (smallest first) of the FP64 comparison")
+    ap.add_argument("--rates", default="0.5,0.8,1.0",
+                    help="serving: arrival rates as fractions of the measured mixed capacity")
     return ap.parse_args()
 
 
@@ -368,8 +377,120 @@ def run_ours(args):
     ctx.destroy()
 
 
+# ------------------------------------------------------------------ serving
+SERVE_DEGREE, SERVE_ITERS, SERVE_WARM, SERVE_TOL = 30, 20, 6, 1.0e-5
+
+
+def serve_stream(reqs, prec, slots, arrivals=None, budget=150 << 30):
+    """Submit the requests (at the arrival times, seconds from now, or all at
+    once) to a fresh server and wait for all; per-request results + makespan."""
+    import threading
+    from paper_1903_10959_gb300 import Server
+    with Server(budget, slots) as sv:
+        tickets = [None] * len(reqs)
+        t_sub = [0.0] * len(reqs)
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, (s, seq) in enumerate(reqs):
+                if arrivals is not None:
+                    dt = t0 + arrivals[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                t_sub[i] = time.perf_counter()
+                tickets[i] = sv.submit(((s.ncell,) * 3, (s.L,) * 3, s.p, True), s.n_sub, s.centres,
+                                       s.depths, s.widths, depth_seq=seq, degree=SERVE_DEGREE,
+                                       iters=SERVE_ITERS, warm_iters=SERVE_WARM, tol=SERVE_TOL,
+                                       n_check=s.n_want, prec=prec, seed=s.seed)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        res = [sv.poll(t, wait=True) for t in tickets]
+        t_end = max(ts + r["total_ms"] * 1e-3 for ts, r in zip(t_sub, res))
+    return res, t_end - t0
+
+
+def serve_summary(res, makespan):
+    ok = [r for r in res if r["status"] == 0]
+    nsolves = sum(r["nsolves"] for r in ok)
+    first = np.array([r["first_ms"] for r in ok])
+    total = np.array([r["total_ms"] for r in ok])
+    resolve = np.array([x for r in ok for x in r["solve_ms"][1:]])
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None  # noqa: E731
+    return {"requests": len(res), "failed": len(res) - len(ok), "solves": nsolves,
+            "makespan_s": makespan, "solves_per_s": nsolves / makespan,
+            "first_solve_ms_p50": pct(first, 50), "first_solve_ms_p99": pct(first, 99),
+            "request_ms_p50": pct(total, 50), "request_ms_p99": pct(total, 99),
+            "warm_resolve_ms_p50": pct(resolve, 50), "warm_resolve_ms_p99": pct(resolve, 99),
+            "queue_ms_max": max(r["queue_ms"] for r in ok) if ok else None,
+            "iters_cold_mean": float(np.mean([r["iters"][0] for r in ok])) if ok else None,
+            "iters_warm_mean": float(np.mean([x for r in ok for x in r["iters"][1:]])) if ok else None,
+            "max_gresidual": max(max(r["max_gresidual"]) for r in ok) if ok else None,
+            "frac_solves_gres_le_1e-6": float(np.mean([x <= 1e-6 for r in ok for x in r["max_gresidual"]]))
+            if ok else None}
+
+
+def run_serving(args):
+    """Continuous-batching serving on a Poisson request stream: mixed-precision
+    capacity (all requests at once), then arrival rates at fractions of it,
+    against the plain FP64 path run one request at a time on the same stream."""
+    import torch
+    from paper_1903_10959_gb300 import workloads as W
+    torch.cuda.init()
+    reqs = W.serving_requests(seed=5, count=args.requests, dof_range=(2.0e4, args.dof_max),
+                              degree=SERVE_DEGREE)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    warm, _ = serve_stream(reqs[:1], "mixed", 1)                     # builds, first-use costs
+    res_cap, span_cap = serve_stream(reqs, "mixed", args.slots)
+    cap = serve_summary(res_cap, span_cap)
+    rate_cap = len(reqs) / span_cap                                    # requests / s
+    sweep = {}
+    for f in [float(x) for x in args.rates.split(",") if x]:
+        arr = W.poisson_arrivals(5, len(reqs), f * rate_cap)
+        r, span = serve_stream(reqs, "mixed", args.slots, arrivals=arr)
+        sweep["%.2f" % f] = serve_summary(r, span)
+    # plain FP64, one request at a time, against the mixed server on the same
+    # subset (the smallest requests: binary64 cell products run ~50x slower)
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i][0].ndofs * reqs[i][0].n_sub)
+    sub = [reqs[i] for i in order[:args.fp64_requests]]
+    r64, span64 = serve_stream(sub, "fp64", 1)
+    rmx, spanmx = serve_stream(sub, "mixed", args.slots)
+    fp64 = {"subset": [s.name for s, _ in sub], "fp64_sequential": serve_summary(r64, span64),
+            "mixed_server": serve_summary(rmx, spanmx)}
+    errs = [float(np.abs(a["evals"][:, :s.n_want] - b["evals"][:, :s.n_want]).max())
+            for a, b, (s, _) in zip(rmx, r64, sub) if a["status"] == 0 and b["status"] == 0]
+    fp64["max_abs_eval_diff_mixed_vs_fp64"] = max(errs) if errs else None
+    fp64["speedup_solves_per_s"] = (fp64["mixed_server"]["solves_per_s"]
+                                    / fp64["fp64_sequential"]["solves_per_s"])
+    clk = clocks.stop()
+    s08 = sweep.get("0.80", cap)
+    line = {
+        "metric": "serving solves/s and p50/p99 latency (mixed, continuous batching)",
+        "value": cap["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
+        "warmup": 1, "ms_per_step": 1e3 / cap["solves_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32x3 (f64 CholGS/RR/residual)",
+        "data": "synthetic",
+        "config": {"workload": "serving: %d periodic Gaussian-well requests, unknowns log-uniform "
+                               "2e4-%.0e, p in {5,6,7}, N log-uniform 32-1000, 5 warm re-solves "
+                               "(1%% depth noise), degree %d, stop at generalized residual %g"
+                               % (len(reqs), args.dof_max, SERVE_DEGREE, SERVE_TOL),
+                   "slots": args.slots, "budget_bytes": 150 << 30,
+                   "iters_cap": [SERVE_ITERS, SERVE_WARM]},
+        "capacity": cap, "arrival_sweep": sweep, "fp64_comparison": fp64,
+        "p99_request_ms_mixed_at_0.8": s08["request_ms_p99"],
+        "clocks": clk,
+    }
+    del warm
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "serving" and args.impl != "reference":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -185,6 +185,9 @@ chfsi_status chfsi_bounds(chfsi_ctx* ctx, int lanczos_steps, uint64_t seed, doub
  * receives the final Ritz values.  When tol > 0 the loop stops early once
  * the largest residual of the lowest n_check pairs is below tol (adaptive
  * filtering, Sec. 3.3); n_check <= 0 means n.  iters_done may be NULL.
+ * The stopping residual is the generalized one of chfsi_residuals (gres,
+ * ||H Psi - l M Psi|| with Psi^T M Psi = 1) in binary64, with l the Ritz value
+ * (FP64) or the column's binary64 Rayleigh quotient (mixed).
  * Mixed precisions: every RR but the last uses the tensor-core operator;
  * the last one applies H~ with binary64 cell products, so the returned
  * eigenvalues carry only second-order error from the binary32 subspace. */
@@ -263,6 +266,77 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
                                int iters, int degree, const double* bnd,
                                chfsi_precision filter_prec, chfsi_precision orth_prec,
                                double* const* evals);
+
+/* ----------------------------------------------------------------- serving
+ * Continuous-batching request loop for SCF-like sequences of eigensolves.
+ * The paper has no serving layer; this wraps the calls above.  A request is
+ * one system (mesh, Gaussian wells) plus `resolves` follow-up potentials
+ * (the same wells with new depths, e.g. a perturbed V_eff of the next SCF
+ * step).  The server admits queued requests in FIFO order as soon as fewer
+ * than max_active requests run and the request's device-memory estimate fits
+ * in what is left of hbm_budget_bytes; every admitted request gets its own
+ * host worker thread, CUDA stream and context, so the GPU work of admitted
+ * requests overlaps.  A request keeps its block X (n columns, binary64 for
+ * CHFSI_FP64, binary32 otherwise) and its upper bound b (one Lanczos run of
+ * 20 steps on the first potential, raised by 2%) resident for all of its
+ * solves: solve 0 starts from chfsi_fill_uniform(seed, stream 1) and runs
+ * `iters` ChFSI iterations, every re-solve rebuilds the cell matrices and
+ * runs `warm_iters` iterations from the previous X (warm start).  Each solve
+ * uses chfsi_solve (tol, n_check as there) and then chfsi_residuals on the
+ * lowest n_check pairs.  Requests share no device data, so a request's
+ * results do not depend on what else runs.  A request whose estimate exceeds
+ * the whole budget completes with CHFSI_ERR_OOM; one that only has to wait
+ * for memory stays queued.  chfsi_server_destroy lets running requests finish,
+ * fails the ones still queued (CHFSI_ERR_STATE) and joins every thread. */
+#define CHFSI_MAX_SOLVES 16
+
+typedef struct chfsi_server chfsi_server;
+
+typedef struct {
+  chfsi_mesh_desc mesh;
+  int n;                  /* wanted + buffer states (columns of X)                    */
+  int nwells;             /* Gaussian wells V(r) = -sum_k d_k exp(-|r-r_k|^2/(2 w_k^2)) */
+  const double* xyz;      /* host, 3 * nwells (copied at submit)                       */
+  const double* depth;    /* host, nwells: depths of solve 0 (copied)                  */
+  const double* width;    /* host, nwells (copied)                                     */
+  int resolves;           /* warm re-solves after solve 0, resolves + 1 <= CHFSI_MAX_SOLVES */
+  const double* depth_seq;/* host, resolves * nwells: depths of re-solve k at k*nwells  */
+  int degree;             /* Chebyshev degree m                                        */
+  int iters;              /* ChFSI iterations of solve 0 (upper limit when tol > 0)     */
+  int warm_iters;         /* iterations of each re-solve                               */
+  double tol;             /* early stop on residual (chfsi_solve), 0 = fixed counts     */
+  int n_check;            /* pairs checked by the early stop and reported residuals     */
+  chfsi_precision prec;   /* filter / orthogonalisation precision                       */
+  uint64_t seed;          /* start block and Lanczos seed                              */
+} chfsi_request;
+
+typedef struct {
+  int done;               /* 0 while queued or running                                 */
+  chfsi_status status;    /* first error of the request, CHFSI_OK on success           */
+  int nsolves;            /* solves completed                                          */
+  double queue_ms;        /* submit -> admission (host clock)                          */
+  double first_ms;        /* submit -> end of solve 0                                  */
+  double total_ms;        /* submit -> end of the last solve                           */
+  size_t est_bytes;       /* device-memory estimate used for admission                 */
+  size_t used_bytes;      /* device bytes the request actually held (context + X)       */
+  double solve_ms[CHFSI_MAX_SOLVES];     /* host wall time of each solve                */
+  double max_residual[CHFSI_MAX_SOLVES]; /* max ||H~x - l x||/||x|| of the n_check pairs */
+  double max_gresidual[CHFSI_MAX_SOLVES];/* max ||H Psi - l M Psi||, Psi^T M Psi = 1      */
+  int iters[CHFSI_MAX_SOLVES];            /* ChFSI iterations each solve ran             */
+  char error[160];        /* message of the first error                                */
+} chfsi_result;
+
+chfsi_status chfsi_server_create(size_t hbm_budget_bytes, int max_active, chfsi_server** out);
+/* Copies the request (and its host arrays); *ticket identifies it. */
+chfsi_status chfsi_server_submit(chfsi_server* sv, const chfsi_request* req, uint64_t* ticket);
+/* Fills *out; with wait != 0 blocks until the request is done.  When done and
+ * evals_host != NULL, copies the Ritz values of every solve, solve k at
+ * evals_host[k * n], (resolves + 1) * n doubles. */
+chfsi_status chfsi_server_poll(chfsi_server* sv, uint64_t ticket, int wait, chfsi_result* out,
+                               double* evals_host);
+/* Device-memory estimate the server admits a request by (bytes). */
+size_t       chfsi_server_estimate(const chfsi_request* req);
+chfsi_status chfsi_server_destroy(chfsi_server* sv);
 
 #ifdef __cplusplus
 }

@@ -6,6 +6,7 @@ library's CUDA kernels.  ``workloads`` holds the seeded synthetic inputs.
 Importing this package does not load the library; constructing a Context
 does, and fails loudly if it has not been built.
 """
-from ._lib import FP64, MIXED_TF32, MIXED_TF32X3, Batch, ChfsiError, Context, load  # noqa: F401
+from ._lib import (FP64, MIXED_TF32, MIXED_TF32X3, Batch, ChfsiError, Context, Server,  # noqa: F401
+                   load)
 
-__all__ = ["Context", "Batch", "ChfsiError", "load", "FP64", "MIXED_TF32", "MIXED_TF32X3"]
+__all__ = ["Context", "Batch", "Server", "ChfsiError", "load", "FP64", "MIXED_TF32", "MIXED_TF32X3"]

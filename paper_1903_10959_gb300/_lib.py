@@ -34,6 +34,27 @@ class MeshDesc(C.Structure):
                 ("periodic", C.c_int), ("quad_points", C.c_int)]
 
 
+MAX_SOLVES = 16
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", MeshDesc), ("n", C.c_int), ("nwells", C.c_int),
+                ("xyz", C.POINTER(C.c_double)), ("depth", C.POINTER(C.c_double)),
+                ("width", C.POINTER(C.c_double)), ("resolves", C.c_int),
+                ("depth_seq", C.POINTER(C.c_double)), ("degree", C.c_int), ("iters", C.c_int),
+                ("warm_iters", C.c_int), ("tol", C.c_double), ("n_check", C.c_int),
+                ("prec", C.c_int), ("seed", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("nsolves", C.c_int),
+                ("queue_ms", C.c_double), ("first_ms", C.c_double),
+                ("total_ms", C.c_double), ("est_bytes", C.c_size_t), ("used_bytes", C.c_size_t),
+                ("solve_ms", C.c_double * MAX_SOLVES), ("max_residual", C.c_double * MAX_SOLVES),
+                ("max_gresidual", C.c_double * MAX_SOLVES), ("iters", C.c_int * MAX_SOLVES),
+                ("error", C.c_char * 160)]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
@@ -74,6 +95,11 @@ _SIGS = {
     "chfsi_batch_candidates": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
     "chfsi_batch_solve": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int), C.c_int,
                                     C.c_int, _dp, C.c_int, C.c_int, C.POINTER(_dp)]),
+    "chfsi_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_vp)]),
+    "chfsi_server_submit": (C.c_int, [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "chfsi_server_poll": (C.c_int, [_vp, C.c_uint64, C.c_int, C.POINTER(Result), _dp]),
+    "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
+    "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "chfsi_kernel_timings": (C.c_int, [_vp, _dp]),
 }
@@ -355,3 +381,91 @@ class Batch:
         self._check(self._lib.chfsi_batch_solve(self._h, p, ld, n, int(iters), int(degree), _ptr(bnd),
                                                 _prec(filter_prec), FP64, earr))
         return evs
+
+
+def _request(mesh, n, centres, depths, widths, depth_seq=(), degree=30, iters=20, warm_iters=4,
+             tol=0.0, n_check=0, prec="mixed", seed=1):
+    """ctypes Request plus the numpy arrays it points into (kept alive by the caller)."""
+    xyz = _host(centres).reshape(-1)
+    dep, wid = _host(depths), _host(widths)
+    seq = _host(depth_seq).reshape(-1) if len(depth_seq) else np.zeros(0)
+    nw = dep.size
+    if xyz.size != 3 * nw or wid.size != nw or seq.size % max(nw, 1):
+        raise ValueError("inconsistent well arrays")
+    resolves = seq.size // nw if nw else len(depth_seq)
+    ncell, length, p, periodic = mesh[:4]
+    md = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p), int(bool(periodic)),
+                  int(mesh[4]) if len(mesh) > 4 else 0)
+    r = Request(md, int(n), nw, _ptr(xyz), _ptr(dep), _ptr(wid), int(resolves),
+                _ptr(seq) if seq.size else None, int(degree), int(iters), int(warm_iters),
+                float(tol), int(n_check), _prec(prec), int(seed))
+    return r, (xyz, dep, wid, seq)
+
+
+class Server:
+    """Continuous-batching eigensolve server (chfsi_server_*).
+
+    ``submit`` takes one system -- ``mesh = (ncell, length, p, periodic)``,
+    Gaussian wells -- and the depths of its warm re-solves; ``poll`` returns
+    a dict with the Ritz values of every solve, the latencies and residuals.
+    """
+
+    def __init__(self, hbm_budget_bytes, max_active=4):
+        lib = load()
+        self._lib = lib
+        h = _vp()
+        st = lib.chfsi_server_create(int(hbm_budget_bytes), int(max_active), C.byref(h))
+        if st != 0:
+            raise ChfsiError(st, "chfsi_server_create failed")
+        self._h = h
+        self._n = {}
+
+    @staticmethod
+    def estimate(mesh, n, prec="mixed", nwells=0):
+        r, keep = _request(mesh, n, np.zeros((nwells, 3)), np.zeros(nwells), np.ones(nwells),
+                           prec=prec)
+        return int(load().chfsi_server_estimate(C.byref(r)))
+
+    def submit(self, mesh, n, centres, depths, widths, depth_seq=(), **kw) -> int:
+        r, keep = _request(mesh, n, centres, depths, widths, depth_seq, **kw)
+        t = C.c_uint64(0)
+        st = self._lib.chfsi_server_submit(self._h, C.byref(r), C.byref(t))
+        if st != 0:
+            raise ChfsiError(st, "chfsi_server_submit rejected the request")
+        self._n[t.value] = (int(n), r.resolves + 1)
+        return t.value
+
+    def poll(self, ticket, wait=True):
+        n, ns = self._n[ticket]
+        res = Result()
+        ev = np.zeros(ns * n)
+        st = self._lib.chfsi_server_poll(self._h, C.c_uint64(ticket), int(bool(wait)), C.byref(res),
+                                         _ptr(ev))
+        if st != 0:
+            raise ChfsiError(st, "chfsi_server_poll failed")
+        if not res.done:
+            return None
+        k = res.nsolves
+        return {"status": res.status, "error": res.error.decode(errors="replace"),
+                "evals": ev.reshape(ns, n)[:k], "nsolves": k, "iters": list(res.iters[:k]),
+                "queue_ms": res.queue_ms, "first_ms": res.first_ms, "total_ms": res.total_ms,
+                "est_bytes": res.est_bytes, "used_bytes": res.used_bytes,
+                "solve_ms": list(res.solve_ms[:k]), "max_residual": list(res.max_residual[:k]),
+                "max_gresidual": list(res.max_gresidual[:k])}
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.chfsi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

@@ -132,6 +132,7 @@ size_t esize(chfsi_precision p) { return p == CHFSI_FP64 ? 8 : 4; }
 void free_device_data(chfsi_ctx* ctx) {
   const HostMesh& m = ctx->mesh;
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
+  ctx->dev_bytes -= (int64_t)ctx->tc.bytes;   // packed binary32 copies (0 when never packed)
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
@@ -442,8 +443,12 @@ chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precisio
   return rotate_impl(ctx, prec, X, ldx, n, Hh, 0, 0);
 }
 
+// Residual norms in binary64.  rayleigh: use each column's Rayleigh quotient
+// x.H~x / x.x (computed here in binary64) instead of evals, so the norm
+// measures the vector alone (stopping test of the mixed solve, whose Ritz
+// values carry the first-order error of the binary32 projection).
 chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
-                           const double* evals, double* res, double* gres) {
+                           const double* evals, double* res, double* gres, bool rayleigh = false) {
   const HostMesh& m = ctx->mesh;
   chfsi_status st;
   if (n == 0) return CHFSI_OK;
@@ -464,9 +469,18 @@ chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, ch
                         prec == CHFSI_FP64, 1, ctx->stream));
     if ((st = apply_step(ctx, CHFSI_FP64, X64, nb, Y64, nb, nullptr, 0, nb, 1.0, 0.0, 0.0)) != CHFSI_OK)
       return st;
+    std::vector<double> h(3 * (size_t)nb);
+    if (rayleigh) {
+      CK(launch_resid_norms(Y64, nb, X64, nb, m.ndofs, nb, nullptr, nullptr, out,
+                            (double*)ctx->part.ptr, ctx->part.bytes, ctx->stream));
+      CK(cudaMemcpyAsync(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      std::vector<double> rho(nb);
+      for (int i = 0; i < nb; ++i) rho[i] = h[i] / h[2 * nb + i];
+      CK(cudaMemcpyAsync(dl + j0, rho.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, ctx->stream));
+    }
     CK(launch_resid_norms(Y64, nb, X64, nb, m.ndofs, nb, dl + j0, ctx->d_mass, out,
                           (double*)ctx->part.ptr, ctx->part.bytes, ctx->stream));
-    std::vector<double> h(3 * (size_t)nb);
     CK(cudaMemcpyAsync(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < nb; ++i) {
@@ -913,7 +927,8 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
     toc(ctx, 2);
     if (tol > 0.0) {
       tic(ctx);
-      if ((st = residual_impl(ctx, X, ldx, n_check, prec, D.data(), res.data(), nullptr)) != CHFSI_OK)
+      if ((st = residual_impl(ctx, X, ldx, n_check, prec, D.data(), nullptr, res.data(),
+                              is_mixed(prec))) != CHFSI_OK)
         return st;
       toc(ctx, 3);
       double mx = *std::max_element(res.begin(), res.begin() + n_check);

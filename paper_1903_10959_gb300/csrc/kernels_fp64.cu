@@ -14,6 +14,7 @@
 //  nl_*_fp64      : separable projector term C~^T h C~ Y (Eqs. nlps,
 //                   nonlocalHamDiscrete) in owner-computes form.
 #include <cstdint>
+#include <mutex>
 
 #include "internal.h"
 
@@ -85,12 +86,11 @@ cudaError_t launch_cell_fp64(const CellLaunch& L, const double* Yin, double* You
   const double* prev = (st.beta != 0.0) ? Yprev : nullptr;
 #define CHFSI_CELL_LAUNCH(B)                                                                      \
   do {                                                                                            \
-    static bool attr_##B = false;                                                                 \
-    if (!attr_##B) {                                                                              \
+    static std::once_flag attr_##B;                                                               \
+    std::call_once(attr_##B, [] {                                                                 \
       cudaFuncSetAttribute(cell_fp64_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                            96 * 1024);                                                            \
-      attr_##B = true;                                                                            \
-    }                                                                                             \
+    });                                                                                           \
     note_launch();                                                                                \
     cell_fp64_kernel<B><<<grid, 256, smem, s>>>(L.Ht, L.dofmap, L.modes, L.cells, L.ne, L.ncol,   \
                                                 Yin, L.ld_in, Yout, L.ld_out, prev, L.ld_prev, W,  \
@@ -248,7 +248,9 @@ cudaError_t launch_tallgemm_fp64(const double* A, int64_t lda, const double* U, 
 
 // ---------------------------------------------------------------- residual norms
 // out_sq[2*i]   = sum_r (Y - l X)^2,  out_sq[2*i+1] = sum_r w_r (Y - l X)^2,
-// out_sq[2*n+i] = sum_r X^2.  Block: 32 columns x 8 row lanes; fixed-order reductions.
+// out_sq[2*n+i] = sum_r X^2.  With lam == nullptr, out_sq[i] = sum_r X Y instead
+// (numerator of the Rayleigh quotient).  Block: 32 columns x 8 row lanes;
+// fixed-order reductions.
 __global__ void resid_partial_kernel(const double* __restrict__ Y, int64_t ldy,
                                      const double* __restrict__ X, int64_t ldx, int64_t M, int n,
                                      const double* __restrict__ lam, const double* __restrict__ wgt,
@@ -259,13 +261,21 @@ __global__ void resid_partial_kernel(const double* __restrict__ Y, int64_t ldy,
   const int64_t r1 = min(M, r0 + rows_per_chunk);
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   if (c < n) {
-    const double l = lam[c];
-    for (int64_t r = r0 + ty; r < r1; r += 8) {
-      const double x = X[r * ldx + c];
-      const double d = Y[r * ldy + c] - l * x;
-      s0 = fma(d, d, s0);
-      if (wgt) s1 = fma(wgt[r] * d, d, s1);
-      s2 = fma(x, x, s2);
+    if (lam) {
+      const double l = lam[c];
+      for (int64_t r = r0 + ty; r < r1; r += 8) {
+        const double x = X[r * ldx + c];
+        const double d = Y[r * ldy + c] - l * x;
+        s0 = fma(d, d, s0);
+        if (wgt) s1 = fma(wgt[r] * d, d, s1);
+        s2 = fma(x, x, s2);
+      }
+    } else {
+      for (int64_t r = r0 + ty; r < r1; r += 8) {
+        const double x = X[r * ldx + c];
+        s0 = fma(x, Y[r * ldy + c], s0);
+        s2 = fma(x, x, s2);
+      }
     }
   }
   __shared__ double red[3][8][32];

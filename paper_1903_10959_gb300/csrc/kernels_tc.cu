@@ -22,6 +22,7 @@
 //  tc_tallgemm  : X U (Algorithm CholGS step 4, subspace rotation of Sec. 3.5).
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 #include "tc.h"
@@ -326,11 +327,10 @@ cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStre
   if (!d.hi) return cudaErrorInvalidValue;
   RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3};
   const CellSmem L = cell_smem(d.mt, a.split3);
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(tc_cell_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  });
   dim3 grid((a.ncol + CELL_BN - 1) / CELL_BN, (unsigned)a.ncells);
   note_launch();
   tc_cell_r_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
@@ -675,11 +675,10 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
   nsplit = (M + rps - 1) / rps;
   GramParams P{A, B, lda, ldb, M, n1, n2, lower, split3, rps, (double*)partial};
   const int smem = GR_S * gram_stage_bytes(0) + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  });
   note_launch();
   tc_gram_kernel<<<dim3(t1, t2, (unsigned)nsplit), GR_THREADS, smem, s>>>(P);
   const int64_t tot = (int64_t)n1 * n2;
@@ -951,11 +950,10 @@ cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int6
   tc_splitu_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans, bd, Us);
   TallParams P{A, lda, M, Us, U, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
   const int smem = TG_S * (2 * TG_T * TG_KC * 4 * 2) + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [&] {
     cudaFuncSetAttribute(tc_tall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  });
   dim3 grid(ntile, (unsigned)((M + TG_T - 1) / TG_T));
   note_launch();
   tc_tall_kernel<<<grid, TG_THREADS, smem, s>>>(P);

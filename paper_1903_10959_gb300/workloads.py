@@ -223,3 +223,43 @@ def perturbed_depths(sys: System, seed: int, step: int, rel: float = 0.01) -> np
                                       np.arange(len(sys.depths), dtype=np.uint64)
                                       + np.uint64(step) * np.uint64(1 << 20))
     return sys.depths * (1.0 + rel * xi)
+
+
+STREAM_ARRIVALS = 10
+
+
+def serving_requests(seed: int = 5, count: int = 24, dof_range=(2.0e4, 2.0e6),
+                     n_range=(32, 1000), h: float = 2.0, well_volume: float = 125.0,
+                     degree: int = 30, iters: int = 24, resolves: int = 5):
+    """Stream of eigensolve requests for the serving loop.
+
+    Per request: DOFs log-uniform in dof_range, p ~ U{5,6,7}, n = round(DOF^(1/3) / p)
+    cells per side (at least 2) of size h (periodic), one well per
+    ``well_volume`` bohr^3 at uniform centres, N log-uniform in n_range
+    (capped at M/8), and ``resolves`` follow-up well-depth sets from
+    ``perturbed_depths`` (1 % noise, step k = 1..resolves).  Returns a list of
+    (System, [depths of re-solve 1..resolves]).
+    """
+    u = uniform01(seed, STREAM_SYSTEMS, np.arange(3 * count, dtype=np.uint64)).reshape(count, 3)
+    out = []
+    for s in range(count):
+        dof = math.exp(math.log(dof_range[0]) + u[s, 0] * (math.log(dof_range[1]) - math.log(dof_range[0])))
+        p = 5 + min(2, int(u[s, 1] * 3))
+        n = max(2, int(round(dof ** (1.0 / 3.0) / p)))
+        L = n * h
+        nw = max(1, int(round(L ** 3 / well_volume)))
+        M = (n * p) ** 3
+        nwant = math.exp(math.log(n_range[0]) + u[s, 2] * (math.log(n_range[1]) - math.log(n_range[0])))
+        nwant = max(8, min(int(round(nwant)), M // 8))
+        sseed = seed * 1000 + s
+        c, d, w = _wells_uniform(sseed, nw, np.zeros(3), np.full(3, L))
+        sys = System("serve-%d" % s, n, p, L, True, c, d, w, nwant, degree, iters, sseed)
+        seq = [perturbed_depths(sys, sseed, k) for k in range(1, resolves + 1)]
+        out.append((sys, seq))
+    return out
+
+
+def poisson_arrivals(seed: int, count: int, rate: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate (exponential gaps)."""
+    u = uniform01(seed, STREAM_ARRIVALS, np.arange(count, dtype=np.uint64))
+    return np.cumsum(-np.log1p(-u) / rate)
