@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """ChFSI benchmark on GB300: seconds per ChFSI iteration on the periodic FCC
 Gaussian-well workload (16^3 cells, p = 6, 884,736 unknowns, N = 1000 wanted
-pairs + 100 buffer, filter block 200, Chebyshev degree 40).
+pairs + 100 buffer, Chebyshev degree 40; wavefunction block and cell tile
+chosen by the library autotuner, the paper-sized block of 200 among the candidates).
 
 One step = one ChFSI iteration on device-resident data: Chebyshev filter
 (Eq. chebFilter), CholGS (Algorithm CholGS) and Rayleigh-Ritz (Sec. 3.5) of
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
+    ap.add_argument("--block", type=int, default=0,
+                    help="wavefunction block of the filter (0: the workload's)")
     ap.add_argument("--workload", default="chfsi", choices=["chfsi", "serving"],
                     help="serving: request stream through the continuous-batching server")
     ap.add_argument("--requests", type=int, default=12, help="serving: number of requests")
@@ -66,7 +69,7 @@ def workload(small=False):
 def workload_config(s, l2_note):
     return {
         "workload": "fcc-periodic %d^3 cells p=%d L=%g, %d unknowns, %d Gaussian wells, "
-                    "N=%d (+%d buffer), filter block %d, Chebyshev degree %d"
+                    "N=%d (+%d buffer), wavefunction block %d, Chebyshev degree %d"
                     % (s.ncell, s.p, s.L, s.ndofs, len(s.depths), s.n_want, s.n_buffer, s.block,
                        s.degree),
         "unknowns": s.ndofs, "n_sub": s.n_sub, "block": s.block, "degree": s.degree, "p": s.p,
@@ -228,7 +231,10 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    import dataclasses
     s = workload(args.small)
+    if args.block:
+        s = dataclasses.replace(s, block=args.block)
     prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32"}[args.prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.current_stream()
@@ -240,6 +246,13 @@ def run_ours(args):
     b = ctx.bounds(20, s.seed)
     X = torch.empty((M, n), dtype=dt, device="cuda")
     ctx.fill_uniform(X, s.seed, prec=prec)
+    tuned = None
+    if not args.block:
+        # wavefunction block and cell tile picked by the library's autotuner
+        blk, tile, cand = ctx.autotune(X, prec=prec)
+        s = dataclasses.replace(s, block=blk)
+        tuned = {"block": blk, "tile": tile,
+                 "candidates_ms": {"%d/%d" % k: round(v, 3) for k, v in cand.items()}}
     ctx.cholgs(X, prec=prec)
     state = {"D": ctx.rayleigh_ritz(X, prec=prec)}
     phase = np.zeros(3)
@@ -370,7 +383,7 @@ def run_ours(args):
                           / (cell_ms / 1e3) / 1e12 if prec != "fp64" else None,
                           "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
         "roofline": roof, "roofline_filter_step": step_roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches,
+        "gpu_launches": launches, "autotune": tuned,
         "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
     }
     print(json.dumps(line), flush=True)

@@ -116,6 +116,22 @@ chfsi_status chfsi_build(chfsi_ctx* ctx);
  * Takes effect on the next call. */
 chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block);
 
+/* Columns per CTA of the tensor-core cell kernel (mixed precisions): 64
+ * (default; two CTAs per SM) or 128 (one CTA per SM, wider MMAs).  Results
+ * do not depend on it. */
+chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
+
+/* Autotuner of the filter's blocking: times a degree-2 filter on a scratch
+ * copy of X (M x n, device; X itself is not modified) for every candidate
+ * (wavefunction block 200, ceil(n/2) and n, times cell tile 64 and 128 for
+ * the mixed precisions), and keeps the fastest in the context (as
+ * chfsi_set_blocking / chfsi_set_cell_tile would).  Needs a built context
+ * and M * n element-sized bytes of free device memory for the copy.
+ * block_out, tile_out may be NULL; ms_out (may be NULL) receives the time of
+ * each candidate in that order (at most 6 entries).  Synchronises. */
+chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n,
+                            chfsi_precision prec, int* block_out, int* tile_out, double* ms_out);
+
 /* Fill rows x ncol of X (device, leading dimension ldx) with the seeded
  * SplitMix64 stream (Steele, Lea & Flood 2014), mapped to [-1, 1): element
  * (r, c) is draw r * ncol + c of the stream keyed by (seed, stream). */

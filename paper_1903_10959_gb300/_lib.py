@@ -71,6 +71,9 @@ _SIGS = {
     "chfsi_set_projectors": (C.c_int, [_vp, C.c_int, _dp, _dp, C.c_double, C.c_double]),
     "chfsi_build": (C.c_int, [_vp]),
     "chfsi_set_blocking": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "chfsi_set_cell_tile": (C.c_int, [_vp, C.c_int]),
+    "chfsi_autotune": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), _dp]),
     "chfsi_fill_uniform": (C.c_int, [_vp, _vp, _i64, _i64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]),
     "chfsi_apply": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int, C.c_int]),
     "chfsi_apply_noalloc": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int]),
@@ -232,6 +235,26 @@ class Context:
 
     def set_blocking(self, filter_block=200, diag_block=1):
         self._check(self._lib.chfsi_set_blocking(self._h, int(filter_block), int(diag_block)))
+
+    def set_cell_tile(self, tile=64):
+        self._check(self._lib.chfsi_set_cell_tile(self._h, int(tile)))
+
+    def autotune(self, X, prec="mixed"):
+        """(block, tile, {(block, tile): ms}) chosen by chfsi_autotune."""
+        pr = _prec(prec)
+        p, ld, n = _dev(X, pr)
+        ms = np.zeros(6)
+        blk, tile = C.c_int(0), C.c_int(0)
+        self._check(self._lib.chfsi_autotune(self._h, p, ld, n, pr, C.byref(blk), C.byref(tile),
+                                             _ptr(ms)))
+        blocks = []
+        for bk in (200, (n + 1) // 2, n):
+            bk = max(1, min(bk, n))
+            if bk not in blocks:
+                blocks.append(bk)
+        tiles = (64, 128) if pr != FP64 else (64,)
+        cands = [(bk, t) for bk in blocks for t in tiles]
+        return blk.value, tile.value, {c: float(ms[i]) for i, c in enumerate(cands)}
 
     def fill_uniform(self, X, seed, stream=1, prec="fp64"):
         pr = _prec(prec)

@@ -213,6 +213,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.ld_in = ld_in;
   ra.R = (float*)ctx->Rb.ptr;
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
+  ra.tile = ctx->cell_tile;
   {
     KTimer kt(ctx, 0);
     CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
@@ -703,6 +704,69 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
   if (filter_block < 1 || diag_block < 1) return fail(ctx, CHFSI_ERR_ARG, "block sizes must be >= 1");
   ctx->filter_block = filter_block;
   ctx->diag_block = diag_block;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile) {
+  CHECK_CTX();
+  if (tile != 64 && tile != 128) return fail(ctx, CHFSI_ERR_ARG, "cell tile must be 64 or 128");
+  ctx->cell_tile = tile;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
+                            int* block_out, int* tile_out, double* ms_out) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (!ctx->built) return fail(ctx, CHFSI_ERR_STATE, "autotune before build");
+  const HostMesh& m = ctx->mesh;
+  const size_t es = esize(prec);
+  // candidates: the paper-sized block of 200, half and all of the columns;
+  // the tensor-core cell kernel with 64- and 128-column tiles
+  std::vector<int> blocks;
+  for (int bk : {200, (n + 1) / 2, n}) {
+    bk = std::max(1, std::min(bk, n));
+    if (std::find(blocks.begin(), blocks.end(), bk) == blocks.end()) blocks.push_back(bk);
+  }
+  std::vector<int> tiles = is_mixed(prec) ? std::vector<int>{64, 128} : std::vector<int>{64};
+  void* scratch = nullptr;
+  CK(dalloc(ctx, &scratch, (size_t)m.ndofs * n * es));
+  CK(cudaMemcpy2DAsync(scratch, n * es, X, ldx * es, n * es, m.ndofs, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  const int save_block = ctx->filter_block, save_tile = ctx->cell_tile;
+  double best = 1e300;
+  int best_block = save_block, best_tile = save_tile, k = 0;
+  for (int bk : blocks) {
+    for (int tl : tiles) {
+      ctx->filter_block = bk;
+      ctx->cell_tile = tl;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == CHFSI_OK; ++rep) {   // first run grows the scratch
+        cudaEventRecord(ctx->ev[0], ctx->stream);
+        st = filter_impl(ctx, scratch, n, n, 2, 1.0, 2.0, 0.0, prec);
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+        cudaEventSynchronize(ctx->ev[1]);
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+      }
+      if (st != CHFSI_OK) break;
+      if (ms_out) ms_out[k] = ms;
+      ++k;
+      if (ms < best) {
+        best = ms;
+        best_block = bk;
+        best_tile = tl;
+      }
+    }
+    if (st != CHFSI_OK) break;
+  }
+  dfree(ctx, scratch, (size_t)m.ndofs * n * es);
+  ctx->filter_block = st == CHFSI_OK ? best_block : save_block;
+  ctx->cell_tile = st == CHFSI_OK ? best_tile : save_tile;
+  if (st != CHFSI_OK) return st;
+  if ((st = check_device_status(ctx, prec)) != CHFSI_OK) return st;
+  if (block_out) *block_out = best_block;
+  if (tile_out) *tile_out = best_tile;
   return CHFSI_OK;
 }
 

@@ -20,6 +20,7 @@ struct chfsi_ctx {
   chfsi_status latched = CHFSI_OK;
   std::string err;
   int filter_block = 200, diag_block = 1;
+  int cell_tile = 64;              // columns per CTA of the tensor-core cell kernel
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices

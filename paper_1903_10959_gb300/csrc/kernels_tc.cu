@@ -34,7 +34,7 @@ using namespace ptx;
 
 __device__ int g_tc_status = 0;   // nonzero after a bounded wait gave up
 
-constexpr int CELL_BN = 64;       // columns per CTA
+constexpr int CELL_BN = 64;       // default columns per CTA (128 selectable)
 constexpr int CELL_KC = 8;        // K per pipeline stage (one MMA K-step)
 constexpr int CELL_THREADS = 192;
 
@@ -115,12 +115,15 @@ struct CellSmem {
   int total;
 };
 
-__host__ __device__ inline CellSmem cell_smem(int mt, int split3) {
+// Stage sizes of the cell kernel.  64-column tiles keep two CTAs per SM
+// (about 110 KB each); 128-column tiles take the SM alone (TMEM holds one
+// CTA's mt x 128 accumulator columns) and use up to 200 KB of stages.
+__host__ __device__ inline CellSmem cell_smem(int mt, int split3, int bn = CELL_BN) {
   CellSmem c;
   c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
-  c.y_bytes = CELL_BN * CELL_KC * 4 * 2;
+  c.y_bytes = bn * CELL_KC * 4 * 2;
   const int stage = c.a_bytes + c.y_bytes;
-  int S = (110 * 1024 - 3072) / stage;
+  int S = ((bn > 64 ? 200 : 110) * 1024 - 3072) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
   c.stages = S;
   c.total = S * stage + 3072;   // + barriers, the cell's dof map (<= 512) and modes
@@ -144,14 +147,15 @@ struct RParams {
   int ncol, ne, mt, nk, split3;
 };
 
+template <int BN>
 __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t e = blockIdx.y;
-  const int c0 = blockIdx.x * CELL_BN;
-  const int ncv = min(CELL_BN, P.ncol - c0);
+  const int c0 = blockIdx.x * BN;
+  const int ncv = min(BN, P.ncol - c0);
   const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
-  const CellSmem L = cell_smem(P.mt, P.split3);
+  const CellSmem L = cell_smem(P.mt, P.split3, BN);
   const int S = L.stages;
   const int stage_bytes = L.a_bytes + L.y_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
@@ -163,7 +167,8 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
   auto fy = [&](int s) { return smem_u32(bars + S + s); };
   auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
   const uint32_t accb = smem_u32(bars + 3 * S);
-  const uint32_t tmem_cols = P.mt == 1 ? 64 : (P.mt == 2 ? 128 : 256);
+  const int tc_need = P.mt * BN;   // accumulator columns: one BN-wide block per 128-row tile
+  const uint32_t tmem_cols = tc_need <= 64 ? 64 : (tc_need <= 128 ? 128 : (tc_need <= 256 ? 256 : 512));
   const int nk = P.nk, ne = P.ne;
 
   if (tid == 0) {
@@ -220,9 +225,9 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
         const uint32_t sa = sbase + s * stage_bytes;
         const uint32_t sy = sa + L.a_bytes;
         const uint64_t yhi = umma_desc(sy, 128, 256);
-        const uint64_t ylo = umma_desc(sy + CELL_BN * CELL_KC * 4, 128, 256);
+        const uint64_t ylo = umma_desc(sy + BN * CELL_KC * 4, 128, 256);
         for (int t = 0; t < P.mt; ++t) {
-          const uint32_t d = tmem + t * CELL_BN;
+          const uint32_t d = tmem + t * BN;
           const uint64_t ahi = umma_desc(sa + t * 4096, 128, 256);
           if (P.split3) {
             const uint64_t alo = umma_desc(sa + P.mt * 4096 + t * 4096, 128, 256);
@@ -240,26 +245,31 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
   } else {
     // gather + split (warp w: chunks w, w + G, ...; G = min(4, S) keeps parity waits sound)
     const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
+    constexpr int CPT = BN / 16;   // columns per thread (16 threads span the tile)
     const int q = lane >> 4;
-    const int cq = (lane & 15) * 4;
+    const int cq = (lane & 15) * CPT;
     const int G = S < 4 ? S : 4;
     for (int i = warp; i < nk && warp < G; i += G) {
       const int s = i % S;
-      float v[4][4];
+      float v[4][CPT];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int l = i * CELL_KC + q * 4 + a;
         const int g = l < ne ? dm[l] : -1;
-        v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) v[a][u] = 0.f;
         if (g >= 0) {
           const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
-          if (vec && cq + 4 <= ncv) {
-            const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
-            v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
-          } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (cq + u < ncv) v[a][u] = __ldg(src + u);
+          for (int u4 = 0; u4 < CPT; u4 += 4) {
+            if (vec && cq + u4 + 4 <= ncv) {
+              const float4 t4 = __ldg(reinterpret_cast<const float4*>(src + u4));
+              v[a][u4] = t4.x; v[a][u4 + 1] = t4.y; v[a][u4 + 2] = t4.z; v[a][u4 + 3] = t4.w;
+            } else {
+#pragma unroll
+              for (int u = u4; u < u4 + 4; ++u)
+                if (cq + u < ncv) v[a][u] = __ldg(src + u);
+            }
           }
         }
       }
@@ -269,9 +279,9 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
       }
       if (*(volatile int*)abort_flag) break;
       float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
-      float* yl = yh + CELL_BN * CELL_KC;
+      float* yl = yh + BN * CELL_KC;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < CPT; ++u) {
         const int n = cq + u;
         const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
         float4 h, lo;
@@ -301,7 +311,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
         float acc[16];
         __syncwarp();
         if (run) {
-          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * CELL_BN + cb, acc);
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * BN + cb, acc);
           tmem_wait_ld();
         }
         if (!run || l >= ne) continue;
@@ -326,14 +336,19 @@ cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStre
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.hi) return cudaErrorInvalidValue;
   RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3};
-  const CellSmem L = cell_smem(d.mt, a.split3);
   static std::once_flag attr;
   std::call_once(attr, [&] {
-    cudaFuncSetAttribute(tc_cell_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_r_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_r_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   });
-  dim3 grid((a.ncol + CELL_BN - 1) / CELL_BN, (unsigned)a.ncells);
+  const int bn = a.tile == 128 ? 128 : 64;
+  const CellSmem L = cell_smem(d.mt, a.split3, bn);
+  dim3 grid((a.ncol + bn - 1) / bn, (unsigned)a.ncells);
   note_launch();
-  tc_cell_r_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
+  if (bn == 128)
+    tc_cell_r_kernel<128><<<grid, CELL_THREADS, L.total, s>>>(P);
+  else
+    tc_cell_r_kernel<64><<<grid, CELL_THREADS, L.total, s>>>(P);
   return cudaGetLastError();
 }
 

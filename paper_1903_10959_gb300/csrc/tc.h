@@ -29,6 +29,7 @@ struct TcApplyArgs {
   int64_t ld_in;
   float* R;                 // ncells * ne * ncol scratch
   int split3;
+  int tile = 64;            // columns per CTA of the cell kernel: 64 or 128
 };
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
 cudaError_t tc_assemble_launch(const int32_t* node_ptr, const int32_t* node_ent, int64_t M,

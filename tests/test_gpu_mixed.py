@@ -66,6 +66,42 @@ def test_mixed_apply(case, ncol, prec, tol):
     assert rel_fro(Y.cpu().numpy().astype(np.float64), ref) < tol
 
 
+@pytest.mark.parametrize("ncol", [13, 128, 200, 301])
+def test_mixed_apply_tile128(case, ncol):
+    """The 128-column cell tile (one CTA per SM) against the oracle, with a
+    ragged last tile; bit-identical to the 64-column tile (same per-element
+    MMA order: every K-chunk adds into the same accumulator row)."""
+    s, prob, ctx = case
+    X0 = _x32(5, prob.ndofs, ncol)
+    X = torch.tensor(X0, device=DEV)
+    Y64, Y128 = torch.empty_like(X), torch.empty_like(X)
+    ctx.set_blocking(400, 8)
+    ctx.set_cell_tile(64)
+    ctx.apply(X, Y64, prec="tf32x3")
+    ctx.set_cell_tile(128)
+    ctx.apply(X, Y128, prec="tf32x3")
+    ctx.set_cell_tile(64)
+    ref = prob.apply_Htilde(X0.astype(np.float64))
+    assert rel_fro(Y128.cpu().numpy().astype(np.float64), ref) < 1e-5
+    assert torch.equal(Y64, Y128)
+
+
+def test_autotune_keeps_x_and_picks_a_candidate(case):
+    s, prob, ctx = case
+    X0 = _x32(6, prob.ndofs, 150)
+    X = torch.tensor(X0, device=DEV)
+    blk, tile, ms = ctx.autotune(X, prec="mixed")
+    assert (blk, tile) in ms and all(v > 0 for v in ms.values())
+    assert ms[(blk, tile)] == min(ms.values())
+    assert np.array_equal(X.cpu().numpy(), X0)
+    Y = torch.empty_like(X)
+    ctx.apply(X, Y, prec="tf32x3")       # runs with the chosen blocking
+    ref = prob.apply_Htilde(X0.astype(np.float64))
+    assert rel_fro(Y.cpu().numpy().astype(np.float64), ref) < 1e-5
+    ctx.set_blocking(200, 8)
+    ctx.set_cell_tile(64)
+
+
 def test_mixed_filter(case):
     s, prob, ctx = case
     X0 = _x32(4, prob.ndofs, 45)
