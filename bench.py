@@ -46,9 +46,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
     ap.add_argument("--block", type=int, default=0,
-                    help="wavefunction block of the filter (0: the workload's)")
-    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "serving"],
-                    help="serving: request stream through the continuous-batching server")
+                    help="wavefunction block of the filter (0: chosen by the autotuner)")
+    ap.add_argument("--tile", type=int, default=64, choices=[64, 128],
+                    help="cell-kernel column tile when --block is given")
+    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "c3", "serving"],
+                    help="chfsi: the 16^3-cell p=6 FCC system; c3: 20^3 cells p=7 with "
+                         "projectors, N=3000 (block 1100); serving: request stream through "
+                         "the continuous-batching server")
     ap.add_argument("--requests", type=int, default=12, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrently admitted requests")
     ap.add_argument("--dof-max", type=float, default=2.0e6, help="serving: largest request (unknowns)")
@@ -59,19 +63,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload(small=False):
+def workload(small=False, kind="chfsi"):
     from paper_1903_10959_gb300 import workloads as W
+    if kind == "c3":
+        return W.cubic_sites_nonlocal(block=1100)
     if small:
         return W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=200, degree=40, iters=4, block=200)
     return W.fcc_periodic()
 
 
 def workload_config(s, l2_note):
+    nl = " + %d sites x 4 projectors" % len(s.nl_centres) if len(s.nl_centres) else ""
     return {
-        "workload": "fcc-periodic %d^3 cells p=%d L=%g, %d unknowns, %d Gaussian wells, "
+        "workload": "%s %d^3 cells p=%d L=%g, %d unknowns, %d Gaussian wells%s, "
                     "N=%d (+%d buffer), wavefunction block %d, Chebyshev degree %d"
-                    % (s.ncell, s.p, s.L, s.ndofs, len(s.depths), s.n_want, s.n_buffer, s.block,
-                       s.degree),
+                    % (s.name.rsplit("-", 2)[0], s.ncell, s.p, s.L, s.ndofs, len(s.depths), nl,
+                       s.n_want, s.n_buffer, s.block, s.degree),
         "unknowns": s.ndofs, "n_sub": s.n_sub, "block": s.block, "degree": s.degree, "p": s.p,
         "cells": s.ncell ** 3, "l2": l2_note,
     }
@@ -127,6 +134,42 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ replicas
+def job_seconds_per_iter(t_local, steps, dist=None, device="cpu"):
+    """Whole-job time and s/iter of N independent replicas: the slowest rank's
+    time (max over ranks, then a barrier) over the steps all ranks ran."""
+    import torch
+    world = 1
+    t = float(t_local)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        dist.barrier()
+    return t, t / (steps * world)
+
+
+# ------------------------------------------------------------------ profiled traffic
+def profiled_traffic(kernel, s, n):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    `kernel` for this workload and block, from the committed ncu summary
+    profiles/<kernel>_traffic.txt (lines "<cells> <p> <block> <bytes>"); None
+    when that configuration has not been profiled."""
+    path = os.path.join(ROOT, "profiles", kernel + "_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) == 4 and not line.startswith("#"):
+            try:
+                if (int(f[0]), int(f[1]), int(f[2])) == (s.ncell ** 3, s.p, min(s.block, n)):
+                    return float(f[3])
+            except ValueError:
+                continue
+    return None
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -232,7 +275,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     import dataclasses
-    s = workload(args.small)
+    s = workload(args.small, args.workload)
     if args.block:
         s = dataclasses.replace(s, block=args.block)
     prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32"}[args.prec]
@@ -240,14 +283,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
     ctx.set_potential_gaussians(s.centres, s.depths, s.widths)
+    if len(s.nl_centres):
+        ctx.set_projectors(s.nl_centres, s.nl_h, s.nl_sigma, s.nl_rcut)
     ctx.build()
     ctx.set_blocking(s.block, 1)
+    ctx.set_cell_tile(args.tile)
     n, M = s.n_sub, ctx.ndofs
     b = ctx.bounds(20, s.seed)
     X = torch.empty((M, n), dtype=dt, device="cuda")
     ctx.fill_uniform(X, s.seed, prec=prec)
     tuned = None
-    if not args.block:
+    if not args.block and args.workload != "c3":
         # wavefunction block and cell tile picked by the library's autotuner
         blk, tile, cand = ctx.autotune(X, prec=prec)
         s = dataclasses.replace(s, block=blk)
@@ -289,20 +335,17 @@ def run_ours(args):
     ctx.set_kernel_timing(False)
     clk = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
-    if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-        dist.barrier()
-    value = t / (args.steps * world)
+    t, value = job_seconds_per_iter(t, args.steps, dist, "cuda")
 
-    # Roofline of the dominant kernel, the tensor-core cell-product kernel
-    # (per-launch CUDA events on the context stream).  Its algorithmic bytes per
-    # launch (one filter block of nb columns): the split cell matrices
-    # (N_c n_e^2 x 8 B), the block of Y read once (M nb x s_X) and the dense
-    # cell blocks written (N_c n_e nb x s_X).  The whole filter step (cell +
-    # assembly kernels) is also reported against the fused-recurrence minimum
-    # 3 s_X per unknown and vector plus the cell matrices.
+    # Rooflines (per-launch CUDA events on the context stream).
+    # Cell-product kernel, algorithmic work per launch (one block of nb
+    # columns): 2 n_e^2 flops per cell and vector; bytes = the split cell
+    # matrices (N_c n_e^2 x 8 B) + the block of Y (M nb s_X) + the dense cell
+    # blocks written (N_c n_e nb s_X).  With 3xTF32 each flop takes three
+    # TF32 MMA passes, so its tensor peak is the TF32 peak / 3.
+    # Assembly kernel, bytes per launch: the cell blocks read (N_c n_e nb s_X),
+    # Y_in, Y_prev read and Y_out written (3 M nb s_X) and the unknown -> cell
+    # row table ((M + 1 + N_c n_e) x 4 B).
     nblocks = -(-n // s.block)
     ne = (s.p + 1) ** 3
     ncells = s.ncell ** 3
@@ -314,33 +357,49 @@ def run_ours(args):
     col_steps = steps_blocks * n                  # (vector, application) units
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-    cell_ms, asm_ms, cell_n, asm_n = [float(v) for v in kt]
+    cell_ms, asm_ms, cell_n, asm_n, nl_ms, nl_n = [float(v) for v in kt]
     alg_flops = col_steps * ncells * 2 * ne * ne          # dense cell products, one per vector
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1672.5) * 1.1 / 2.25
     if prec == "fp64":
-        roof = {"bound": "alu", "achieved": alg_flops / (cell_ms / 1e3) / 1e12, "peak": 1.0,
+        roof = {"bound": "alu", "achieved": alg_flops / (cell_ms / 1e3) / 1e12, "peak": 1.25,
                 "unit": "TFLOP/s", "kernel": "cell_fp64_kernel", "launches": int(cell_n),
                 "avg_launch_ms": cell_ms / max(cell_n, 1),
-                "peak_note": "binary64 DFMA peak 1.0 TFLOP/s measured by a DFMA probe on this GB300"}
+                "peak_note": "nominal binary64 rate of GB300 (1.25 TFLOP/s)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
-        step_roof = None
+        step_roof = asm_roof = None
     else:
+        passes = 3 if prec == "mixed" else 1
         cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * 8
                       + col_steps * M * sx + col_steps * ncells * ne * sx)
-        per_launch = cell_bytes / cell_n
-        achieved = cell_bytes / (cell_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "tc_cell_r_kernel",
+        tpeak = tf32_peak / passes
+        achieved = alg_flops / (cell_ms / 1e3) / 1e12
+        traffic = profiled_traffic("tc_cell_r_kernel", s, n)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": achieved / tpeak, "traffic": traffic, "kernel": "tc_cell_r_kernel",
                 "launches": int(cell_n), "avg_launch_ms": cell_ms / cell_n,
-                "bytes_per_launch": per_launch,
-                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
+                "flops_per_launch": alg_flops / cell_n, "bytes_per_launch": cell_bytes / cell_n,
+                "hbm_gbs": cell_bytes / (cell_ms / 1e3) / 1e9,
+                "peak_note": "TF32 dense peak = measured bf16 sustained (MEASURED_PEAKS.json) x "
+                             "1.1/2.25 nominal ratio, / %d MMA passes per flop; of measured" % passes}
+        asm_bytes = (col_steps * ncells * ne * sx + col_steps * 3 * M * sx
+                     + steps_blocks * nblocks * (M + 1 + ncells * ne) * 4)
+        if len(s.nl_centres):
+            asm_bytes += col_steps * M * sx          # the projector term read by the assembly
+        asm_roof = {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernel": "tc_assemble_kernel",
+                    "launches": int(asm_n), "avg_launch_ms": asm_ms / max(asm_n, 1),
+                    "bytes_per_launch": asm_bytes / max(asm_n, 1),
+                    "traffic": profiled_traffic("tc_assemble_kernel", s, n),
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
+        asm_roof["frac"] = asm_roof["achieved"] / peaks["hbm_gbs"]
         step_bytes = col_steps * 3 * sx * M + steps_blocks * nblocks * ncells * ne * ne * 8
         step_roof = {"bound": "hbm", "achieved": step_bytes / ((cell_ms + asm_ms) / 1e3) / 1e9,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "kernels": "tc_cell_r_kernel + tc_assemble_kernel",
-                     "assemble_avg_launch_ms": asm_ms / max(asm_n, 1)}
+                     "note": "filter degree step against the fused-recurrence minimum "
+                             "(3 s_X per unknown and vector + the cell matrices)"}
         step_roof["frac"] = step_roof["achieved"] / peaks["hbm_gbs"]
-    tf32_peak = peaks.get("bf16_tflops_sustained", 1672.5) * 1.1 / 2.25
     phase_timed = phase.copy()
     # end to end through host buffers: H2D of X, one iteration, D2H of X and the Ritz values
     e2e = None
@@ -368,7 +427,10 @@ def run_ours(args):
         cpu = {"value": tcpu, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": sample, "phases_s": parts}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "chfsi" else
+        "ChFSI s/iter (filter + CholGS + RR), %s %d^3 cells p=%d" % (s.name.rsplit("-", 2)[0],
+                                                                      s.ncell, s.p),
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else ("tf32x3" if prec == "mixed" else "tf32"),
@@ -382,8 +444,10 @@ def run_ours(args):
                           "cell_kernel_executed_tensor": (3 if prec == "mixed" else 1) * alg_flops
                           / (cell_ms / 1e3) / 1e12 if prec != "fp64" else None,
                           "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
-        "roofline": roof, "roofline_filter_step": step_roof, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roof, "roofline_assembly": asm_roof, "roofline_filter_step": step_roof,
+        "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "autotune": tuned,
+        "projector_kernels_ms_per_step": nl_ms / args.steps if nl_n else None,
         "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
     }
     print(json.dumps(line), flush=True)

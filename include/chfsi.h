@@ -127,8 +127,11 @@ chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
  * the mixed precisions), and keeps the fastest in the context (as
  * chfsi_set_blocking / chfsi_set_cell_tile would).  Needs a built context
  * and M * n element-sized bytes of free device memory for the copy.
- * block_out, tile_out may be NULL; ms_out (may be NULL) receives the time of
- * each candidate in that order (at most 6 entries).  Synchronises. */
+ * A candidate whose scratch does not fit in device memory is skipped (its
+ * ms_out entry is -1); CHFSI_ERR_OOM only when none fits.  The scratch grown
+ * while tuning is released afterwards.  block_out, tile_out may be NULL;
+ * ms_out (may be NULL) receives the time of each candidate in that order (at
+ * most 6 entries).  Synchronises. */
 chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n,
                             chfsi_precision prec, int* block_out, int* tile_out, double* ms_out);
 
@@ -228,9 +231,11 @@ int64_t      chfsi_device_bytes(const chfsi_ctx* ctx);
 chfsi_status chfsi_set_kernel_timing(chfsi_ctx* ctx, int on);
 
 /* Accumulated device times since the last call, then reset:
- * out4[0] cell-product kernel ms, out4[1] assembly kernel ms, out4[2] and
- * out4[3] the numbers of launches timed.  Synchronises the stream. */
-chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out4);
+ * out6[0] cell-product kernel ms, out6[1] assembly kernel ms, out6[2] and
+ * out6[3] the numbers of launches timed, out6[4] ms of the binary32
+ * projector kernels (projection + expansion), out6[5] their timed pairs.
+ * Synchronises the stream. */
+chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out6);
 
 /* Number of kernels this library has launched so far (all contexts; a
  * monotonic counter for accounting, e.g. launches per ChFSI iteration). */

@@ -322,8 +322,9 @@ class Context:
         self._check(self._lib.chfsi_set_kernel_timing(self._h, int(bool(on))))
 
     def kernel_timings(self) -> np.ndarray:
-        """[cell-product ms, assembly ms, cell launches, assembly launches] since the last call."""
-        out = np.zeros(4)
+        """[cell-product ms, assembly ms, cell launches, assembly launches, projector ms,
+        projector launch pairs] since the last call."""
+        out = np.zeros(6)
         self._check(self._lib.chfsi_kernel_timings(self._h, _ptr(out)))
         return out
 

@@ -126,6 +126,19 @@ chfsi_status grow(chfsi_ctx* ctx, DevBuf& b, size_t bytes) {
 }
 
 bool is_mixed(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32; }
+// Columns per block of the binary64 staging copies (residuals, binary64 RR apply).
+constexpr int kStage64 = 512;
+// Free the per-call scratch that grows with the column block (filter, cell
+// blocks, projector and binary64 staging buffers); later calls regrow it.
+void release_scratch(chfsi_ctx* ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot}) {
+    dfree(ctx, b->ptr, b->bytes);
+    b->ptr = nullptr;
+    b->bytes = 0;
+  }
+}
+
 bool valid_prec(chfsi_precision p) { return p == CHFSI_FP64 || is_mixed(p); }
 size_t esize(chfsi_precision p) { return p == CHFSI_FP64 ? 8 : 4; }
 
@@ -197,6 +210,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     }
   }
   if (nl) {
+    KTimer kt(ctx, 2);
     CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
                      (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
     CK(tc_nl_expand(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c32, m.ndofs,
@@ -404,9 +418,10 @@ chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precisio
   double* Hh = (double*)ctx->Ssq.ptr;
   int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
   const size_t es = esize(prec);
-  const int B = std::max(1, std::min(ctx->filter_block, n));
-  if ((st = grow(ctx, ctx->T1, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
   const bool via64 = fp64_apply && is_mixed(prec);
+  // binary64 staging (X and H~X copies) is capped at kStage64 columns
+  const int B = std::max(1, std::min({ctx->filter_block, n, via64 ? kStage64 : n}));
+  if ((st = grow(ctx, ctx->T1, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
   if (via64 && (st = grow(ctx, ctx->rot, (size_t)m.ndofs * B * 8 * 2)) != CHFSI_OK) return st;
   // 1. H^ = X^T (H~ X), lower triangle, one column block at a time
   for (int j0 = 0; j0 < n; j0 += B) {
@@ -453,7 +468,7 @@ chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, ch
   const HostMesh& m = ctx->mesh;
   chfsi_status st;
   if (n == 0) return CHFSI_OK;
-  const int B = std::max(1, std::min(ctx->filter_block, n));
+  const int B = std::max(1, std::min({ctx->filter_block, n, kStage64}));
   // binary64 copies of the block and of H~ x (residual check always in binary64)
   if ((st = grow(ctx, ctx->rot, (size_t)m.ndofs * B * 8 * 2)) != CHFSI_OK) return st;
   if ((st = grow(ctx, ctx->lam, (size_t)n * 8 * 4 + 64)) != CHFSI_OK) return st;
@@ -606,7 +621,8 @@ chfsi_status chfsi_set_kernel_timing(chfsi_ctx* ctx, int on) {
   return CHFSI_OK;
 }
 
-chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out4) {
+chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out6) {
+  double* out4 = out6;
   CHECK_CTX();
   if (!out4) return CHFSI_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -623,8 +639,10 @@ chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out4) {
   out4[1] = ctx->kms[1];
   out4[2] = (double)ctx->kcount[0];
   out4[3] = (double)ctx->kcount[1];
-  ctx->kms[0] = ctx->kms[1] = 0.0;
-  ctx->kcount[0] = ctx->kcount[1] = 0;
+  out4[4] = ctx->kms[2];
+  out4[5] = (double)ctx->kcount[2];
+  ctx->kms[0] = ctx->kms[1] = ctx->kms[2] = 0.0;
+  ctx->kcount[0] = ctx->kcount[1] = ctx->kcount[2] = 0;
   return CHFSI_OK;
 }
 
@@ -749,6 +767,13 @@ chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, c
         cudaEventSynchronize(ctx->ev[1]);
         cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
       }
+      if (st == CHFSI_ERR_OOM) {   // candidate does not fit: skip it, free what it grew
+        st = CHFSI_OK;
+        release_scratch(ctx);
+        if (ms_out) ms_out[k] = -1.0;
+        ++k;
+        continue;
+      }
       if (st != CHFSI_OK) break;
       if (ms_out) ms_out[k] = ms;
       ++k;
@@ -761,6 +786,8 @@ chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, c
     if (st != CHFSI_OK) break;
   }
   dfree(ctx, scratch, (size_t)m.ndofs * n * es);
+  release_scratch(ctx);   // regrown at the chosen size by the next call
+  if (st == CHFSI_OK && best > 1e299) st = fail(ctx, CHFSI_ERR_OOM, "no blocking candidate fits in device memory");
   ctx->filter_block = st == CHFSI_OK ? best_block : save_block;
   ctx->cell_tile = st == CHFSI_OK ? best_tile : save_tile;
   if (st != CHFSI_OK) return st;

@@ -52,6 +52,6 @@ struct chfsi_ctx {
     cudaEvent_t a, b;
   };
   std::vector<KRec> krec;
-  double kms[2] = {0, 0};
-  int64_t kcount[2] = {0, 0};
+  double kms[3] = {0, 0, 0};       // cell products, assembly, projector kernels
+  int64_t kcount[3] = {0, 0, 0};
 };

@@ -618,42 +618,63 @@ __global__ void tc_gram_reduce_kernel(const double* __restrict__ partial, int ns
 }
 
 // Binary64 diagonal blocks: C[i, j] = sum_r A[r, i] B[r, j] for i / bd == j / bd
-// (i, j < min(n1, n2); bd divides 32).  Block: 8 row lanes x 32 columns; a
-// thread owns column i and accumulates its bd block partners, whose B values
-// come from neighbouring lanes by warp shuffles.  Products of binary32 values
-// are exact in binary64; partial sums over row chunks are reduced in fixed order.
-__global__ void diag_gram_fp64_kernel(const float* __restrict__ A, int64_t lda,
-                                      const float* __restrict__ B, int64_t ldb, int64_t M, int nd,
-                                      int bd, int64_t rows_per_chunk, double* __restrict__ part) {
+// (i, j < min(n1, n2); BD divides 32).  Block: 8 row lanes x 32 columns; a
+// thread owns column i and accumulates its BD block partners, whose B values
+// come from neighbouring lanes by warp shuffles.  Rows are taken four at a
+// time (four loads in flight per thread, four partial sums combined in a
+// fixed order).  Products of binary32 values are exact in binary64; partial
+// sums over row chunks are reduced in fixed order.
+template <int BD>
+__global__ void __launch_bounds__(256) diag_gram_fp64_kernel(const float* __restrict__ A, int64_t lda,
+                                                             const float* __restrict__ B, int64_t ldb,
+                                                             int64_t M, int nd, int64_t rows_per_chunk,
+                                                             double* __restrict__ part) {
   const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
   const int64_t r1 = min(M, r0 + rows_per_chunk);
-  const int jb = lane / bd * bd;            // first lane of this column's block
-  double acc[32];
+  const int jb = lane / BD * BD;            // first lane of this column's block
+  const bool in = i < nd;
+  constexpr int NA = BD >= 8 ? 1 : 4;       // partial-sum sets (register budget)
+  double acc[4][BD];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-  for (int64_t r = r0 + rl; r < r1; r += 8) {
-    const float a = i < nd ? A[r * lda + i] : 0.f;
-    const float b = i < nd ? B[r * ldb + i] : 0.f;
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      if (q < bd) {
-        const float bq = __shfl_sync(0xffffffffu, b, jb + q);
-        acc[q] = fma((double)a, (double)bq, acc[q]);
+    for (int q = 0; q < BD; ++q) acc[u][q] = 0.0;
+  int64_t r = r0 + rl;
+  for (; r + 24 < r1; r += 32) {
+    float a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = in ? A[(r + 8 * u) * lda + i] : 0.f;
+      b[u] = in ? B[(r + 8 * u) * ldb + i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < BD; ++q) {
+        const float bq = BD == 1 ? b[u] : __shfl_sync(0xffffffffu, b[u], jb + q);
+        acc[u % NA][q] = fma((double)a[u], (double)bq, acc[u % NA][q]);
       }
+  }
+  for (; r < r1; r += 8) {
+    const float a = in ? A[r * lda + i] : 0.f;
+    const float b = in ? B[r * ldb + i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < BD; ++q) {
+      const float bq = BD == 1 ? b : __shfl_sync(0xffffffffu, b, jb + q);
+      acc[0][q] = fma((double)a, (double)bq, acc[0][q]);
     }
   }
   __shared__ double red[8][32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    if (q >= bd) break;
-    red[rl][lane] = acc[q];
+  for (int q = 0; q < BD; ++q) {
+    red[rl][lane] = (acc[0][q] + acc[1][q]) + (acc[2][q] + acc[3][q]);
     __syncthreads();
-    if (rl == 0 && i < nd) {
+    if (rl == 0 && in) {
       double t = 0.0;
       for (int w = 0; w < 8; ++w) t += red[w][lane];
-      part[((int64_t)blockIdx.y * gridDim.x * 32 + i) * bd + q] = t;
+      part[((int64_t)blockIdx.y * gridDim.x * 32 + i) * BD + q] = t;
     }
     __syncthreads();
   }
@@ -707,14 +728,22 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
     const int nd = std::min(n1, n2);
     const int ntile = (nd + 31) / 32;
     double* dpart = (double*)((char*)partial + (partial_bytes - diag_bytes));
-    int64_t nchunk = std::max<int64_t>(1, (4 * 152 + ntile - 1) / ntile);
+    // about 64 resident blocks of 256 threads per SM's worth of row chunks
+    int64_t nchunk = std::max<int64_t>(1, (64 * 152 + ntile - 1) / ntile);
     nchunk = std::min<int64_t>(nchunk, (int64_t)(diag_bytes / (8 * (size_t)ntile * 32 * bd)));
-    nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, (M + 63) / 64));
+    nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, (M + 255) / 256));
     int64_t rpc = (M + nchunk - 1) / nchunk;
     nchunk = (M + rpc - 1) / rpc;
+    const dim3 dg(ntile, (unsigned)nchunk);
     note_launch();
-    diag_gram_fp64_kernel<<<dim3(ntile, (unsigned)nchunk), 256, 0, s>>>(A, lda, B, ldb, M, nd, bd, rpc,
-                                                                          dpart);
+    switch (bd) {
+      case 1: diag_gram_fp64_kernel<1><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 2: diag_gram_fp64_kernel<2><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 4: diag_gram_fp64_kernel<4><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 8: diag_gram_fp64_kernel<8><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 16: diag_gram_fp64_kernel<16><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      default: diag_gram_fp64_kernel<32><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+    }
     const int64_t tot2 = (int64_t)nd * bd;
     note_launch();
     diag_reduce_kernel<<<(unsigned)((tot2 + 255) / 256), 256, 0, s>>>(dpart, (int)nchunk, ntile * 32, nd,
@@ -982,69 +1011,136 @@ size_t tc_tallgemm_work_bytes(int n1, int n2) {
 }
 
 // ----------------------------------------------------------------- nonlocal (binary32)
-__global__ void nl_project32_kernel(const int64_t* __restrict__ site_ptr,
-                                    const int32_t* __restrict__ site_dof,
-                                    const float* __restrict__ site_c, const float* __restrict__ Y,
-                                    int64_t ldy, int ncol, float* __restrict__ Z) {
+// Z[4 s + t][c] = sum over the support of site s of C~[s, j, t] Y[j][c].
+// Block: one site x 128 columns, 8 warps; a lane owns 4 consecutive columns
+// (16-byte loads).  Warp w takes the support entries w, w + 8, ...; four of
+// them per step, with their unknown indices and rows loaded before the FMAs so
+// four row gathers are in flight per lane.  Partial sums are combined in a
+// fixed order (deterministic).
+__global__ void __launch_bounds__(256) nl_project32_kernel(const int64_t* __restrict__ site_ptr,
+                                                           const int32_t* __restrict__ site_dof,
+                                                           const float* __restrict__ site_c,
+                                                           const float* __restrict__ Y, int64_t ldy,
+                                                           int ncol, float* __restrict__ Z) {
   const int s = blockIdx.x;
-  const int c = blockIdx.y * 32 + threadIdx.x % 32;
-  const int w = threadIdx.x / 32;  // 8 warps
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (c < ncol) {
-    for (int64_t e = site_ptr[s] + w; e < site_ptr[s + 1]; e += 8) {
-      const float y = Y[(int64_t)site_dof[e] * ldy + c];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cb = blockIdx.y * 128;
+  const int c0 = cb + lane * 4;
+  const bool vec = ((ldy & 3) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) && c0 + 4 <= ncol;
+  float acc[4][4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) acc[t] = fmaf(site_c[4 * e + t], y, acc[t]);
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
+  const int64_t e0 = site_ptr[s], e1 = site_ptr[s + 1];
+  for (int64_t e = e0 + w; e < e1; e += 32) {
+    int64_t row[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) row[q] = e + 8 * q < e1 ? (int64_t)site_dof[e + 8 * q] : -1;
+    float y[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[q][u] = 0.f;
+      if (row[q] < 0) continue;
+      const float* src = Y + row[q] * ldy + c0;
+      if (vec) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+        y[q][0] = v.x; y[q][1] = v.y; y[q][2] = v.z; y[q][3] = v.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c0 + u < ncol) y[q][u] = __ldg(src + u);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (row[q] < 0) continue;
+      const float4 cf = __ldg(reinterpret_cast<const float4*>(site_c) + (e + 8 * q));
+      const float cq[4] = {cf.x, cf.y, cf.z, cf.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[t][u] = fmaf(cq[t], y[q][u], acc[t][u]);
     }
   }
-  __shared__ float red[8][4][32];
+  __shared__ float red[8][4][128];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) red[w][t][threadIdx.x % 32] = acc[t];
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[w][t][lane * 4 + u] = acc[t][u];
   __syncthreads();
-  if (w == 0 && c < ncol) {
+  for (int o = threadIdx.x; o < 512; o += 256) {
+    const int t = o >> 7, cc = o & 127;
+    if (cb + cc >= ncol) continue;
+    float v = 0.f;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float v = 0.f;
-      for (int q = 0; q < 8; ++q) v += red[q][t][threadIdx.x];
-      Z[(int64_t)(4 * s + t) * ncol + c] = v;
-    }
+    for (int q = 0; q < 8; ++q) v += red[q][t][cc];
+    Z[(int64_t)(4 * s + t) * ncol + cb + cc] = v;
   }
 }
 
+// NL[j][c] = sum over the sites s touching unknown j of sum_t h C~[s, j, t] Z[4 s + t][c]
+// (coefficients pre-multiplied by h).  Thread: one unknown, 4 consecutive columns.
 __global__ void nl_expand32_kernel(const int64_t* __restrict__ dof_ptr,
                                    const int32_t* __restrict__ dof_site,
                                    const float* __restrict__ dof_c, int64_t M,
                                    const float* __restrict__ Z, int ncol, float* __restrict__ NL,
-                                   int64_t ldn) {
+                                   int64_t ldn, int vec) {
+  const int nq = (ncol + 3) >> 2;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * ncol) return;
-  const int64_t j = idx / ncol;
-  const int c = (int)(idx - j * ncol);
-  float v = 0.f;
+  if (idx >= M * nq) return;
+  const int64_t j = idx / nq;
+  const int c0 = (int)(idx - j * nq) * 4;
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
   for (int64_t e = dof_ptr[j]; e < dof_ptr[j + 1]; ++e) {
     const int64_t s = dof_site[e];
+    const float4 cf = __ldg(reinterpret_cast<const float4*>(dof_c) + e);
+    const float cq[4] = {cf.x, cf.y, cf.z, cf.w};
 #pragma unroll
-    for (int t = 0; t < 4; ++t) v = fmaf(dof_c[4 * e + t], Z[(4 * s + t) * ncol + c], v);
+    for (int t = 0; t < 4; ++t) {
+      const float* zr = Z + (4 * s + t) * ncol + c0;
+      if (vec) {
+        const float4 z = __ldg(reinterpret_cast<const float4*>(zr));
+        v[0] = fmaf(cq[t], z.x, v[0]);
+        v[1] = fmaf(cq[t], z.y, v[1]);
+        v[2] = fmaf(cq[t], z.z, v[2]);
+        v[3] = fmaf(cq[t], z.w, v[3]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c0 + u < ncol) v[u] = fmaf(cq[t], __ldg(zr + u), v[u]);
+      }
+    }
   }
-  NL[j * ldn + c] = v;
+  float* out = NL + j * ldn + c0;
+  if (vec && (ldn & 3) == 0) {
+    *reinterpret_cast<float4*>(out) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c0 + u < ncol) out[u] = v[u];
+  }
 }
 
 cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, const float* site_c,
                           int nsite, const float* Y, int64_t ldy, int ncol, float* Z, cudaStream_t s) {
   if (nsite == 0 || ncol == 0) return cudaSuccess;
   note_launch();
-  nl_project32_kernel<<<dim3(nsite, (ncol + 31) / 32), 256, 0, s>>>(site_ptr, site_dof, site_c, Y, ldy,
-                                                                     ncol, Z);
+  nl_project32_kernel<<<dim3(nsite, (ncol + 127) / 128), 256, 0, s>>>(site_ptr, site_dof, site_c, Y,
+                                                                       ldy, ncol, Z);
   return cudaGetLastError();
 }
 
 cudaError_t tc_nl_expand(const int64_t* dof_ptr, const int32_t* dof_site, const float* dof_c, int64_t M,
                          const float* Z, int ncol, float* NL, int64_t ldn, cudaStream_t s) {
-  const int64_t tot = M * ncol;
+  const int64_t tot = M * ((ncol + 3) / 4);
   if (tot == 0) return cudaSuccess;
+  const int vec = (ncol & 3) == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(NL) & 15) == 0;
   note_launch();
   nl_expand32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dof_ptr, dof_site, dof_c, M, Z, ncol,
-                                                                    NL, ldn);
+                                                                    NL, ldn, vec);
   return cudaGetLastError();
 }
 

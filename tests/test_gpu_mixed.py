@@ -91,7 +91,7 @@ def test_autotune_keeps_x_and_picks_a_candidate(case):
     X0 = _x32(6, prob.ndofs, 150)
     X = torch.tensor(X0, device=DEV)
     blk, tile, ms = ctx.autotune(X, prec="mixed")
-    assert (blk, tile) in ms and all(v > 0 for v in ms.values())
+    assert (blk, tile) in ms and all(v > 0 for v in ms.values())   # every candidate fits here
     assert ms[(blk, tile)] == min(ms.values())
     assert np.array_equal(X.cpu().numpy(), X0)
     Y = torch.empty_like(X)
