@@ -49,10 +49,11 @@ def parse():
                     help="wavefunction block of the filter (0: chosen by the autotuner)")
     ap.add_argument("--tile", type=int, default=64, choices=[64, 128],
                     help="cell-kernel column tile when --block is given")
-    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "c3", "serving"],
+    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "c3", "batch", "serving"],
                     help="chfsi: the 16^3-cell p=6 FCC system; c3: 20^3 cells p=7 with "
-                         "projectors, N=3000 (block 1100); serving: request stream through "
-                         "the continuous-batching server")
+                         "projectors, N=3000 (block 1100); batch: 64 small Dirichlet systems "
+                         "filtered together; serving: request stream through the "
+                         "continuous-batching server")
     ap.add_argument("--requests", type=int, default=12, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrently admitted requests")
     ap.add_argument("--dof-max", type=float, default=2.0e6, help="serving: largest request (unknowns)")
@@ -563,10 +564,95 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batching
+def run_batch(args):
+    """64 uneven Dirichlet systems (p = 5): the batched Chebyshev filter (one
+    persistent launch per degree step for all systems, CUDA graph, autotuned
+    tile) against filtering the systems one after another, and one batched
+    ChFSI iteration (binary32 filter, binary64 CholGS/RR per system)."""
+    import torch
+    from paper_1903_10959_gb300 import Batch, Context, workloads as W
+    systems = W.batched_systems()
+    stream = torch.cuda.current_stream()
+    ctxs, X, bnd = [], [], []
+    for s in systems:
+        c = Context(s.ncell, s.L, s.p, periodic=False, stream=stream)
+        c.set_potential_gaussians(s.centres, s.depths, s.widths)
+        c.build()
+        x = torch.empty((c.ndofs, s.n_sub), dtype=torch.float32, device="cuda")
+        c.fill_uniform(x, s.seed, prec="mixed")
+        ctxs.append(c)
+        X.append(x)
+        bnd.append(c.bounds(20, s.seed))
+    bnd = np.array(bnd)
+    a, a0 = 0.2 * bnd, np.full(len(bnd), -3.0)
+    m = systems[0].degree
+    ne = (systems[0].p + 1) ** 3
+    flops = sum(s.ncell ** 3 * 2 * ne * ne * s.n_sub for s in systems) * m
+    bt = Batch(ctxs, stream=stream)
+    choice, cand_ms = bt.autotune(X, prec="mixed")
+    cands = bt.candidates()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    t_batch = timed(lambda: bt.filter(X, m, a, bnd, a0, prec="mixed"), args.steps)
+
+    def seq():
+        for c, x, ai, bi, a0i in zip(ctxs, X, a, bnd, a0):
+            c.filter(x, m, float(ai), float(bi), float(a0i), prec="mixed")
+    t_seq = timed(seq, args.steps)
+    X64 = []
+    for c, s, x in zip(ctxs, systems, X):            # fresh start blocks (the filtered ones are
+        x64 = torch.empty(x.shape, dtype=torch.float64, device="cuda")   # nearly rank-deficient)
+        c.fill_uniform(x64, s.seed + 1, prec="fp64")
+        X64.append(x64)
+    evs = bt.solve(X64, 1, m, bnd * 1.02)           # warm-up of the per-system solver state
+    t_solve = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02), 1)
+    clk = clocks.stop()
+    tf32_peak = 1672.5 * 1.1 / 2.25
+    line = {
+        "metric": "batched Chebyshev filter aggregate TFLOP/s (64 Dirichlet systems, p=5)",
+        "value": flops / t_batch / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "config": {"workload": "64 Dirichlet Gaussian-well systems, 4-12 cells per side, p=5, "
+                               "h=1.5, N log-uniform 16-400, degree %d" % m,
+                   "unknowns_total": int(sum(c.ndofs for c in ctxs)),
+                   "columns_total": int(sum(s.n_sub for s in systems))},
+        "autotune": {"choice": cands[choice], "candidates_ms": {"%d/%d" % c: round(float(t), 3)
+                                                                 for c, t in zip(cands, cand_ms)}},
+        "filter_s_batched": t_batch, "filter_s_sequential": t_seq,
+        "speedup_vs_sequential": t_seq / t_batch,
+        "tensor_frac_of_3xtf32_peak": flops / t_batch / 1e12 / (tf32_peak / 3),
+        "batched_chfsi_iteration_s": t_solve,
+        "clocks": clk,
+    }
+    del evs
+    print(json.dumps(line), flush=True)
+    bt.destroy()
+    for c in ctxs:
+        c.destroy()
+
+
 def main():
     args = parse()
     if args.workload == "serving" and args.impl != "reference":
         run_serving(args)
+        return
+    if args.workload == "batch" and args.impl != "reference":
+        run_batch(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -244,8 +244,9 @@ int64_t      chfsi_kernel_launches(void);
 /* ---------------------------------------------------------------- batching
  * Many independent systems of the same FE degree (typically small and of
  * uneven size) filtered together on the tensor cores.  Per Chebyshev degree
- * step one persistent launch of the cell kernel covers the (system, cell,
- * column-tile) items of every system and one launch of the assembly kernel
+ * step one launch of the cell kernel (a grid over, or a persistent loop over,
+ * the (system, cell, column-tile) items of every system) and one launch of
+ * the assembly kernel
  * covers every unknown of every system; the whole degree-m filter is
  * captured once into a CUDA graph and replayed while the buffers, widths,
  * degree and tile choice stay the same (the recurrence scalars live in device
@@ -275,8 +276,14 @@ chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t
                                   double* ms_out);
 
 /* Candidate tile configurations: fills up to max (column tile, stages) pairs,
- * returns their number. */
+ * returns their number.  Stages -1 denotes the non-persistent multi-system
+ * cell kernel (one CTA per (system, cell, 64-column tile) item, two CTAs per
+ * SM), the default before autotuning; the others are the persistent kernel. */
 int          chfsi_batch_candidates(const chfsi_batch* b, int* bn_out, int* stages_out, int max);
+
+/* Select candidate k of chfsi_batch_candidates for later filter calls (as the
+ * autotuner would).  CHFSI_ERR_ARG for an index out of range. */
+chfsi_status chfsi_batch_set_candidate(chfsi_batch* b, int k);
 
 /* ChFSI on every system: X[s] (device, binary64, M_s x n[s], in/out start
  * block), bnd[s] the upper bound of spec(H~_s); per iteration the batched

@@ -96,6 +96,7 @@ _SIGS = {
     "chfsi_batch_autotune": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int),
                                        C.c_int, C.POINTER(C.c_int), _dp]),
     "chfsi_batch_candidates": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]),
+    "chfsi_batch_set_candidate": (C.c_int, [_vp, C.c_int]),
     "chfsi_batch_solve": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int), C.c_int,
                                     C.c_int, _dp, C.c_int, C.c_int, C.POINTER(_dp)]),
     "chfsi_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_vp)]),
@@ -387,6 +388,9 @@ class Batch:
         bn, st = (C.c_int * k)(), (C.c_int * k)()
         self._lib.chfsi_batch_candidates(self._h, bn, st, k)
         return list(zip(list(bn), list(st)))
+
+    def set_candidate(self, k):
+        self._check(self._lib.chfsi_batch_set_candidate(self._h, int(k)))
 
     def autotune(self, X, prec="mixed"):
         pr = _prec(prec)

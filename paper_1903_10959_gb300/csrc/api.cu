@@ -170,7 +170,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   if (prec == CHFSI_FP64 && (st = grow(ctx, ctx->Wb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
   const bool nl = ctx->hproj.nsite > 0;
   if (nl) {
-    if ((st = grow(ctx, ctx->NLb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
+    if (prec == CHFSI_FP64 && (st = grow(ctx, ctx->NLb, (size_t)m.ndofs * B * es)) != CHFSI_OK) return st;
     if ((st = grow(ctx, ctx->Zb, (size_t)4 * ctx->hproj.nsite * B * es)) != CHFSI_OK) return st;
   }
   const int ncolour = (int)m.colour_offsets.size() - 1;
@@ -209,12 +209,10 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
                   std::string("tensor-core cell data: ") + cudaGetErrorString(pe));
     }
   }
-  if (nl) {
+  if (nl) {   // projection Z = C~^T Y; the expansion is fused into the assembly
     KTimer kt(ctx, 2);
     CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
                      (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
-    CK(tc_nl_expand(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c32, m.ndofs,
-                    (const float*)ctx->Zb.ptr, ncol, (float*)ctx->NLb.ptr, B, ctx->stream));
   }
   // owner-computes: dense cell blocks R_e (one launch over all cells), then the
   // fixed-order assembly fused with the Chebyshev update
@@ -233,11 +231,28 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
   }
   KTimer kt(ctx, 1);
-  CK(tc_assemble_launch(ctx->d_node_ptr, ctx->d_node_ent, m.ndofs, ncol, (const float*)ctx->Rb.ptr,
-                        (const float*)Yin, ld_in, (float*)Yout, ld_out,
-                        beta != 0.0 ? (const float*)Yprev : nullptr, ld_prev,
-                        nl ? (const float*)ctx->NLb.ptr : nullptr, B, (float)alpha, (float)beta,
-                        (float)shift, ctx->stream));
+  AssembleParams ap{};
+  ap.node_ptr = ctx->d_node_ptr;
+  ap.node_ent = ctx->d_node_ent;
+  ap.M = m.ndofs;
+  ap.ncol = ncol;
+  ap.R = (const float*)ctx->Rb.ptr;
+  ap.Yin = (const float*)Yin;
+  ap.ld_in = ld_in;
+  ap.Yout = (float*)Yout;
+  ap.ld_out = ld_out;
+  ap.Yprev = beta != 0.0 ? (const float*)Yprev : nullptr;
+  ap.ld_prev = ld_prev;
+  if (nl) {
+    ap.dof_ptr = ctx->d_dof_ptr;
+    ap.dof_site = ctx->d_dof_site;
+    ap.dof_c = ctx->d_dof_c32;
+    ap.Z = (const float*)ctx->Zb.ptr;
+  }
+  ap.alpha = (float)alpha;
+  ap.beta = (float)beta;
+  ap.shift = (float)shift;
+  CK(tc_assemble_launch(ap, ctx->stream));
   return CHFSI_OK;
 }
 

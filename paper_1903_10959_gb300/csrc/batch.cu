@@ -24,19 +24,7 @@ namespace chfsi {
 
 __device__ int g_batch_status = 0;
 
-struct BSys {
-  const float* A;          // split cell matrices (tc_pack layout)
-  const int32_t* dofmap;
-  const float* Y[2];       // recurrence buffers: Y[0] = caller block, Y[1] = scratch
-  int64_t ldY[2];
-  float* R;                // dense cell blocks, ncells * ne * ncol
-  const int32_t* node_ptr;
-  const int32_t* node_ent;
-  int64_t ncells, M;
-  int ncol, tiles;
-  int64_t item0;           // first (cell, tile) item of this system
-  int64_t q0;              // first (unknown, column quad) of this system
-};
+using BSys = TcBatchSys;
 
 struct BParams {
   const BSys* sys;
@@ -285,10 +273,10 @@ __global__ void __launch_bounds__(320, 1) tc_cell_batched_kernel(BParams P) {
       }
       tc_fence_after();
       const bool run = __all_sync(0xffffffffu, okw);
-      const bool vst = (sy.ncol & 3) == 0;
+      const bool vst = (sy.ldr & 3) == 0;
       for (int t = 0; t < mt; ++t) {
         const int l = t * 128 + qd * 32 + lane;
-        float* dst = sy.R + (I.e * ne + l) * (int64_t)sy.ncol + I.c0;
+        float* dst = sy.R + (I.e * ne + l) * sy.ldr + I.c0;
         for (int cb = 0; cb < bne; cb += 16) {
           float acc[16];
           __syncwarp();
@@ -321,8 +309,10 @@ __global__ void __launch_bounds__(320, 1) tc_cell_batched_kernel(BParams P) {
 // cell rows of the unknown in ascending cell order and applies
 // Y_out = alpha (sum - shift Y_in) + beta Y_prev with the system's scalars of
 // this degree step (coef[3 * s]); beta == 0 skips the read of Y_prev.
-__global__ void tc_assemble_batched_kernel(const BSys* __restrict__ sys, int nsys, int64_t nq_total,
-                                           const float* __restrict__ coef, int parity) {
+__global__ void __launch_bounds__(256) tc_assemble_batched_kernel(const BSys* __restrict__ sys, int nsys,
+                                                                   int64_t nq_total,
+                                                                   const float* __restrict__ coef,
+                                                                   int parity) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nq_total) return;
   int lo = 0, hi = nsys - 1;
@@ -332,24 +322,48 @@ __global__ void tc_assemble_batched_kernel(const BSys* __restrict__ sys, int nsy
     else hi = mid - 1;
   }
   const BSys& sy = sys[lo];
-  const int nq = (sy.ncol + 3) / 4;
+  const int ncol = sy.ncol;
+  const int nq = (ncol + 3) / 4;
   const int64_t li = idx - sy.q0;
   const int64_t j = li / nq;
   const int c = (int)(li - j * nq) * 4;
-  const int nc = min(4, sy.ncol - c);
+  const int nc = min(4, ncol - c);
   const float alpha = coef[3 * lo], beta = coef[3 * lo + 1], shift = coef[3 * lo + 2];
   const float* Yin = sy.Y[parity];
   float* Yout = const_cast<float*>(sy.Y[1 - parity]);
-  const int64_t ldi = sy.ldY[parity], ldo = sy.ldY[1 - parity];
+  const int64_t ldi = sy.ldY[parity], ldo = sy.ldY[1 - parity], ldr = sy.ldr;
   float sum[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k = sy.node_ptr[j]; k < sy.node_ptr[j + 1]; ++k) {
-    const float* src = sy.R + (int64_t)sy.node_ent[k] * sy.ncol + c;
-    for (int u = 0; u < nc; ++u) sum[u] += __ldg(src + u);
+  for (int k = sy.node_ptr[j]; k < sy.node_ptr[j + 1]; ++k) {   // R rows are 16-byte aligned
+    const float4 r = __ldg(reinterpret_cast<const float4*>(sy.R + (int64_t)sy.node_ent[k] * ldr + c));
+    sum[0] += r.x; sum[1] += r.y; sum[2] += r.z; sum[3] += r.w;
   }
-  for (int u = 0; u < nc; ++u) {
-    float out = alpha * (sum[u] - shift * Yin[j * ldi + c + u]);
-    if (beta != 0.f) out = fmaf(beta, Yout[j * ldo + c + u], out);
-    Yout[j * ldo + c + u] = out;
+  const bool vin = nc == 4 && (ldi & 3) == 0 && ((reinterpret_cast<uintptr_t>(Yin) & 15) == 0);
+  const bool vout = nc == 4 && (ldo & 3) == 0 && ((reinterpret_cast<uintptr_t>(Yout) & 15) == 0);
+  float yin[4] = {0.f, 0.f, 0.f, 0.f}, yp[4] = {0.f, 0.f, 0.f, 0.f};
+  if (vin) {
+    const float4 t = *reinterpret_cast<const float4*>(Yin + j * ldi + c);
+    yin[0] = t.x; yin[1] = t.y; yin[2] = t.z; yin[3] = t.w;
+  } else {
+    for (int u = 0; u < nc; ++u) yin[u] = Yin[j * ldi + c + u];
+  }
+  if (beta != 0.f) {
+    if (vout) {
+      const float4 t = *reinterpret_cast<const float4*>(Yout + j * ldo + c);
+      yp[0] = t.x; yp[1] = t.y; yp[2] = t.z; yp[3] = t.w;
+    } else {
+      for (int u = 0; u < nc; ++u) yp[u] = Yout[j * ldo + c + u];
+    }
+  }
+  float out[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    out[u] = alpha * (sum[u] - shift * yin[u]);
+    if (beta != 0.f) out[u] = fmaf(beta, yp[u], out[u]);
+  }
+  if (vout) {
+    *reinterpret_cast<float4*>(Yout + j * ldo + c) = make_float4(out[0], out[1], out[2], out[3]);
+  } else {
+    for (int u = 0; u < nc; ++u) Yout[j * ldo + c + u] = out[u];
   }
 }
 
@@ -375,7 +389,7 @@ struct chfsi_batch {
   std::vector<int> g_ncol;
   int g_degree = -1, g_split3 = -1, g_bn = -1, g_S = -1;
   // tile choice: BN (32 / 64) and stages; set by the autotuner
-  int bn = 64, S = 0;
+  int bn = 64, S = -1;             // S < 0: the non-persistent multi-system kernel
   int nsm = 0;
   std::string err;
 };
@@ -418,16 +432,18 @@ cudaError_t batch_describe(chfsi_batch* b, float* const* X, const int64_t* ldx, 
     chfsi_ctx* c = b->ctx[i];
     const HostMesh& m = c->mesh;
     cudaError_t e;
-    if ((e = ensure_dbuf(b->T1[i], (size_t)m.ndofs * ncol[i] * 4 + 16)) != cudaSuccess) return e;
-    if ((e = ensure_dbuf(b->R[i], (size_t)m.ncells * m.ne * ncol[i] * 4 + 16)) != cudaSuccess) return e;
+    const int64_t ld4 = (ncol[i] + 3) / 4 * 4;   // 16-byte rows for the scratch and R
+    if ((e = ensure_dbuf(b->T1[i], (size_t)m.ndofs * ld4 * 4 + 16)) != cudaSuccess) return e;
+    if ((e = ensure_dbuf(b->R[i], (size_t)m.ncells * m.ne * ld4 * 4 + 16)) != cudaSuccess) return e;
     BSys& sy = b->h_sys[i];
     sy.A = c->tc.hi;
     sy.dofmap = c->d_dofmap;
     sy.Y[0] = X[i];
     sy.ldY[0] = ldx[i];
     sy.Y[1] = (const float*)b->T1[i].ptr;
-    sy.ldY[1] = ncol[i];
+    sy.ldY[1] = ld4;
     sy.R = (float*)b->R[i].ptr;
+    sy.ldr = ld4;
     sy.node_ptr = c->d_node_ptr;
     sy.node_ent = c->d_node_ent;
     sy.ncells = m.ncells;
@@ -454,8 +470,11 @@ cudaError_t batch_enqueue(chfsi_batch* b, float* const* X, const int* ncol, int 
   if (e != cudaSuccess) return e;
   for (int k = 1; k <= degree; ++k) {
     const int parity = (k - 1) & 1;
-    e = bn == 64 ? launch_batched_cell<64>(b, split3, S, parity, b->stream)
-                 : launch_batched_cell<32>(b, split3, S, parity, b->stream);
+    if (S < 0)
+      e = tc_cell_multi_launch(b->d_sys, n, b->nitems, b->ne, b->mt, b->nk, split3, parity, b->stream);
+    else
+      e = bn == 64 ? launch_batched_cell<64>(b, split3, S, parity, b->stream)
+                   : launch_batched_cell<32>(b, split3, S, parity, b->stream);
     if (e != cudaSuccess) return e;
     note_launch();
     tc_assemble_batched_kernel<<<(unsigned)((b->nq + 255) / 256), 256, 0, b->stream>>>(
@@ -465,8 +484,9 @@ cudaError_t batch_enqueue(chfsi_batch* b, float* const* X, const int* ncol, int 
   if (degree & 1)   // Y_m sits in the scratch buffer: copy it back into X
     for (int i = 0; i < n; ++i) {
       const HostMesh& m = b->ctx[i]->mesh;
-      e = cudaMemcpy2DAsync(X[i], b->h_sys[i].ldY[0] * 4, b->T1[i].ptr, (size_t)ncol[i] * 4,
-                            (size_t)ncol[i] * 4, m.ndofs, cudaMemcpyDeviceToDevice, b->stream);
+      e = cudaMemcpy2DAsync(X[i], b->h_sys[i].ldY[0] * 4, b->T1[i].ptr,
+                            (size_t)b->h_sys[i].ldY[1] * 4, (size_t)ncol[i] * 4, m.ndofs,
+                            cudaMemcpyDeviceToDevice, b->stream);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
@@ -535,7 +555,14 @@ chfsi_status batch_prepare(chfsi_batch* b, float* const* X, const int64_t* ldx, 
   return CHFSI_OK;
 }
 
+int batch_read_status_persistent(cudaStream_t s);
+// Status words of both cell kernels (persistent batched, multi-system).
 int batch_read_status(cudaStream_t s) {
+  const int a = batch_read_status_persistent(s);
+  const int c = tc_read_status(s);
+  return a ? a : c;
+}
+int batch_read_status_persistent(cudaStream_t s) {
   int v = 0;
   cudaMemcpyFromSymbolAsync(&v, g_batch_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -583,6 +610,7 @@ chfsi_status chfsi_batch_create(int n, chfsi_ctx* const* ctxs, void* stream, chf
     b->own_stream = true;
   }
   // kernel attributes are set here: they may not be changed during stream capture
+  tc_cell_prepare();
   cudaFuncSetAttribute(tc_cell_batched_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(tc_cell_batched_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   int dev = 0;
@@ -626,7 +654,7 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
     if (!(a0[i] < a[i]) || !(a[i] < bb[i])) return bfail(b, CHFSI_ERR_ARG, "need a0 < a < b");
   const int split3 = prec == CHFSI_MIXED_TF32X3;
   const int bn = b->bn;
-  const int S = b->S > 0 ? b->S : default_stages(b, bn, split3);
+  const int S = b->S != 0 ? b->S : default_stages(b, bn, split3);
   if (b->own_stream) cudaDeviceSynchronize();   // order after the caller's work on any stream
   // the graph is valid while pointers, widths, degree and tile choice stay the same
   bool same = b->gexec && b->g_degree == degree && b->g_split3 == split3 && b->g_bn == bn &&
@@ -678,8 +706,9 @@ chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t
   const int split3 = prec == CHFSI_MIXED_TF32X3;
   const int n = (int)b->ctx.size();
   if (b->own_stream) cudaDeviceSynchronize();
-  // candidates: column tile 64 / 32 x deepest pipeline / 4 stages
-  std::vector<std::pair<int, int>> cand;
+  // candidates: the non-persistent multi-system kernel (64-column tiles), then
+  // the persistent kernel with column tile 64 / 32 x deepest pipeline / 4 stages
+  std::vector<std::pair<int, int>> cand{{64, -1}};
   for (int bn : {64, 32}) {
     const int smax = default_stages(b, bn, split3);
     cand.push_back({bn, smax});
@@ -726,10 +755,27 @@ chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t
   return CHFSI_OK;
 }
 
+chfsi_status chfsi_batch_set_candidate(chfsi_batch* b, int k) {
+  if (!b) return CHFSI_ERR_ARG;
+  const int n = chfsi_batch_candidates(b, nullptr, nullptr, 0);
+  if (k < 0 || k >= n) return bfail(b, CHFSI_ERR_ARG, "no such candidate");
+  std::vector<int> bn(n), st(n);
+  chfsi_batch_candidates(b, bn.data(), st.data(), n);
+  b->bn = bn[k];
+  b->S = st[k];
+  batch_free_graph(b);
+  return CHFSI_OK;
+}
+
 int chfsi_batch_candidates(const chfsi_batch* b, int* bn_out, int* stages_out, int max) {
   if (!b) return 0;
   int k = 0;
   const int split3 = 1;
+  if (max > 0) {
+    if (bn_out) bn_out[0] = 64;
+    if (stages_out) stages_out[0] = -1;
+  }
+  ++k;
   for (int bn : {64, 32}) {
     const int smax = bn == 64 ? b_max_stages<64>(b->mt, split3) : b_max_stages<32>(b->mt, split3);
     for (int S : {smax, 4}) {

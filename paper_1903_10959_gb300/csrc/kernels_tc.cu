@@ -116,14 +116,18 @@ struct CellSmem {
 };
 
 // Stage sizes of the cell kernel.  64-column tiles keep two CTAs per SM
-// (about 110 KB each); 128-column tiles take the SM alone (TMEM holds one
-// CTA's mt x 128 accumulator columns) and use up to 200 KB of stages.
+// (about 110 KB each; 113 KB, three stages, for four 128-row tiles), three
+// when the cell has at most two 128-row tiles (p <= 5: 72 KB each, TMEM 3 x
+// 128 columns); 128-column tiles take the SM
+// alone (TMEM holds one CTA's mt x 128 accumulator columns) and use up to
+// 200 KB of stages.
 __host__ __device__ inline CellSmem cell_smem(int mt, int split3, int bn = CELL_BN) {
   CellSmem c;
   c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
   c.y_bytes = bn * CELL_KC * 4 * 2;
   const int stage = c.a_bytes + c.y_bytes;
-  int S = ((bn > 64 ? 200 : 110) * 1024 - 3072) / stage;
+  const int budget_kb = bn > 64 ? 200 : (mt <= 2 ? 72 : (mt == 3 ? 110 : 113));
+  int S = (budget_kb * 1024 - 3072) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
   c.stages = S;
   c.total = S * stage + 3072;   // + barriers, the cell's dof map (<= 512) and modes
@@ -145,14 +149,37 @@ struct RParams {
   float* R;
   int64_t ld_in;
   int ncol, ne, mt, nk, split3;
+  // multi-system mode: grid x runs over the items of all systems
+  const TcBatchSys* sys;
+  int nsys, parity;
+  int64_t ldr;              // row stride of R (>= ncol)
 };
 
-template <int BN>
+template <int BN, bool MULTI>
 __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t e = blockIdx.y;
-  const int c0 = blockIdx.x * BN;
+  int64_t e = blockIdx.y;
+  int c0 = blockIdx.x * BN;
+  if (MULTI) {   // item -> (system, cell, tile): binary search over the systems' first items
+    const int64_t item = blockIdx.x;
+    int lo = 0, hi = P.nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.sys[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    const TcBatchSys& sy = P.sys[lo];
+    const int64_t li = item - sy.item0;
+    e = li / sy.tiles;
+    c0 = (int)(li % sy.tiles) * BN;
+    P.A = sy.A;
+    P.dofmap = sy.dofmap;
+    P.Yin = sy.Y[P.parity];
+    P.ld_in = sy.ldY[P.parity];
+    P.R = sy.R;
+    P.ncol = sy.ncol;
+    P.ldr = sy.ldr;
+  }
   const int ncv = min(BN, P.ncol - c0);
   const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
   const CellSmem L = cell_smem(P.mt, P.split3, BN);
@@ -249,9 +276,8 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
     const int q = lane >> 4;
     const int cq = (lane & 15) * CPT;
     const int G = S < 4 ? S : 4;
-    for (int i = warp; i < nk && warp < G; i += G) {
-      const int s = i % S;
-      float v[4][CPT];
+    // rows l = 8 i + 4 q + a of the cell block, CPT columns per lane, zero-filled
+    auto load_chunk = [&](int i, float (&v)[4][CPT]) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int l = i * CELL_KC + q * 4 + a;
@@ -273,27 +299,36 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
           }
         }
       }
-      if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
-        atomicExch(&g_tc_status, 23);
-        *(volatile int*)abort_flag = 1;
-      }
-      if (*(volatile int*)abort_flag) break;
-      float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
-      float* yl = yh + BN * CELL_KC;
+    };
+    if (warp < G) {
+      // (a second chunk prefetched into registers measured no faster: the two
+      // co-resident CTAs per SM already overlap the gathers)
+      float v[4][CPT];
+      for (int i = warp; i < nk; i += G) {
+        const int s = i % S;
+        load_chunk(i, v);
+        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+          atomicExch(&g_tc_status, 23);
+          *(volatile int*)abort_flag = 1;
+        }
+        if (*(volatile int*)abort_flag) break;
+        float* yh = reinterpret_cast<float*>(smem + s * stage_bytes + L.a_bytes);
+        float* yl = yh + BN * CELL_KC;
 #pragma unroll
-      for (int u = 0; u < CPT; ++u) {
-        const int n = cq + u;
-        const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
-        float4 h, lo;
-        h.x = tf32_rna(v[0][u]); lo.x = v[0][u] - h.x;
-        h.y = tf32_rna(v[1][u]); lo.y = v[1][u] - h.y;
-        h.z = tf32_rna(v[2][u]); lo.z = v[2][u] - h.z;
-        h.w = tf32_rna(v[3][u]); lo.w = v[3][u] - h.w;
-        *reinterpret_cast<float4*>(yh + o) = h;
-        *reinterpret_cast<float4*>(yl + o) = lo;
+        for (int u = 0; u < CPT; ++u) {
+          const int n = cq + u;
+          const int o = (n >> 3) * 64 + q * 32 + (n & 7) * 4;
+          float4 h, lo;
+          h.x = tf32_rna(v[0][u]); lo.x = v[0][u] - h.x;
+          h.y = tf32_rna(v[1][u]); lo.y = v[1][u] - h.y;
+          h.z = tf32_rna(v[2][u]); lo.z = v[2][u] - h.z;
+          h.w = tf32_rna(v[3][u]); lo.w = v[3][u] - h.w;
+          *reinterpret_cast<float4*>(yh + o) = h;
+          *reinterpret_cast<float4*>(yl + o) = lo;
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(fy(s));
       }
-      fence_proxy_async_smem();
-      mbar_arrive(fy(s));
     }
     // epilogue: TMEM row -> R row (16-byte stores only)
     const bool okacc = mbar_wait(accb, 0);
@@ -303,10 +338,10 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
     }
     tc_fence_after();
     const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
-    const bool vst = (P.ncol & 3) == 0;
+    const bool vst = (P.ldr & 3) == 0;
     for (int t = 0; t < P.mt; ++t) {
       const int l = t * 128 + warp * 32 + lane;
-      float* dst = P.R + ((int64_t)e * ne + l) * P.ncol + c0;
+      float* dst = P.R + ((int64_t)e * ne + l) * P.ldr + c0;
       for (int cb = 0; cb < bne; cb += 16) {
         float acc[16];
         __syncwarp();
@@ -335,73 +370,135 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.hi) return cudaErrorInvalidValue;
-  RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3};
-  static std::once_flag attr;
-  std::call_once(attr, [&] {
-    cudaFuncSetAttribute(tc_cell_r_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(tc_cell_r_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-  });
+  RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3,
+            nullptr, 0, 0, a.ncol};
+  tc_cell_prepare();
   const int bn = a.tile == 128 ? 128 : 64;
   const CellSmem L = cell_smem(d.mt, a.split3, bn);
   dim3 grid((a.ncol + bn - 1) / bn, (unsigned)a.ncells);
   note_launch();
   if (bn == 128)
-    tc_cell_r_kernel<128><<<grid, CELL_THREADS, L.total, s>>>(P);
+    tc_cell_r_kernel<128, false><<<grid, CELL_THREADS, L.total, s>>>(P);
   else
-    tc_cell_r_kernel<64><<<grid, CELL_THREADS, L.total, s>>>(P);
+    tc_cell_r_kernel<64, false><<<grid, CELL_THREADS, L.total, s>>>(P);
+  return cudaGetLastError();
+}
+
+void tc_cell_prepare() {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_cell_r_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_r_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(tc_cell_r_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+}
+
+cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
+                                 int nk, int split3, int parity, cudaStream_t s) {
+  if (nitems == 0 || nsys == 0) return cudaSuccess;
+  if (nitems > 0x7fffffff) return cudaErrorInvalidValue;
+  RParams P{nullptr, nullptr, nullptr, nullptr, 0, 0, ne, mt, nk, split3, d_sys, nsys, parity, 0};
+  tc_cell_prepare();
+  const CellSmem L = cell_smem(mt, split3, 64);
+  note_launch();
+  tc_cell_r_kernel<64, true><<<(unsigned)nitems, CELL_THREADS, L.total, s>>>(P);
   return cudaGetLastError();
 }
 
 // Each thread: one unknown j, 4 consecutive columns.  Sums the cell rows
-// holding j in ascending cell order, adds the projector term, applies the
-// three-term update.  Y_out may alias Y_prev (each element is read before it
-// is written by the same thread); it must not alias Y_in.
-__global__ void tc_assemble_kernel(const int32_t* __restrict__ node_ptr,
-                                   const int32_t* __restrict__ node_ent, int64_t M, int ncol,
-                                   const float* __restrict__ R, const float* __restrict__ Yin,
-                                   int64_t ld_in, float* Yout, int64_t ld_out, const float* Yprev,
-                                   int64_t ld_prev, const float* __restrict__ NL, int64_t ld_nl,
-                                   float alpha, float beta, float shift, int vec) {
-  const int nq = (ncol + 3) / 4;
+// holding j in ascending cell order, adds the projector term (when Z is set:
+// sum over the sites touching j of the h-scaled coefficients times the
+// projected block Z, the expansion half of H~_nl, in the order of j's site
+// list), then applies the three-term update.  Y_out may alias Y_prev (each
+// element is read before it is written by the same thread); it must not
+// alias Y_in.
+template <bool NL>
+__global__ void __launch_bounds__(256) tc_assemble_kernel(AssembleParams P) {
+  const int nq = (P.ncol + 3) / 4;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * nq) return;
+  if (idx >= P.M * nq) return;
   const int64_t j = idx / nq;
   const int c = (int)(idx - j * nq) * 4;
-  const int nc = min(4, ncol - c);
+  const int nc = min(4, P.ncol - c);
+  const bool v4 = P.vec && nc == 4;
   float sum[4] = {0.f, 0.f, 0.f, 0.f};
-  const int k0 = node_ptr[j], k1 = node_ptr[j + 1];
+  const int k0 = P.node_ptr[j], k1 = P.node_ptr[j + 1];
   for (int k = k0; k < k1; ++k) {
-    const float* src = R + (int64_t)node_ent[k] * ncol + c;
-    if (vec && nc == 4) {
+    const float* src = P.R + (int64_t)P.node_ent[k] * P.ncol + c;
+    if (v4) {
       const float4 r = __ldg(reinterpret_cast<const float4*>(src));
       sum[0] += r.x; sum[1] += r.y; sum[2] += r.z; sum[3] += r.w;
     } else {
       for (int u = 0; u < nc; ++u) sum[u] += __ldg(src + u);
     }
   }
+  if (NL) {
+    float nl[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t e = P.dof_ptr[j]; e < P.dof_ptr[j + 1]; ++e) {
+      const int64_t st = P.dof_site[e];
+      const float4 cf = __ldg(reinterpret_cast<const float4*>(P.dof_c) + e);
+      const float cq[4] = {cf.x, cf.y, cf.z, cf.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float* zr = P.Z + (4 * st + t) * P.ncol + c;
+        if (v4) {
+          const float4 z = __ldg(reinterpret_cast<const float4*>(zr));
+          nl[0] = fmaf(cq[t], z.x, nl[0]);
+          nl[1] = fmaf(cq[t], z.y, nl[1]);
+          nl[2] = fmaf(cq[t], z.z, nl[2]);
+          nl[3] = fmaf(cq[t], z.w, nl[3]);
+        } else {
+          for (int u = 0; u < nc; ++u) nl[u] = fmaf(cq[t], __ldg(zr + u), nl[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sum[u] += nl[u];
+  }
+  float yin[4] = {0.f, 0.f, 0.f, 0.f}, yp[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool vin = v4 && P.vin, vprev = v4 && P.vprev, vout = v4 && P.vout;
+  if (vin) {
+    const float4 t = *reinterpret_cast<const float4*>(P.Yin + j * P.ld_in + c);
+    yin[0] = t.x; yin[1] = t.y; yin[2] = t.z; yin[3] = t.w;
+  } else {
+    for (int u = 0; u < nc; ++u) yin[u] = P.Yin[j * P.ld_in + c + u];
+  }
+  if (P.Yprev) {
+    if (vprev) {
+      const float4 t = *reinterpret_cast<const float4*>(P.Yprev + j * P.ld_prev + c);
+      yp[0] = t.x; yp[1] = t.y; yp[2] = t.z; yp[3] = t.w;
+    } else {
+      for (int u = 0; u < nc; ++u) yp[u] = P.Yprev[j * P.ld_prev + c + u];
+    }
+  }
+  float out[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    if (u >= nc) break;
-    float v = sum[u];
-    if (NL) v += NL[j * ld_nl + c + u];
-    float out = alpha * (v - shift * Yin[j * ld_in + c + u]);
-    if (Yprev) out = fmaf(beta, Yprev[j * ld_prev + c + u], out);
-    Yout[j * ld_out + c + u] = out;
+    out[u] = P.alpha * (sum[u] - P.shift * yin[u]);
+    if (P.Yprev) out[u] = fmaf(P.beta, yp[u], out[u]);
+  }
+  float* dst = P.Yout + j * P.ld_out + c;
+  if (vout) {
+    *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+  } else {
+    for (int u = 0; u < nc; ++u) dst[u] = out[u];
   }
 }
 
-cudaError_t tc_assemble_launch(const int32_t* node_ptr, const int32_t* node_ent, int64_t M,
-                               int ncol, const float* R, const float* Yin, int64_t ld_in,
-                               float* Yout, int64_t ld_out, const float* Yprev, int64_t ld_prev,
-                               const float* NL, int64_t ld_nl, float alpha, float beta,
-                               float shift, cudaStream_t s) {
-  const int64_t tot = M * ((ncol + 3) / 4);
+cudaError_t tc_assemble_launch(const AssembleParams& P0, cudaStream_t s) {
+  const int64_t tot = P0.M * ((P0.ncol + 3) / 4);
   if (tot == 0) return cudaSuccess;
-  const int vec = (ncol & 3) == 0;
+  AssembleParams P = P0;
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  P.vec = (P.ncol & 3) == 0 && al16(P.R) && (!P.Z || al16(P.Z));
+  P.vin = (P.ld_in & 3) == 0 && al16(P.Yin);
+  P.vprev = P.Yprev && (P.ld_prev & 3) == 0 && al16(P.Yprev);
+  P.vout = (P.ld_out & 3) == 0 && al16(P.Yout);
   note_launch();
-  tc_assemble_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      node_ptr, node_ent, M, ncol, R, Yin, ld_in, Yout, ld_out, Yprev, ld_prev, NL, ld_nl, alpha,
-      beta, shift, vec);
+  if (P.Z)
+    tc_assemble_kernel<true><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P);
+  else
+    tc_assemble_kernel<false><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -440,32 +537,28 @@ __device__ __forceinline__ int k8_off(int n, int k) {
   return (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
 }
 
-// Load 4 rows x 4 columns (row-major source, column offset col0) and store the
-// TF32 hi / lo split transposed: per column, 4 consecutive K values as one
-// 16-byte store (K-major layout).  Rows >= r1 or columns >= nmax read as 0.
-__device__ __forceinline__ void load4x4(const float* __restrict__ X, int64_t ld, int64_t row0,
-                                        int64_t r1, int col0, int nmax, bool vec, float v[4][4]) {
+// Load 4 rows x the 4 columns col0 + 32 v (v = 0..3; one lane of a warp, so a
+// warp reads 128 contiguous bytes per row and column block): v[a][u] = X[row0 + a][col0 + 32 u].
+__device__ __forceinline__ void load4x4_strided(const float* __restrict__ X, int64_t ld, int64_t row0,
+                                                int64_t r1, int col0, int nmax, float v[4][4]) {
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int64_t row = row0 + a;
-    v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
-    if (row < r1) {
-      const float* src = X + row * ld + col0;
-      if (vec && col0 + 4 <= nmax) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(src));
-        v[a][0] = t.x; v[a][1] = t.y; v[a][2] = t.z; v[a][3] = t.w;
-      } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (col0 + u < nmax) v[a][u] = __ldg(src + u);
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int c = col0 + 32 * u;
+      v[a][u] = (row < r1 && c < nmax) ? __ldg(X + row * ld + c) : 0.f;
     }
   }
 }
-__device__ __forceinline__ void store_split_t(float* hi, float* lo, int nbase, int kq, const float v[4][4]) {
+// Store of load4x4_strided's block: column n = nbase + 32 u, its 4 K values as
+// one 16-byte store.  Eight consecutive lanes write one 128-byte core matrix,
+// so each quarter-warp phase is free of bank conflicts.
+__device__ __forceinline__ void store_split_t_strided(float* hi, float* lo, int nbase, int kq,
+                                                      const float v[4][4]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const int o = k8_off(nbase + u, kq * 4);
+    const int o = k8_off(nbase + 32 * u, kq * 4);
     float4 h, l;
     h.x = tf32_rna(v[0][u]); l.x = v[0][u] - h.x;
     h.y = tf32_rna(v[1][u]); l.y = v[1][u] - h.y;
@@ -475,7 +568,6 @@ __device__ __forceinline__ void store_split_t(float* hi, float* lo, int nbase, i
     *reinterpret_cast<float4*>(lo + o) = l;
   }
 }
-
 // Output tile 128 x 128 of C = A^T B (rows i of C <-> columns of A, columns j
 // <-> columns of B); K = unknowns, split over grid.z.  Warps 0-3 produce the
 // K-chunks (warp w: chunks w, w+4, ...; registers prefetched before the stage
@@ -547,17 +639,16 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
       umma_commit(accb);
     }
   } else {
-    const bool vecA = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
-    const bool vecB = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0);
-    const int ia = ti * GR_T + lane * 4, jb = tj * GR_T + lane * 4;
+    // lane l owns the tile columns l, l + 32, l + 64, l + 96 (conflict-free split stores)
+    const int ia = ti * GR_T + lane, jb = tj * GR_T + lane;
     for (int i = warp; i < nk; i += 4) {
       const int s = i % S;
       const int64_t row0 = r0 + (int64_t)i * GR_KC;
       float va[2][4][4], vb[2][4][4];
 #pragma unroll
       for (int kq = 0; kq < 2; ++kq) {
-        load4x4(P.A, P.lda, row0 + kq * 4, r1, ia, P.n1, vecA, va[kq]);
-        if (!same) load4x4(P.B, P.ldb, row0 + kq * 4, r1, jb, P.n2, vecB, vb[kq]);
+        load4x4_strided(P.A, P.lda, row0 + kq * 4, r1, ia, P.n1, va[kq]);
+        if (!same) load4x4_strided(P.B, P.ldb, row0 + kq * 4, r1, jb, P.n2, vb[kq]);
       }
       if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 6);
@@ -567,8 +658,8 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
       float* sh = reinterpret_cast<float*>(smem + s * SB);
 #pragma unroll
       for (int kq = 0; kq < 2; ++kq) {
-        store_split_t(sh, sh + GR_T * GR_KC, lane * 4, kq, va[kq]);
-        if (!same) store_split_t(sh + GR_T * GR_KC * 2, sh + GR_T * GR_KC * 3, lane * 4, kq, vb[kq]);
+        store_split_t_strided(sh, sh + GR_T * GR_KC, lane, kq, va[kq]);
+        if (!same) store_split_t_strided(sh + GR_T * GR_KC * 2, sh + GR_T * GR_KC * 3, lane, kq, vb[kq]);
       }
       fence_proxy_async_smem();
       mbar_arrive(full(s));
@@ -761,6 +852,7 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
 // tiles so the CTAs sharing a row block of A run together (A read once from
 // HBM).  The epilogue stages the tile in shared memory and writes whole rows.
 constexpr int TG_T = 128, TG_KC = 8, TG_THREADS = 160, TG_S = 6;
+constexpr uint32_t TG_UBYTES = 2 * TG_T * TG_KC * 4;   // U chunk, hi + lo
 static_assert(TG_S >= 4, "parity waits of the 4 producer warps need at least 4 stages");
 
 // U split layout: [col tile][k chunk][hi|lo][128 cols x 8 K in k8_off layout]
@@ -865,6 +957,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
     }
   } else {
     const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+    int last_issued = -1;
     for (int i = warp; i < nk; i += 4) {
       const int s = i % S;
       // A: rows rb + lane + 32 j, K quads kq: 4 consecutive K values (already K-major)
@@ -890,11 +983,6 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
           av[j][kq] = t;
         }
       }
-      const float4* usrc = reinterpret_cast<const float4*>(
-          P.Us + ((int64_t)tj * nkc_all + i) * 2 * TG_T * TG_KC);
-      float4 uv[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) uv[q] = __ldg(usrc + lane + 32 * q);
       if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 9);
         *(volatile int*)abort_flag = 1;
@@ -917,12 +1005,21 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
           *reinterpret_cast<float4*>(sa + TG_T * TG_KC + o) = l;
         }
       }
-      float4* udst = reinterpret_cast<float4*>(sa + 2 * TG_T * TG_KC);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) udst[lane + 32 * q] = uv[q];
+      // the pre-split U chunk (already in the operand layout): one bulk copy,
+      // counted on the same barrier; issued after the stage is free and never
+      // abandoned before this warp's arrivals, so the phase always completes
+      if (lane == 0) {
+        mbar_expect_tx(full(s), TG_UBYTES);
+        bulk_g2s(smem_u32(sa + 2 * TG_T * TG_KC),
+                 P.Us + ((int64_t)tj * nkc_all + i) * 2 * TG_T * TG_KC, TG_UBYTES, full(s));
+        last_issued = i;
+      }
       fence_proxy_async_smem();
       mbar_arrive(full(s));
     }
+    // on an abort, wait (bounded) for this warp's last bulk copy before leaving
+    if (lane == 0 && last_issued >= 0 && *(volatile int*)abort_flag)
+      mbar_wait(full(last_issued % S), (last_issued / S) & 1);
     bool okacc = true;
     if (nk > 0) {
       okacc = mbar_wait(accb, 0);
@@ -1021,10 +1118,12 @@ __global__ void __launch_bounds__(256) nl_project32_kernel(const int64_t* __rest
                                                            const int32_t* __restrict__ site_dof,
                                                            const float* __restrict__ site_c,
                                                            const float* __restrict__ Y, int64_t ldy,
-                                                           int ncol, float* __restrict__ Z) {
-  const int s = blockIdx.x;
+                                                           int ncol, int nsite,
+                                                           float* __restrict__ Z) {
+  // grid y strides over the sites; the column tiles of one site run together
+  for (int s = blockIdx.y; s < nsite; s += gridDim.y) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cb = blockIdx.y * 128;
+  const int cb = blockIdx.x * 128;
   const int c0 = cb + lane * 4;
   const bool vec = ((ldy & 3) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) && c0 + 4 <= ncol;
   float acc[4][4];
@@ -1078,48 +1177,7 @@ __global__ void __launch_bounds__(256) nl_project32_kernel(const int64_t* __rest
     for (int q = 0; q < 8; ++q) v += red[q][t][cc];
     Z[(int64_t)(4 * s + t) * ncol + cb + cc] = v;
   }
-}
-
-// NL[j][c] = sum over the sites s touching unknown j of sum_t h C~[s, j, t] Z[4 s + t][c]
-// (coefficients pre-multiplied by h).  Thread: one unknown, 4 consecutive columns.
-__global__ void nl_expand32_kernel(const int64_t* __restrict__ dof_ptr,
-                                   const int32_t* __restrict__ dof_site,
-                                   const float* __restrict__ dof_c, int64_t M,
-                                   const float* __restrict__ Z, int ncol, float* __restrict__ NL,
-                                   int64_t ldn, int vec) {
-  const int nq = (ncol + 3) >> 2;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * nq) return;
-  const int64_t j = idx / nq;
-  const int c0 = (int)(idx - j * nq) * 4;
-  float v[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int64_t e = dof_ptr[j]; e < dof_ptr[j + 1]; ++e) {
-    const int64_t s = dof_site[e];
-    const float4 cf = __ldg(reinterpret_cast<const float4*>(dof_c) + e);
-    const float cq[4] = {cf.x, cf.y, cf.z, cf.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float* zr = Z + (4 * s + t) * ncol + c0;
-      if (vec) {
-        const float4 z = __ldg(reinterpret_cast<const float4*>(zr));
-        v[0] = fmaf(cq[t], z.x, v[0]);
-        v[1] = fmaf(cq[t], z.y, v[1]);
-        v[2] = fmaf(cq[t], z.z, v[2]);
-        v[3] = fmaf(cq[t], z.w, v[3]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (c0 + u < ncol) v[u] = fmaf(cq[t], __ldg(zr + u), v[u]);
-      }
-    }
-  }
-  float* out = NL + j * ldn + c0;
-  if (vec && (ldn & 3) == 0) {
-    *reinterpret_cast<float4*>(out) = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (c0 + u < ncol) out[u] = v[u];
+  __syncthreads();   // red is reused by the next site
   }
 }
 
@@ -1127,20 +1185,9 @@ cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, cons
                           int nsite, const float* Y, int64_t ldy, int ncol, float* Z, cudaStream_t s) {
   if (nsite == 0 || ncol == 0) return cudaSuccess;
   note_launch();
-  nl_project32_kernel<<<dim3(nsite, (ncol + 127) / 128), 256, 0, s>>>(site_ptr, site_dof, site_c, Y,
-                                                                       ldy, ncol, Z);
-  return cudaGetLastError();
-}
-
-cudaError_t tc_nl_expand(const int64_t* dof_ptr, const int32_t* dof_site, const float* dof_c, int64_t M,
-                         const float* Z, int ncol, float* NL, int64_t ldn, cudaStream_t s) {
-  const int64_t tot = M * ((ncol + 3) / 4);
-  if (tot == 0) return cudaSuccess;
-  const int vec = (ncol & 3) == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0 &&
-                  (reinterpret_cast<uintptr_t>(NL) & 15) == 0;
-  note_launch();
-  nl_expand32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dof_ptr, dof_site, dof_c, M, Z, ncol,
-                                                                    NL, ldn, vec);
+  const unsigned gy = (unsigned)std::min(nsite, 65535);
+  nl_project32_kernel<<<dim3((ncol + 127) / 128, gy), 256, 0, s>>>(site_ptr, site_dof, site_c, Y, ldy,
+                                                                   ncol, nsite, Z);
   return cudaGetLastError();
 }
 

@@ -32,11 +32,51 @@ struct TcApplyArgs {
   int tile = 64;            // columns per CTA of the cell kernel: 64 or 128
 };
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
-cudaError_t tc_assemble_launch(const int32_t* node_ptr, const int32_t* node_ent, int64_t M,
-                               int ncol, const float* R, const float* Yin, int64_t ld_in,
-                               float* Yout, int64_t ld_out, const float* Yprev, int64_t ld_prev,
-                               const float* NL, int64_t ld_nl, float alpha, float beta,
-                               float shift, cudaStream_t s);
+
+// One system of a batched filter (device array, one entry per system).
+struct TcBatchSys {
+  const float* A;          // split cell matrices (tc_pack layout)
+  const int32_t* dofmap;
+  const float* Y[2];       // recurrence buffers: Y[0] = caller block, Y[1] = scratch
+  int64_t ldY[2];
+  float* R;                // dense cell blocks, ncells * ne rows of stride ldr
+  int64_t ldr;             // ncol rounded up to a multiple of 4 (16-byte rows)
+  const int32_t* node_ptr;
+  const int32_t* node_ent;
+  int64_t ncells, M;
+  int ncol, tiles;         // tiles: 64-column tiles (multi-system kernel) or BN tiles
+  int64_t item0;           // first (cell, tile) item of this system
+  int64_t q0;              // first (unknown, column quad) of this system
+};
+// The cell kernel over the (cell, 64-column tile) items of every system of a
+// batch in one launch (items of system s start at sys[s].item0, tiles fastest);
+// Y[parity] of each system is the input.  All systems share n_e / mt / nk.
+cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
+                                 int nk, int split3, int parity, cudaStream_t s);
+// Set the cell kernels' shared-memory attributes (before any stream capture).
+void tc_cell_prepare();
+// Owner-computes assembly fused with the Chebyshev update:
+// Yout = alpha (sum_cells R + H~_nl Y - shift Yin) + beta Yprev (Yprev may be null).
+struct AssembleParams {
+  const int32_t* node_ptr;    // unknown -> rows of R (CSR, ascending cell order)
+  const int32_t* node_ent;
+  int64_t M;
+  int ncol;
+  const float* R;             // dense cell blocks, (cell, local node) rows x ncol
+  const float* Yin;
+  int64_t ld_in;
+  float* Yout;
+  int64_t ld_out;
+  const float* Yprev;
+  int64_t ld_prev;
+  const int64_t* dof_ptr;     // projector expansion (when Z != null): unknown -> sites
+  const int32_t* dof_site;
+  const float* dof_c;         // 4 h-scaled coefficients per entry
+  const float* Z;             // projected block, (4 nsite) x ncol
+  float alpha, beta, shift;
+  int vec, vin, vprev, vout;  // set by the launcher
+};
+cudaError_t tc_assemble_launch(const AssembleParams& P, cudaStream_t s);
 
 cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
                      cudaStream_t s, int64_t* dev_bytes);
@@ -57,8 +97,4 @@ cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int6
 cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, const float* site_c,
                           int nsite, const float* Y, int64_t ldy, int ncol, float* Z,
                           cudaStream_t s);
-cudaError_t tc_nl_expand(const int64_t* dof_ptr, const int32_t* dof_site, const float* dof_c,
-                         int64_t M, const float* Z, int ncol, float* NL, int64_t ldn,
-                         cudaStream_t s);
-
 }  // namespace chfsi

@@ -69,11 +69,30 @@ def test_batched_filter_matches_single_and_oracle(batch_setup):
     B.destroy()
 
 
+@pytest.mark.parametrize("choice", [0, 1])
+def test_each_kernel_matches_single_system(batch_setup, choice):
+    """The multi-system grid kernel and the persistent kernel give the
+    single-system filter's result (same per-element arithmetic)."""
+    systems, ctxs = batch_setup
+    B = Batch(ctxs)
+    B.set_candidate(choice)
+    X0 = [W.start_block(31 + i, c.ndofs, s.n_sub).astype(np.float32) for i, (s, c) in
+          enumerate(zip(systems, ctxs))]
+    X = [torch.tensor(x, device=DEV) for x in X0]
+    n = len(ctxs)
+    B.filter(X, 5, np.full(n, 5.0), np.full(n, 60.0), np.full(n, -3.0))
+    for i, c in enumerate(ctxs):
+        Xs = torch.tensor(X0[i], device=DEV)
+        c.filter(Xs, 5, 5.0, 60.0, -3.0, prec="mixed")
+        assert rel_fro(X[i].cpu().numpy(), Xs.cpu().numpy()) < 1e-6
+
+
 def test_autotune_picks_a_candidate_and_keeps_results(batch_setup):
     systems, ctxs = batch_setup
     B = Batch(ctxs)
     cands = B.candidates()
-    assert len(cands) >= 2 and all(bn in (32, 64) and st >= 4 for bn, st in cands)
+    assert cands[0] == (64, -1)                      # the multi-system kernel
+    assert len(cands) >= 3 and all(bn in (32, 64) and st >= 4 for bn, st in cands[1:])
     scratch = [torch.rand((c.ndofs, s.n_sub), device=DEV) for s, c in zip(systems, ctxs)]
     choice, ms = B.autotune(scratch)
     assert 0 <= choice < len(cands) and np.all(ms > 0)
