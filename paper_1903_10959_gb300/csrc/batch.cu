@@ -237,16 +237,31 @@ __global__ void __launch_bounds__(320, 1) tc_cell_batched_kernel(BParams P) {
       if (*(volatile int*)abort_flag) break;
       float* yh = reinterpret_cast<float*>(smem + s * L.stage + L.a_bytes);
       float* yl = yh + BN * 8;
+      // the NPT K values of one column are consecutive in the K-major core
+      // matrix: one 16-byte (NPT 4) or 8-byte (NPT 2) store each for hi and lo
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int n = cq + u;
+        const int k0 = q * NPT;            // first K index of this lane within the chunk
+        const int o = (n >> 3) * 64 + (k0 >> 2) * 32 + (n & 7) * 4 + (k0 & 3);
+        float h[NPT], l[NPT];
 #pragma unroll
         for (int a = 0; a < NPT; ++a) {
-          const int k = q * NPT + a;       // K index within the chunk
-          const int o = (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
-          const float h = tf32_rna(va[a][u]);
-          yh[o] = h;
-          yl[o] = va[a][u] - h;
+          h[a] = tf32_rna(va[a][u]);
+          l[a] = va[a][u] - h[a];
+        }
+        if constexpr (NPT == 4) {
+          *reinterpret_cast<float4*>(yh + o) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(yl + o) = make_float4(l[0], l[1], l[2], l[3]);
+        } else if constexpr (NPT == 2) {
+          *reinterpret_cast<float2*>(yh + o) = make_float2(h[0], h[1]);
+          *reinterpret_cast<float2*>(yl + o) = make_float2(l[0], l[1]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < NPT; ++a) {
+            yh[o + a] = h[a];
+            yl[o + a] = l[a];
+          }
         }
       }
       fence_proxy_async_smem();
