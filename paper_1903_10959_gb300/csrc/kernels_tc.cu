@@ -126,7 +126,11 @@ __host__ __device__ inline CellSmem cell_smem(int mt, int split3, int bn = CELL_
   c.a_bytes = mt * 4096 * (split3 ? 2 : 1);
   c.y_bytes = bn * CELL_KC * 4 * 2;
   const int stage = c.a_bytes + c.y_bytes;
-  const int budget_kb = bn > 64 ? 200 : (mt <= 2 ? 72 : (mt == 3 ? 110 : 113));
+  // CTAs per SM that TMEM allows (accumulator columns rounded to a power of two)
+  const int cols = mt * bn;
+  const int alloc = cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512));
+  const int per_sm = 512 / alloc >= 3 ? 3 : 512 / alloc;
+  const int budget_kb = per_sm >= 3 ? 72 : (per_sm == 2 ? 113 : 200);
   int S = (budget_kb * 1024 - 3072) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
   c.stages = S;
@@ -153,13 +157,14 @@ struct RParams {
   const TcBatchSys* sys;
   int nsys, parity;
   int64_t ldr;              // row stride of R (>= ncol)
+  int64_t e_off;            // first cell of this launch (grids of at most 65535 cells)
 };
 
 template <int BN, bool MULTI>
 __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int64_t e = blockIdx.y;
+  int64_t e = P.e_off + blockIdx.y;
   int c0 = blockIdx.x * BN;
   if (MULTI) {   // item -> (system, cell, tile): binary search over the systems' first items
     const int64_t item = blockIdx.x;
@@ -370,17 +375,23 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_r_kernel(RParams P) {
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.hi) return cudaErrorInvalidValue;
-  RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3,
-            nullptr, 0, 0, a.ncol};
-  tc_cell_prepare();
+  // (128-column tiles with the 128-row tiles split over two CTAs per SM
+  // measured slower than both variants here: the two halves gather Y twice)
   const int bn = a.tile == 128 ? 128 : 64;
+  RParams P{d.hi, a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt, d.kt / CELL_KC, a.split3,
+            nullptr, 0, 0, a.ncol, 0};
+  tc_cell_prepare();
   const CellSmem L = cell_smem(d.mt, a.split3, bn);
-  dim3 grid((a.ncol + bn - 1) / bn, (unsigned)a.ncells);
-  note_launch();
-  if (bn == 128)
-    tc_cell_r_kernel<128, false><<<grid, CELL_THREADS, L.total, s>>>(P);
-  else
-    tc_cell_r_kernel<64, false><<<grid, CELL_THREADS, L.total, s>>>(P);
+  for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {   // grid y is limited to 65535
+    P.e_off = e0;
+    dim3 grid((unsigned)((a.ncol + bn - 1) / bn),
+              (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+    note_launch();
+    if (bn == 128)
+      tc_cell_r_kernel<128, false><<<grid, CELL_THREADS, L.total, s>>>(P);
+    else
+      tc_cell_r_kernel<64, false><<<grid, CELL_THREADS, L.total, s>>>(P);
+  }
   return cudaGetLastError();
 }
 
@@ -397,7 +408,7 @@ cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nite
                                  int nk, int split3, int parity, cudaStream_t s) {
   if (nitems == 0 || nsys == 0) return cudaSuccess;
   if (nitems > 0x7fffffff) return cudaErrorInvalidValue;
-  RParams P{nullptr, nullptr, nullptr, nullptr, 0, 0, ne, mt, nk, split3, d_sys, nsys, parity, 0};
+  RParams P{nullptr, nullptr, nullptr, nullptr, 0, 0, ne, mt, nk, split3, d_sys, nsys, parity, 0, 0};
   tc_cell_prepare();
   const CellSmem L = cell_smem(mt, split3, 64);
   note_launch();
