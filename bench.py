@@ -239,6 +239,7 @@ def host_cores():
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    import dataclasses
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -254,7 +255,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(s, "host memory"),
+        "data": "synthetic",
+        # the GPU arm's configuration (its autotuner filters all columns in one
+        # block); the oracle's arithmetic does not depend on the blocking
+        "config": workload_config(dataclasses.replace(s, block=s.n_sub), "host memory"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
