@@ -19,6 +19,8 @@ Every function cites the passage of arXiv:1903.10959 (DFT-FE) it follows:
 * ``chfsi``       -- Chebyshev filter (Eq. chebFilter, Sec. 3.3), CholGS
                      (Algorithm CholGS, Sec. 3.4), Rayleigh-Ritz (Sec. 3.5),
                      bound estimate, residuals and the iteration loop.
+* ``density``     -- spectrum-splitting Rayleigh-Ritz (Algorithm rr), Fermi
+                     level and electron density (Algorithm dc, Eq. elecDensSP).
 
 Parity status: every function is pinned by ``-m "not gpu"`` tests against
 closed forms, textbook rules, brute-force dense diagonalisation or

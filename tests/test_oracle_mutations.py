@@ -89,3 +89,34 @@ def test_transposed_ritz_rotation_is_caught(monkeypatch):
     D, X = chfsi.rayleigh_ritz(lambda Y: H @ Y, V)
     R = np.linalg.norm(H @ X - X * D[None, :], axis=0)
     assert R.max() > 1e-3
+
+
+def test_missing_mass_scaling_in_density_is_caught():
+    """Density built from X~ instead of Psi = M^{-1/2} X~ breaks the uniform
+    density of the constant state."""
+    from oracle import density as od
+    L = 4.0
+    prob = ham.Problem(2, 3, L, True, lambda x: np.zeros(len(x)))
+    x = np.sqrt(prob.mass) / np.sqrt(L ** 3)
+    assert np.allclose(od.density(prob, x[:, None]), 2.0 / L ** 3, atol=1e-14)
+    prob.minv_sqrt = np.ones_like(prob.minv_sqrt)          # planted: scaling dropped
+    rho = od.density(prob, x[:, None])
+    assert np.abs(rho - 2.0 / L ** 3).max() > 0.1 * 2.0 / L ** 3
+
+
+def test_wrong_sign_of_fractional_correction_is_caught(monkeypatch):
+    """(1 - f) instead of (f - 1) in Eq. elecDensSP breaks the identity with
+    the fully rotated density."""
+    from oracle import density as od
+    from paper_1903_10959_gb300 import workloads as W
+    s = W.small_periodic(seed=5, ncell=2, p=3, L=5.0, n_wells=3, n_want=12)
+    prob = ham.wells_problem(s.ncell, s.p, s.L, True, s.centres, s.depths, s.widths)
+    n, n_fr = 14, 5
+    X = chfsi.cholgs(W.start_block(3, prob.ndofs, n))
+    d_fr, X_fr = od.rayleigh_ritz_split(prob.apply_Htilde, X, n_fr)
+    mu, occ = od.fermi_level(d_fr, n - n_fr, 2 * (n - n_fr) + 3.3, kT=0.05)
+    D, XR = chfsi.rayleigh_ritz(prob.apply_Htilde, X)
+    f = np.concatenate([np.ones(n - n_fr), occ])
+    rho_full = od.density(prob, XR * np.sqrt(f)[None, :])
+    rho_bad = od.density(prob, X, X_fr, 2.0 - occ)          # planted: f - 1 -> 1 - f
+    assert np.abs(rho_bad - rho_full).max() > 1e-3 * np.abs(rho_full).max()
