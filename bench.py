@@ -424,6 +424,47 @@ def run_ours(args):
                "d2h_bytes_per_step": nbytes + n * 8,
                "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
 
+    # the step after RR: spectrum-splitting RR on the
+    # orthonormal block (n_fr = 15 % of the subspace), Fermi level and the
+    # electron density at the Gauss points; timed with events, not in `value`
+    split = None
+    if prec != "tf32":
+        from paper_1903_10959_gb300 import fermi_level
+        n_fr = max(1, int(round(0.15 * n)))
+        Xfr = torch.empty((M, n_fr), dtype=dt, device="cuda")
+        q = s.p + 2
+        rho = torch.empty(ncells * q ** 3, dtype=torch.float64, device="cuda")
+
+        def ev_time(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for _ in range(reps):
+                fn()
+            b_.record(stream)
+            torch.cuda.synchronize()
+            return a_.elapsed_time(b_) / reps
+
+        dfr = {}
+        t_split = ev_time(lambda: dfr.update(d=ctx.rayleigh_ritz_split(X, Xfr, prec=prec)))
+        mu, occ = fermi_level(dfr["d"], n - n_fr, 2 * (n - n_fr) + n_fr, 0.01)
+        t_den = ev_time(lambda: ctx.density(X, rho, Xfr, occ, prec=prec))
+        n1 = s.p + 1
+        den_flops = ncells * (n + n_fr) * 2 * (n1 ** 3 * q + n1 ** 2 * q ** 2 + n1 * q ** 3)
+        # binary64 interpolation: GB300's 1.25 TFLOP/s; binary32: 152 SMs x 128
+        # FP32 lanes x 2 flops x 2.07 GHz = 80.6 TFLOP/s
+        den_peak = 1.25 if prec == "fp64" else 152 * 128 * 2 * 2.07e9 / 1e12
+        achieved = den_flops / (t_den / 1e3) / 1e12
+        split = {"n_fr": n_fr, "split_rr_ms": t_split,
+                 "full_rr_ms": phase_timed[2] / args.steps, "fermi_level": mu,
+                 "density_ms": t_den, "density_gflop": den_flops / 1e9,
+                 "density_roofline": {"bound": "alu", "achieved": achieved, "peak": den_peak,
+                                      "unit": "TFLOP/s", "frac": achieved / den_peak,
+                                      "peak_note": "sum-factorised interpolation in the block's "
+                                                   "precision; peak from unit counts and clock"}}
+        del Xfr, rho
+
     if rank != 0:
         return
     cpu = None
@@ -451,7 +492,7 @@ def run_ours(args):
                           "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
         "roofline": roof, "roofline_assembly": asm_roof, "roofline_filter_step": step_roof,
         "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "autotune": tuned,
+        "gpu_launches": launches, "autotune": tuned, "spectrum_split_and_density": split,
         "projector_kernels_ms_per_step": nl_ms / args.steps if nl_n else None,
         "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
     }

@@ -214,6 +214,40 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
                          double b, double tol, int n_check, chfsi_precision prec,
                          double* evals_host, int* iters_done);
 
+/* Spectrum-splitting Rayleigh-Ritz (Algorithm rr, Sec. 3.5): H^ = X^T H~ X for
+ * the CholGS output X (M x n, not modified), its n_fr largest eigenpairs in
+ * binary64 (cuSOLVER syevdx, index range n-n_fr+1..n), and the partial
+ * rotation X_fr = X Q_fr into the caller's block X_fr (device, M x n_fr,
+ * leading dimension ldfr, same element type as X, must not overlap X).
+ * evals_fr_host[n_fr] receives D_fr ascending.  CHFSI_ERR_EIG when syevdx
+ * fails. */
+chfsi_status chfsi_rayleigh_ritz_split(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, int n_fr,
+                                       void* Xfr, int64_t ldfr, chfsi_precision prec,
+                                       double* evals_fr_host);
+
+/* Fermi level (Algorithm dc, step 1): mu such that
+ * 2 (n_oc + sum_i f(evals[i], mu)) = n_electrons, f the Fermi-Dirac function
+ * 1 / (1 + exp((eps - mu) / kT)) (kT in Ha), over the n partially occupied
+ * Ritz values; the n_oc lower states count as fully occupied.  Bisection on
+ * the host to a relative width of 1e-15; occ_out[n] (may be NULL) receives
+ * f(evals[i], mu).  CHFSI_ERR_ARG when the states cannot hold n_electrons.
+ * Host only: needs no context or device. */
+chfsi_status chfsi_fermi_level(int n, const double* evals, int n_oc, double n_electrons,
+                               double kT, double* mu_out, double* occ_out);
+
+/* Electron density (Algorithm dc, Eq. elecDensSP) at the Gauss points of
+ * every cell (interpolation in the blocks' precision, binary64 sums):
+ *   rho(x) = 2 sum_{i<n} psi_i(x)^2 + 2 sum_{j<n_fr} (f_j - 1) psi_fr,j(x)^2,
+ * psi = M^{-1/2} x for the columns x of X (the CholGS output, M x n) and of
+ * X_fr (chfsi_rayleigh_ritz_split), f_j = occ_fr_host[j] (chfsi_fermi_level).
+ * n_fr = 0 gives the density of n doubly occupied states.  rho: device,
+ * caller-owned, ncells * q^3 doubles with q = quad_points (p + 2 by default);
+ * point (a, b, c) of cell e (cells x fastest) at rho[e q^3 + a + q (b + q c)].
+ * Synchronises the stream. */
+chfsi_status chfsi_density(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, const void* Xfr,
+                           int64_t ldfr, int n_fr, const double* occ_fr_host, chfsi_precision prec,
+                           double* rho);
+
 /* Psi^ = M^{-1/2} x~ in place (Eq. hep, recovery of the FE eigenvectors). */
 chfsi_status chfsi_unscale(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, chfsi_precision prec);
 

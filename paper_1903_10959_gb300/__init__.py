@@ -7,6 +7,6 @@ Importing this package does not load the library; constructing a Context
 does, and fails loudly if it has not been built.
 """
 from ._lib import (FP64, MIXED_TF32, MIXED_TF32X3, Batch, ChfsiError, Context, Server,  # noqa: F401
-                   load)
+                   fermi_level, load)
 
-__all__ = ["Context", "Batch", "Server", "ChfsiError", "load", "FP64", "MIXED_TF32", "MIXED_TF32X3"]
+__all__ = ["Context", "Batch", "Server", "fermi_level", "ChfsiError", "load", "FP64", "MIXED_TF32", "MIXED_TF32X3"]

@@ -86,6 +86,9 @@ _SIGS = {
     "chfsi_solve": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                               C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]),
     "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
+    "chfsi_rayleigh_ritz_split": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, _vp, _i64, C.c_int, _dp]),
+    "chfsi_fermi_level": (C.c_int, [C.c_int, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp]),
+    "chfsi_density": (C.c_int, [_vp, _vp, _i64, C.c_int, _vp, _i64, C.c_int, _dp, C.c_int, _vp]),
     "chfsi_last_timings": (C.c_int, [_vp, _dp]),
     "chfsi_kernel_launches": (_i64, []),
     "chfsi_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp), _vp, C.POINTER(_vp)]),
@@ -314,6 +317,31 @@ class Context:
                                           float(tol), int(n_check), pr, _ptr(ev), C.byref(done)))
         return ev, done.value
 
+    def rayleigh_ritz_split(self, X, Xfr, prec="fp64") -> np.ndarray:
+        """Algorithm rr: the n_fr = Xfr.shape[1] largest Ritz pairs; Xfr <- X Q_fr."""
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        pf, ldf, nfr = _dev(Xfr, pr)
+        ev = np.empty(nfr)
+        self._check(self._lib.chfsi_rayleigh_ritz_split(self._h, px, ldx, n, nfr, pf, ldf, pr,
+                                                        _ptr(ev)))
+        return ev
+
+    def density(self, X, rho, Xfr=None, occ_fr=None, prec="fp64"):
+        """Algorithm dc: rho (device float64, ncells * q^3) at the Gauss points."""
+        import torch
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        if not (isinstance(rho, torch.Tensor) and rho.is_cuda and rho.dtype == torch.float64):
+            raise TypeError("rho must be a float64 CUDA tensor")
+        if Xfr is not None and Xfr.shape[1] > 0:
+            pf, ldf, nfr = _dev(Xfr, pr)
+            occ = _host(occ_fr, nfr)
+        else:
+            pf, ldf, nfr, occ = None, 1, 0, np.zeros(1)
+        self._check(self._lib.chfsi_density(self._h, px, ldx, n, pf, ldf, nfr, _ptr(occ), pr,
+                                            rho.data_ptr()))
+
     def unscale(self, X, prec="fp64"):
         pr = _prec(prec)
         px, ldx, n = _dev(X, pr)
@@ -497,3 +525,15 @@ class Server:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+def fermi_level(evals, n_oc, n_electrons, kT):
+    """Algorithm dc, step 1 (chfsi_fermi_level): (mu, occupations)."""
+    ev = _host(evals)
+    occ = np.empty(ev.size)
+    mu = C.c_double(0.0)
+    st = load().chfsi_fermi_level(int(ev.size), _ptr(ev), int(n_oc), float(n_electrons), float(kT),
+                                  C.byref(mu), _ptr(occ))
+    if st != 0:
+        raise ChfsiError(st, "chfsi_fermi_level: the states cannot hold that many electrons")
+    return mu.value, occ

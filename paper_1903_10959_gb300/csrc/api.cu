@@ -422,16 +422,16 @@ chfsi_status cholgs_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_prec
 // Rayleigh-Ritz.  fp64_apply: for the mixed precisions, evaluate H~ X with the
 // binary64 cell products (then round to binary32) so that H^ carries no
 // binary32-accumulation bias; used for the last RR of a mixed solve.
-chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
-                     double* evals_host, bool fp64_apply = false) {
+// Step 1 of Rayleigh-Ritz: H^ = X^T (H~ X) (lower triangle, binary64, column
+// major n x n) into ctx->Ssq, one column block at a time.  fp64_apply: H~ X
+// with binary64 cell products for a binary32 block.
+chfsi_status projected_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
+                            bool fp64_apply) {
   const HostMesh& m = ctx->mesh;
   chfsi_status st;
-  if (n == 0) return CHFSI_OK;
-  if ((st = ensure_solver(ctx)) != CHFSI_OK) return st;
   if ((st = grow(ctx, ctx->Ssq, (size_t)n * n * 8 + 64)) != CHFSI_OK) return st;
   if ((st = grow(ctx, ctx->lam, (size_t)n * 8 + 64)) != CHFSI_OK) return st;
   double* Hh = (double*)ctx->Ssq.ptr;
-  int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
   const size_t es = esize(prec);
   const bool via64 = fp64_apply && is_mixed(prec);
   // binary64 staging (X and H~X copies) is capped at kStage64 columns
@@ -456,6 +456,18 @@ chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precisio
                         Hh + j0 + (int64_t)j0 * n, n, 1)) != CHFSI_OK)
       return st;
   }
+  return CHFSI_OK;
+}
+
+chfsi_status rr_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
+                     double* evals_host, bool fp64_apply = false) {
+  chfsi_status st;
+  if (n == 0) return CHFSI_OK;
+  if ((st = ensure_solver(ctx)) != CHFSI_OK) return st;
+  // 1. H^ = X^T (H~ X)
+  if ((st = projected_impl(ctx, X, ldx, n, prec, fp64_apply)) != CHFSI_OK) return st;
+  double* Hh = (double*)ctx->Ssq.ptr;
+  int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
   // 2. H^ Q = Q D (binary64 syevd, ascending)
   int lw = 0;
   double* W = (double*)ctx->lam.ptr;
@@ -608,7 +620,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_node_ptr, m.node_ptr.size() * 4);
   release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
-                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb})
+                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db})
     dfree(ctx, b->ptr, b->bytes);
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)
@@ -917,6 +929,99 @@ chfsi_status chfsi_rayleigh_ritz(chfsi_ctx* ctx, void* X, int64_t ldx, int n, ch
   if (st == CHFSI_OK) toc(ctx, 2);
   if (st == CHFSI_OK) st = check_device_status(ctx, prec);
   return st;
+}
+
+chfsi_status chfsi_rayleigh_ritz_split(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, int n_fr,
+                                       void* Xfr, int64_t ldfr, chfsi_precision prec,
+                                       double* evals_fr_host) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (n_fr < 1 || n_fr > n || !Xfr || ldfr < n_fr || !evals_fr_host)
+    return fail(ctx, CHFSI_ERR_ARG, "bad split Rayleigh-Ritz arguments");
+  const HostMesh& m = ctx->mesh;
+  const size_t es = esize(prec);
+  {   // the output block must not overlap X
+    const char* x0 = (const char*)X;
+    const char* x1 = x0 + ((m.ndofs - 1) * ldx + n) * es;
+    const char* f0 = (const char*)Xfr;
+    const char* f1 = f0 + ((m.ndofs - 1) * ldfr + n_fr) * es;
+    if (f0 < x1 && x0 < f1) return fail(ctx, CHFSI_ERR_ARG, "X_fr overlaps X");
+  }
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  tic(ctx);
+  if ((st = ensure_solver(ctx)) != CHFSI_OK) return st;
+  // 1. H^ = X^T H~ X
+  if ((st = projected_impl(ctx, X, ldx, n, prec, false)) != CHFSI_OK) return st;
+  double* Hh = (double*)ctx->Ssq.ptr;
+  int* dinfo = (int*)((char*)ctx->Ssq.ptr + (size_t)n * n * 8);
+  double* W = (double*)ctx->lam.ptr;
+  // 2. the n_fr largest eigenpairs (binary64 syevdx, index range n - n_fr + 1 .. n);
+  //    their eigenvectors overwrite the first n_fr columns of H^
+  int lw = 0, meig = 0;
+  const int il = n - n_fr + 1, iu = n;
+  CS(cusolverDnDsyevdx_bufferSize(ctx->sol, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                  CUBLAS_FILL_MODE_LOWER, n, Hh, n, 0.0, 0.0, il, iu, &meig, W, &lw));
+  if ((st = grow(ctx, ctx->work, (size_t)lw * 8 + 256)) != CHFSI_OK) return st;
+  CS(cusolverDnDsyevdx(ctx->sol, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER,
+                       n, Hh, n, 0.0, 0.0, il, iu, &meig, W, (double*)ctx->work.ptr, lw, dinfo));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(evals_fr_host, W, (size_t)n_fr * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (info != 0 || meig != n_fr)
+    return fail(ctx, CHFSI_ERR_EIG, "split RR: syevdx info = " + std::to_string(info) +
+                                        ", eigenpairs " + std::to_string(meig));
+  // 3. X_fr = X Q_fr (the n x n_fr leading block of H^, leading dimension n)
+  if (prec == CHFSI_FP64) {
+    CK(launch_tallgemm_fp64((const double*)X, ldx, Hh, n, m.ndofs, n, n_fr, (double*)Xfr, ldfr, 0, 0,
+                            ctx->stream));
+  } else {
+    if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n_fr))) != CHFSI_OK) return st;
+    CK(tc_tallgemm_mixed((const float*)X, ldx, Hh, n, m.ndofs, n, n_fr, (float*)Xfr, ldfr, 0, 0, 0,
+                         prec == CHFSI_MIXED_TF32X3, ctx->work.ptr, ctx->stream));
+  }
+  toc(ctx, 2);
+  return check_device_status(ctx, prec);
+}
+
+chfsi_status chfsi_density(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, const void* Xfr,
+                           int64_t ldfr, int n_fr, const double* occ_fr_host, chfsi_precision prec,
+                           double* rho) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (n_fr < 0 || n_fr > 0 && (!Xfr || ldfr < n_fr || !occ_fr_host) || !rho)
+    return fail(ctx, CHFSI_ERR_ARG, "bad density arguments");
+  const HostMesh& m = ctx->mesh;
+  // tables: M^{-1/2} (M doubles), basis at the Gauss points (q x n1), weights 2 (f - 1)
+  const size_t nb = (size_t)m.q * m.n1;
+  if ((st = grow(ctx, ctx->Db, ((size_t)m.ndofs + nb + (size_t)n_fr + 8) * 8)) != CHFSI_OK) return st;
+  std::vector<double> h((size_t)m.ndofs + nb + (size_t)n_fr);
+  for (int64_t j = 0; j < m.ndofs; ++j) h[j] = 1.0 / std::sqrt(m.mass[j]);
+  std::copy(m.B.begin(), m.B.end(), h.begin() + m.ndofs);
+  for (int j = 0; j < n_fr; ++j) h[m.ndofs + nb + j] = 2.0 * (occ_fr_host[j] - 1.0);
+  double* d = (double*)ctx->Db.ptr;
+  CK(cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  DensityArgs a{};
+  a.X = X;
+  a.ldx = ldx;
+  a.n = n;
+  a.Xfr = n_fr > 0 ? Xfr : X;
+  a.ldfr = n_fr > 0 ? ldfr : ldx;
+  a.nfr = n_fr;
+  a.wfr = d + m.ndofs + nb;
+  a.dofmap = ctx->d_dofmap;
+  a.minv_sqrt = d;
+  a.B = d + m.ndofs;
+  a.ncells = m.ncells;
+  a.n1 = m.n1;
+  a.q = m.q;
+  a.is_double = prec == CHFSI_FP64;
+  a.rho = rho;
+  CK(launch_density(a, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));   // the host table must outlive its copy
+  return CHFSI_OK;
 }
 
 chfsi_status chfsi_residuals(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,

@@ -48,6 +48,24 @@ struct HostMesh {
 };
 
 void build_mesh(const chfsi_mesh_desc& d, HostMesh& m);        // map, colours, modes, mass
+
+// Electron density at the Gauss points (density.cu).
+struct DensityArgs {
+  const void* X;             // M x n block (binary64 or binary32), columns weighted 2
+  int64_t ldx;
+  int n;
+  const void* Xfr;           // M x nfr partially occupied block, columns weighted wfr
+  int64_t ldfr;
+  int nfr;
+  const double* wfr;         // device, nfr weights 2 (f_j - 1)
+  const int32_t* dofmap;     // device, ncells x n1^3
+  const double* minv_sqrt;   // device, M^{-1/2} per unknown
+  const double* B;           // device, q x n1 basis values at the Gauss points
+  int64_t ncells;
+  int n1, q, is_double;
+  double* rho;               // device, ncells x q^3
+};
+cudaError_t launch_density(const DensityArgs& a, cudaStream_t s);
 void gll_rule(int p, std::vector<double>& x, std::vector<double>& w);
 void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
 
