@@ -410,18 +410,28 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         Xh = torch.empty((M, n), dtype=dt, pin_memory=True)
-        Xh.copy_(X.cpu())
+        Xh.copy_(X)
         torch.cuda.synchronize()
+        evs = []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
             X.copy_(Xh, non_blocking=True)
+            ev[1].record(stream)
             step()
+            ev[2].record(stream)
             Xh.copy_(X, non_blocking=True)
+            ev[3].record(stream)
             torch.cuda.synchronize()
+            evs.append(ev)
         te = (time.perf_counter() - t0) / args.e2e_steps
         nbytes = M * n * X.element_size()
         e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + n * 8,
+               "device_ms": {"h2d": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
+                             "step": float(np.mean([e[1].elapsed_time(e[2]) for e in evs])),
+                             "d2h": float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))},
                "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
 
     # the step after RR: spectrum-splitting RR on the
