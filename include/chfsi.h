@@ -322,7 +322,10 @@ chfsi_status chfsi_batch_set_candidate(chfsi_batch* b, int k);
 /* ChFSI on every system: X[s] (device, binary64, M_s x n[s], in/out start
  * block), bnd[s] the upper bound of spec(H~_s); per iteration the batched
  * binary32 filter (filter_prec) followed, per system and concurrently, by
- * CholGS and Rayleigh-Ritz in binary64 (orth_prec must be CHFSI_FP64).
+ * CholGS and Rayleigh-Ritz in orth_prec: CHFSI_FP64 (on the binary64 block)
+ * or CHFSI_MIXED_TF32X3 (3xTF32 off-diagonal, binary64 diagonal, on the
+ * binary32 working copy; the last Rayleigh-Ritz applies H~ with binary64
+ * products, as chfsi_solve does); X[s] receives the final block.
  * evals[s][n[s]] (host) receive the Ritz values. */
 chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* ldx, const int* n,
                                int iters, int degree, const double* bnd,

@@ -429,13 +429,13 @@ class Batch:
         self._check(self._lib.chfsi_batch_autotune(self._h, p, ld, n, pr, C.byref(choice), _ptr(ms)))
         return choice.value, ms
 
-    def solve(self, X, iters, degree, bounds, filter_prec="mixed"):
+    def solve(self, X, iters, degree, bounds, filter_prec="mixed", orth_prec="fp64"):
         p, ld, n = self._blocks(X, FP64)
         bnd = _host(bounds)
         evs = [np.empty(x.shape[1]) for x in X]
         earr = (_dp * len(X))(*[_ptr(e) for e in evs])
         self._check(self._lib.chfsi_batch_solve(self._h, p, ld, n, int(iters), int(degree), _ptr(bnd),
-                                                _prec(filter_prec), FP64, earr))
+                                                _prec(filter_prec), _prec(orth_prec), earr))
         return evs
 
 

@@ -570,6 +570,19 @@ cudaError_t noalloc_scratch(void** out) {
 }  // namespace
 
 // ===================================================================== C ABI
+namespace chfsi {
+// Rayleigh-Ritz for the library's own drivers (batched solve): fp64_apply
+// applies H~ with binary64 cell products to a binary32 block.
+chfsi_status rayleigh_ritz_internal(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
+                                    double* evals_host, bool fp64_apply) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if ((st = rr_impl(ctx, X, ldx, n, prec, evals_host, fp64_apply)) != CHFSI_OK) return st;
+  return check_device_status(ctx, prec);
+}
+}  // namespace chfsi
+
 extern "C" {
 
 chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx** out) {

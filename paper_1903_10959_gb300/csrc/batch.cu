@@ -809,7 +809,9 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
                                int iters, int degree, const double* bnd, chfsi_precision filter_prec,
                                chfsi_precision orth_prec, double* const* evals) {
   if (!b || !X || !ldx || !n || !bnd || !evals || iters < 0 || degree < 1) return CHFSI_ERR_ARG;
-  if (orth_prec != CHFSI_FP64) return bfail(b, CHFSI_ERR_ARG, "batched CholGS / RR run in binary64");
+  if (orth_prec != CHFSI_FP64 && orth_prec != CHFSI_MIXED_TF32X3)
+    return bfail(b, CHFSI_ERR_ARG, "batched CholGS / RR run in binary64 or 3xTF32");
+  const bool mixed_orth = orth_prec == CHFSI_MIXED_TF32X3;
   const int ns = (int)b->ctx.size();
   cudaDeviceSynchronize();   // the start blocks may come from any stream
   // binary32 working copies for the filter
@@ -828,6 +830,25 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
   }
   std::vector<std::vector<double>> D(ns);
   std::vector<chfsi_status> sts(ns, CHFSI_OK);
+  // 3xTF32 orthogonalisation works on the binary32 copies in place; the last
+  // Rayleigh-Ritz applies H~ with binary64 products (second-order eigenvalues)
+  auto per_system_mixed = [&](int i, bool first, bool last) {
+    chfsi_ctx* c = b->ctx[i];
+    const int64_t M = c->mesh.ndofs;
+    if (first && launch_copy_cols(X[i], ldx[i], xp[i], ld32[i], M, n[i], 1, 0, c->stream) != cudaSuccess) {
+      sts[i] = CHFSI_ERR_CUDA;
+      return;
+    }
+    D[i].resize(n[i]);
+    chfsi_status s1 = chfsi_cholgs(c, xp[i], ld32[i], n[i], CHFSI_MIXED_TF32X3);
+    if (s1 == CHFSI_OK)
+      s1 = rayleigh_ritz_internal(c, xp[i], ld32[i], n[i], CHFSI_MIXED_TF32X3, D[i].data(), last);
+    if (s1 == CHFSI_OK && last &&
+        launch_copy_cols(xp[i], ld32[i], X[i], ldx[i], M, n[i], 0, 1, c->stream) != cudaSuccess)
+      s1 = CHFSI_ERR_CUDA;
+    if (s1 == CHFSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s1 = CHFSI_ERR_CUDA;
+    sts[i] = s1;
+  };
   auto per_system = [&](int i, bool filtered) {
     chfsi_ctx* c = b->ctx[i];
     const int64_t M = c->mesh.ndofs;
@@ -846,16 +867,19 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
     if (s1 == CHFSI_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s1 = CHFSI_ERR_CUDA;
     sts[i] = s1;
   };
-  auto run_all = [&](bool filtered) {
+  auto run_all = [&](bool filtered, bool last) {
     std::vector<std::thread> th;
-    for (int i = 0; i < ns; ++i) th.emplace_back(per_system, i, filtered);
+    for (int i = 0; i < ns; ++i) {
+      if (mixed_orth) th.emplace_back(per_system_mixed, i, !filtered, last);
+      else th.emplace_back(per_system, i, filtered);
+    }
     for (auto& t : th) t.join();
     for (int i = 0; i < ns; ++i)
       if (sts[i] != CHFSI_OK) return bfail(b, sts[i], "system " + std::to_string(i) + ": " +
                                                            chfsi_last_error(b->ctx[i]));
     return CHFSI_OK;
   };
-  if ((st = run_all(false)) == CHFSI_OK) {
+  if ((st = run_all(false, iters == 0)) == CHFSI_OK) {
     std::vector<double> a(ns), a0(ns);
     for (int it = 0; it < iters && st == CHFSI_OK; ++it) {
       for (int i = 0; i < ns; ++i) {
@@ -865,7 +889,7 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
       }
       st = chfsi_batch_filter(b, xp.data(), ld32.data(), n, degree, a.data(), bnd, a0.data(),
                               filter_prec);
-      if (st == CHFSI_OK) st = run_all(true);
+      if (st == CHFSI_OK) st = run_all(true, it + 1 == iters);
     }
   }
   if (st == CHFSI_OK)

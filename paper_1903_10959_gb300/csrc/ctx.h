@@ -56,3 +56,8 @@ struct chfsi_ctx {
   double kms[3] = {0, 0, 0};       // cell products, assembly, projector kernels
   int64_t kcount[3] = {0, 0, 0};
 };
+
+namespace chfsi {
+chfsi_status rayleigh_ritz_internal(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_precision prec,
+                                    double* evals_host, bool fp64_apply);
+}  // namespace chfsi

@@ -126,3 +126,28 @@ def test_batched_solve_eigenvalues_and_alone_vs_batch(batch_setup):
     ev1 = B1.solve(X1, iters, m, bnd[2:3])
     B1.destroy()
     assert np.abs(ev1[0] - evs[2]).max() <= 1e-10
+
+
+def test_batched_solve_with_tf32x3_orthogonalisation(batch_setup):
+    """3xTF32 CholGS / Rayleigh-Ritz on the binary32 copies (last RR with
+    binary64 products): the wanted eigenvalues still meet 1e-7 Ha, and a
+    system alone gives the same result as in the batch."""
+    systems, ctxs = batch_setup
+    probs = [oracle_problem(s) for s in systems]
+    bnd = np.array([_bounds(p, 4) for p in probs])
+    iters, m = 14, 12
+    X0 = [W.start_block(s.seed, c.ndofs, s.n_sub) for s, c in zip(systems, ctxs)]
+    B = Batch(ctxs)
+    X = [torch.tensor(x, device=DEV) for x in X0]
+    evs = B.solve(X, iters, m, bnd, orth_prec="mixed")
+    B.destroy()
+    for i, (s, p) in enumerate(zip(systems, probs)):
+        D_ref, _ = och.chfsi(p.apply_Htilde, X0[i], m, iters, bnd[i])
+        assert np.abs(evs[i][:s.n_want] - D_ref[:s.n_want]).max() < 1e-7
+        Q = X[i].cpu().numpy()                      # the final block is written back
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-4
+    B1 = Batch([ctxs[1]])
+    X1 = [torch.tensor(X0[1], device=DEV)]
+    ev1 = B1.solve(X1, iters, m, bnd[1:2], orth_prec="mixed")
+    B1.destroy()
+    assert np.abs(ev1[0] - evs[1]).max() <= 1e-10
