@@ -8,8 +8,13 @@ One step = one ChFSI iteration on device-resident data: Chebyshev filter
 (Eq. chebFilter), CholGS (Algorithm CholGS) and Rayleigh-Ritz (Sec. 3.5) of
 arXiv:1903.10959, each through the library's C ABI.  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                  [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|mixed|fp64|tf32]
+                  [--impl ours|reference] [--workload chfsi|c3|batch|serving]
+
+The default precision stores the block in binary32 and forms the cell
+products from three bf16 terms per operand (six kind::f16 MMAs, FP32
+accumulation); CholGS / Rayleigh-Ritz use 3xTF32 off-diagonal and binary64
+diagonal blocks, Cholesky and eigensolve in binary64.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (extrapolated to one iteration by exact operation
@@ -41,8 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "tf32"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "mixed", "fp64", "tf32"],
+                    help="bf16x3: BF16x3 cell products (the fastest mixed path); mixed: 3xTF32")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end steps (median wall time reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
     ap.add_argument("--block", type=int, default=0,
@@ -283,7 +290,7 @@ def run_ours(args):
     s = workload(args.small, args.workload)
     if args.block:
         s = dataclasses.replace(s, block=args.block)
-    prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32"}[args.prec]
+    prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.current_stream()
     ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
@@ -345,9 +352,10 @@ def run_ours(args):
     # Rooflines (per-launch CUDA events on the context stream).
     # Cell-product kernel, algorithmic work per launch (one block of nb
     # columns): 2 n_e^2 flops per cell and vector; bytes = the split cell
-    # matrices (N_c n_e^2 x 8 B) + the block of Y (M nb s_X) + the dense cell
-    # blocks written (N_c n_e nb s_X).  With 3xTF32 each flop takes three
-    # TF32 MMA passes, so its tensor peak is the TF32 peak / 3.
+    # matrices (N_c n_e^2 x s_H: 8 B for TF32 hi + lo, 6 B for three bf16
+    # terms) + the block of Y (M nb s_X) + the dense cell blocks written
+    # (N_c n_e nb s_X).  3xTF32 takes three TF32 MMA passes per flop (peak =
+    # TF32 peak / 3), BF16x3 six BF16 passes (peak = BF16 peak / 6).
     # Assembly kernel, bytes per launch: the cell blocks read (N_c n_e nb s_X),
     # Y_in, Y_prev read and Y_out written (3 M nb s_X) and the unknown -> cell
     # row table ((M + 1 + N_c n_e) x 4 B).
@@ -374,19 +382,24 @@ def run_ours(args):
         roof["traffic"] = None
         step_roof = asm_roof = None
     else:
-        passes = 3 if prec == "mixed" else 1
-        cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * 8
+        passes = {"mixed": 3, "tf32": 1, "bf16x3": 6}[prec]
+        s_h = {"mixed": 8, "tf32": 4, "bf16x3": 6}[prec]     # cell-matrix bytes per element read
+        cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * s_h
                       + col_steps * M * sx + col_steps * ncells * ne * sx)
-        tpeak = tf32_peak / passes
+        bf16_peak = peaks.get("bf16_tflops_sustained", 1672.5)
+        tpeak = (bf16_peak if prec == "bf16x3" else tf32_peak) / passes
         achieved = alg_flops / (cell_ms / 1e3) / 1e12
-        traffic = profiled_traffic("tc_cell_r_kernel", s, n)
+        cell_kernel = "tc_cell_bf16_kernel" if prec == "bf16x3" else "tc_cell_r_kernel"
+        traffic = profiled_traffic(cell_kernel, s, n) if prec in ("mixed", "bf16x3") else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
-                "frac": achieved / tpeak, "traffic": traffic, "kernel": "tc_cell_r_kernel",
+                "frac": achieved / tpeak, "traffic": traffic, "kernel": cell_kernel,
                 "launches": int(cell_n), "avg_launch_ms": cell_ms / cell_n,
                 "flops_per_launch": alg_flops / cell_n, "bytes_per_launch": cell_bytes / cell_n,
                 "hbm_gbs": cell_bytes / (cell_ms / 1e3) / 1e9,
-                "peak_note": "TF32 dense peak = measured bf16 sustained (MEASURED_PEAKS.json) x "
-                             "1.1/2.25 nominal ratio, / %d MMA passes per flop; of measured" % passes}
+                "peak_note": ("BF16 dense peak (measured sustained, MEASURED_PEAKS.json) / %d MMA "
+                              "passes per flop; of measured" % passes) if prec == "bf16x3" else
+                             ("TF32 dense peak = measured bf16 sustained (MEASURED_PEAKS.json) x "
+                              "1.1/2.25 nominal ratio, / %d MMA passes per flop; of measured" % passes)}
         asm_bytes = (col_steps * ncells * ne * sx + col_steps * 3 * M * sx
                      + steps_blocks * nblocks * (M + 1 + ncells * ne) * 4)
         if len(s.nl_centres):
@@ -395,7 +408,8 @@ def run_ours(args):
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernel": "tc_assemble_kernel",
                     "launches": int(asm_n), "avg_launch_ms": asm_ms / max(asm_n, 1),
                     "bytes_per_launch": asm_bytes / max(asm_n, 1),
-                    "traffic": profiled_traffic("tc_assemble_kernel", s, n),
+                    "traffic": profiled_traffic("tc_assemble_kernel", s, n)
+                    if prec in ("mixed", "bf16x3") else None,
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
         asm_roof["frac"] = asm_roof["achieved"] / peaks["hbm_gbs"]
         step_bytes = col_steps * 3 * sx * M + steps_blocks * nblocks * ncells * ne * ne * 8
@@ -412,9 +426,9 @@ def run_ours(args):
         Xh = torch.empty((M, n), dtype=dt, pin_memory=True)
         Xh.copy_(X)
         torch.cuda.synchronize()
-        evs = []
-        t0 = time.perf_counter()
+        evs, walls = [], []
         for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
             X.copy_(Xh, non_blocking=True)
@@ -424,14 +438,15 @@ def run_ours(args):
             Xh.copy_(X, non_blocking=True)
             ev[3].record(stream)
             torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
             evs.append(ev)
-        te = (time.perf_counter() - t0) / args.e2e_steps
+        te = float(np.median(walls))
         nbytes = M * n * X.element_size()
         e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + n * 8,
-               "device_ms": {"h2d": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
-                             "step": float(np.mean([e[1].elapsed_time(e[2]) for e in evs])),
-                             "d2h": float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))},
+               "device_ms": {"h2d": float(np.median([e[0].elapsed_time(e[1]) for e in evs])),
+                             "step": float(np.median([e[1].elapsed_time(e[2]) for e in evs])),
+                             "d2h": float(np.median([e[2].elapsed_time(e[3]) for e in evs]))},
                "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
 
     # the step after RR: spectrum-splitting RR on the
@@ -489,7 +504,7 @@ def run_ours(args):
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == "fp64" else ("tf32x3" if prec == "mixed" else "tf32"),
+        "dtype": {"fp64": "f64", "mixed": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3"}[prec],
         "data": "synthetic",
         "config": workload_config(s, "inputs larger than L2: X %.1f GB, cell matrices %.1f GB"
                                   % (M * n * sx / 1e9, s.ncell ** 3 * ne * ne * 8 / 1e9)),
@@ -497,7 +512,7 @@ def run_ours(args):
                                "cholgs": phase_timed[1] / args.steps,
                                "rr": phase_timed[2] / args.steps},
         "filter_tflops": {"algorithmic_per_filter_time": alg_flops / filter_s / 1e12,
-                          "cell_kernel_executed_tensor": (3 if prec == "mixed" else 1) * alg_flops
+                          "cell_kernel_executed_tensor": {"mixed": 3, "tf32": 1, "bf16x3": 6}.get(prec, 1) * alg_flops
                           / (cell_ms / 1e3) / 1e12 if prec != "fp64" else None,
                           "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
         "roofline": roof, "roofline_assembly": asm_roof, "roofline_filter_step": step_roof,

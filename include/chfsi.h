@@ -60,7 +60,11 @@ typedef enum {
    * diagonal blocks, Cholesky, eigensolve and residuals in binary64. */
   CHFSI_MIXED_TF32X3 = 1,
   /* As above with one TF32 product per term (faster, ~5e-4 relative). */
-  CHFSI_MIXED_TF32 = 2
+  CHFSI_MIXED_TF32 = 2,
+  /* Binary32 storage; cell products with both operands split into three
+   * bf16 terms (about 24 bits) and six kind::f16 MMAs (K = 16) accumulated
+   * in FP32; Gram / rotations as CHFSI_MIXED_TF32X3. */
+  CHFSI_MIXED_BF16X3 = 3
 } chfsi_precision;
 
 /* Uniform mesh of ncell[0] x ncell[1] x ncell[2] boxes on [0,len[0]] x ... .

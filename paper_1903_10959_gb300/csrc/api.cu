@@ -125,7 +125,11 @@ chfsi_status grow(chfsi_ctx* ctx, DevBuf& b, size_t bytes) {
   return CHFSI_OK;
 }
 
-bool is_mixed(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32; }
+bool is_mixed(chfsi_precision p) {
+  return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32 || p == CHFSI_MIXED_BF16X3;
+}
+// Gram and tall GEMMs: 3xTF32 for both three-term precisions, 1xTF32 otherwise.
+int split3_of(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_BF16X3; }
 // Columns per block of the binary64 staging copies (residuals, binary64 RR apply).
 constexpr int kStage64 = 512;
 // Free the per-call scratch that grows with the column block (filter, cell
@@ -145,7 +149,7 @@ size_t esize(chfsi_precision p) { return p == CHFSI_FP64 ? 8 : 4; }
 void free_device_data(chfsi_ctx* ctx) {
   const HostMesh& m = ctx->mesh;
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
-  ctx->dev_bytes -= (int64_t)ctx->tc.bytes;   // packed binary32 copies (0 when never packed)
+  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes);   // packed copies (0 when never packed)
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
@@ -200,8 +204,17 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     }
     return CHFSI_OK;
   }
-  // mixed precisions: binary32 storage, tcgen05 TF32 cell products
-  if (!ctx->tc.hi) {
+  // mixed precisions: binary32 storage, tcgen05 TF32 (or BF16x3) cell products
+  const bool bf16 = prec == CHFSI_MIXED_BF16X3;
+  if (bf16 && !ctx->tc.bf) {
+    cudaError_t pe = tc_pack_bf16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("BF16x3 cell data: ") + cudaGetErrorString(pe));
+    }
+  }
+  if (!bf16 && !ctx->tc.hi) {
     cudaError_t pe = tc_pack_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
     if (pe != cudaSuccess) {
       cudaGetLastError();
@@ -228,7 +241,8 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.tile = ctx->cell_tile;
   {
     KTimer kt(ctx, 0);
-    CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
+    if (bf16) CK(tc_cell_bf16_launch(ctx->tc, ra, ctx->stream));
+    else CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
   }
   KTimer kt(ctx, 1);
   AssembleParams ap{};
@@ -351,7 +365,7 @@ chfsi_status gram_impl(chfsi_ctx* ctx, chfsi_precision prec, const void* A, int6
   size_t want = tc_gram_partial_bytes(m.ndofs, n1, n2);
   if ((st = grow(ctx, ctx->part, want)) != CHFSI_OK) return st;
   CK(tc_gram_mixed((const float*)A, lda, (const float*)Bm, ldb, m.ndofs, n1, n2, C, ldc, lower,
-                   ctx->diag_block, prec == CHFSI_MIXED_TF32X3, ctx->part.ptr, ctx->part.bytes,
+                   ctx->diag_block, split3_of(prec), ctx->part.ptr, ctx->part.bytes,
                    ctx->stream));
   return CHFSI_OK;
 }
@@ -369,7 +383,7 @@ chfsi_status rotate_impl(chfsi_ctx* ctx, chfsi_precision prec, void* X, int64_t 
   } else {
     if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n))) != CHFSI_OK) return st;
     CK(tc_tallgemm_mixed((const float*)X, ldx, U, n, m.ndofs, n, n, (float*)ctx->rot.ptr, n, upper,
-                         trans, ctx->diag_block, prec == CHFSI_MIXED_TF32X3, ctx->work.ptr,
+                         trans, ctx->diag_block, split3_of(prec), ctx->work.ptr,
                          ctx->stream));
   }
   CK(cudaMemcpy2DAsync(X, ldx * es, ctx->rot.ptr, n * es, n * es, m.ndofs, cudaMemcpyDeviceToDevice,
@@ -992,7 +1006,7 @@ chfsi_status chfsi_rayleigh_ritz_split(chfsi_ctx* ctx, const void* X, int64_t ld
   } else {
     if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n_fr))) != CHFSI_OK) return st;
     CK(tc_tallgemm_mixed((const float*)X, ldx, Hh, n, m.ndofs, n, n_fr, (float*)Xfr, ldfr, 0, 0, 0,
-                         prec == CHFSI_MIXED_TF32X3, ctx->work.ptr, ctx->stream));
+                         split3_of(prec), ctx->work.ptr, ctx->stream));
   }
   toc(ctx, 2);
   return check_device_status(ctx, prec);

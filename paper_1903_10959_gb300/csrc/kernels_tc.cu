@@ -24,6 +24,8 @@
 #include <cstdio>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 #include "tc.h"
 #include "tc_ptx.cuh"
@@ -104,10 +106,90 @@ cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s
 
 void tc_free(TcCellData& d) {
   if (d.hi) cudaFree(d.hi);
+  if (d.bf) cudaFree(d.bf);
   d = TcCellData();
 }
 
+// ----------------------------------------------------------------- BF16x3 packing
+// Each value v ~ b1 + b2 + b3 with b1 = bf16(v), b2 = bf16(v - b1),
+// b3 = bf16(v - b1 - b2) (about 24 significant bits together).  Layout: per
+// cell, per K-chunk of 16, the three terms one after another, each holding all
+// 128-row tiles; a tile block is 128 rows x 16 K bf16 in the no-swizzle
+// K-major core-matrix layout (8 rows x 16 B; LBO 128 B along K, SBO 256 B
+// along M), the same byte geometry as the TF32 blocks.
+constexpr int BF_KC = 16;
+__device__ __host__ __forceinline__ int bf_elem_off(int r, int k) {   // in bf16 elements
+  return (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ void bf16_split3(double v, uint16_t& b1, uint16_t& b2, uint16_t& b3) {
+  const __nv_bfloat16 h1 = __float2bfloat16_rn((float)v);
+  const double r1 = v - (double)__bfloat162float(h1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn((float)r1);
+  const double r2 = r1 - (double)__bfloat162float(h2);
+  const __nv_bfloat16 h3 = __float2bfloat16_rn((float)r2);
+  b1 = __bfloat16_as_ushort(h1);
+  b2 = __bfloat16_as_ushort(h2);
+  b3 = __bfloat16_as_ushort(h3);
+}
+
+// The same split of a binary32 value in binary32 arithmetic: v - b1 and
+// r1 - b2 are exact (each term keeps at most 8 significant bits of what is left).
+__device__ __forceinline__ void bf16_split3f(float v, uint16_t& b1, uint16_t& b2, uint16_t& b3) {
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h2);
+  b1 = __bfloat16_as_ushort(h1);
+  b2 = __bfloat16_as_ushort(h2);
+  b3 = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
+__global__ void tc_pack_bf16_kernel(const double* __restrict__ Ht, uint16_t* __restrict__ out,
+                                    int64_t ncells, int ne, int mt, int nk16) {
+  const int64_t per_chunk = (int64_t)mt * 2048;   // elements of one term, all tiles
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ncells * nk16 * per_chunk) return;
+  // one thread per (cell, chunk, tile, row, k); writes the three terms
+  const int64_t e = idx / (nk16 * per_chunk);
+  int64_t rem = idx - e * nk16 * per_chunk;
+  const int kc = (int)(rem / per_chunk);
+  rem -= (int64_t)kc * per_chunk;
+  const int t = (int)(rem / 2048);
+  const int w = (int)(rem - t * 2048);
+  const int r = w / BF_KC, k = w % BF_KC;
+  const int row = t * 128 + r, col = kc * BF_KC + k;
+  const double v = (row < ne && col < ne) ? Ht[(e * ne + row) * (int64_t)ne + col] : 0.0;
+  uint16_t b1, b2, b3;
+  bf16_split3(v, b1, b2, b3);
+  uint16_t* base = out + (e * nk16 + kc) * 3 * per_chunk + (int64_t)t * 2048 + bf_elem_off(r, k);
+  base[0] = b1;
+  base[per_chunk] = b2;
+  base[2 * per_chunk] = b3;
+}
+
+cudaError_t tc_pack_bf16_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                     int64_t* dev_bytes) {
+  const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  d.bf_bytes = (size_t)d.ncells * nk16 * 3 * d.mt * 2048 * sizeof(uint16_t);
+  cudaError_t e = cudaMalloc(&d.bf, d.bf_bytes);
+  if (e != cudaSuccess) {
+    d.bf = nullptr;
+    d.bf_bytes = 0;
+    return e;
+  }
+  if (dev_bytes) *dev_bytes += (int64_t)d.bf_bytes;
+  const int64_t n = d.ncells * (int64_t)nk16 * d.mt * 2048;
+  note_launch();
+  tc_pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dHt, d.bf, d.ncells, d.ne, d.mt, nk16);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- cell kernel
+// Shared memory after the stages: barriers and flags (256 B), then the
+// cell's dof map (n_e <= 729 ints for p <= 8).
+constexpr int kCellSmemTail = 256 + 4 * 729 + 12;   // 3184 B, a multiple of 16
+static_assert(kCellSmemTail % 16 == 0, "stage buffers stay 16-byte aligned");
 struct CellSmem {
   int stages;
   int a_bytes;   // per stage
@@ -131,10 +213,10 @@ __host__ __device__ inline CellSmem cell_smem(int mt, int split3, int bn = CELL_
   const int alloc = cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512));
   const int per_sm = 512 / alloc >= 3 ? 3 : 512 / alloc;
   const int budget_kb = per_sm >= 3 ? 72 : (per_sm == 2 ? 113 : 200);
-  int S = (budget_kb * 1024 - 3072) / stage;
+  int S = (budget_kb * 1024 - kCellSmemTail) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
   c.stages = S;
-  c.total = S * stage + 3072;   // + barriers, the cell's dof map (<= 512) and modes
+  c.total = S * stage + kCellSmemTail;
   return c;
 }
 
@@ -413,6 +495,239 @@ cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nite
   const CellSmem L = cell_smem(mt, split3, 64);
   note_launch();
   tc_cell_r_kernel<64, true><<<(unsigned)nitems, CELL_THREADS, L.total, s>>>(P);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- BF16x3 cell kernel
+// R_e = H~_e Y_e with both operands split into three bf16 terms and the six
+// products a3 y1 + a2 y2 + a1 y3 + a2 y1 + a1 y2 + a1 y1 (smallest first) of
+// kind::f16 MMAs (K = 16) accumulated in FP32 in TMEM.  Same warp roles,
+// bounded waits and store-only epilogue as tc_cell_r_kernel; 64-column tiles.
+struct BfSmem {
+  int stages, a_bytes, y_bytes, total;
+};
+__host__ __device__ inline BfSmem bf_smem(int mt) {
+  BfSmem c;
+  c.a_bytes = mt * 3 * 4096;            // three terms x mt tiles x (128 x 16 bf16)
+  c.y_bytes = 3 * 64 * BF_KC * 2;       // three terms x (64 columns x 16 bf16)
+  const int stage = c.a_bytes + c.y_bytes;
+  const int cols = mt * 64;
+  const int alloc = cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512));
+  const int per_sm = 512 / alloc >= 3 ? 3 : 512 / alloc;
+  const int budget_kb = per_sm >= 3 ? 72 : (per_sm == 2 ? 113 : 200);
+  int S = (budget_kb * 1024 - kCellSmemTail) / stage;
+  S = S < 2 ? 2 : (S > 6 ? 6 : S);
+  c.stages = S;
+  c.total = S * stage + kCellSmemTail;
+  return c;
+}
+
+__global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P) {
+  constexpr int BN = 64;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.e_off + blockIdx.y;
+  const int c0 = blockIdx.x * BN;
+  const int ncv = min(BN, P.ncol - c0);
+  const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
+  const BfSmem L = bf_smem(P.mt);
+  const int S = L.stages;
+  const int stage_bytes = L.a_bytes + L.y_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(smem + S * stage_bytes + 256);
+  const uint32_t sbase = smem_u32(smem);
+  auto fa = [&](int s) { return smem_u32(bars + s); };
+  auto fy = [&](int s) { return smem_u32(bars + S + s); };
+  auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
+  const uint32_t accb = smem_u32(bars + 3 * S);
+  const int tc_need = P.mt * BN;
+  const uint32_t tmem_cols = tc_need <= 64 ? 64 : (tc_need <= 128 ? 128 : (tc_need <= 256 ? 256 : 512));
+  const int nk = P.nk, ne = P.ne;   // nk: K-chunks of 16
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(fa(s), 1);
+      mbar_init(fy(s), 32);
+      mbar_init(em(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(smem_u32(tmem_slot), tmem_cols);
+    tmem_relinquish();
+  }
+  for (int l = tid; l < ne; l += CELL_THREADS) dm[l] = P.dofmap[e * ne + l];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * L.a_bytes;
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+          atomicExch(&g_tc_status, 31);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        mbar_arrive_expect_tx(fa(s), L.a_bytes);
+        bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * L.a_bytes, L.a_bytes, fa(s));
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag)
+        for (int i = max(0, issued - S); i < issued; ++i) mbar_wait(fa(i % S), (i / S) & 1);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, bne);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (!mbar_wait(fa(s), (i / S) & 1) || !mbar_wait(fy(s), (i / S) & 1) ||
+            *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 32);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * stage_bytes;
+        const uint32_t sy = sa + L.a_bytes;
+        uint64_t y[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) y[p] = umma_desc(sy + p * BN * BF_KC * 2, 128, 256);
+        for (int t = 0; t < P.mt; ++t) {
+          const uint32_t d = tmem + t * BN;
+          uint64_t a[3];
+#pragma unroll
+          for (int p = 0; p < 3; ++p) a[p] = umma_desc(sa + (p * P.mt + t) * 4096, 128, 256);
+          mma_f16(d, a[2], y[0], idesc, i > 0);
+          mma_f16(d, a[1], y[1], idesc, 1);
+          mma_f16(d, a[0], y[2], idesc, 1);
+          mma_f16(d, a[1], y[0], idesc, 1);
+          mma_f16(d, a[0], y[1], idesc, 1);
+          mma_f16(d, a[0], y[0], idesc, 1);
+        }
+        umma_commit(em(s));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    // gather + split into three bf16 terms: rows l = 16 i + 8 q + a (a < 8),
+    // 4 columns per lane; one 16-byte store per column and term
+    const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
+    const int q = lane >> 4;
+    const int cq = (lane & 15) * 4;
+    const int G = S < 4 ? S : 4;
+    if (warp < G) {
+      float v[8][4];
+      for (int i = warp; i < nk; i += G) {
+        const int s = i % S;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int l = i * BF_KC + q * 8 + a;
+          const int g = l < ne ? dm[l] : -1;
+          v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
+          if (g >= 0) {
+            const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
+            if (vec && cq + 4 <= ncv) {
+              const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
+              v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (cq + u < ncv) v[a][u] = __ldg(src + u);
+            }
+          }
+        }
+        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+          atomicExch(&g_tc_status, 33);
+          *(volatile int*)abort_flag = 1;
+        }
+        if (*(volatile int*)abort_flag) break;
+        uint16_t* ys = reinterpret_cast<uint16_t*>(smem + s * stage_bytes + L.a_bytes);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int n = cq + u;
+          const int o = bf_elem_off(n, q * 8);
+          uint32_t w[3][4];
+#pragma unroll
+          for (int a = 0; a < 8; a += 2) {
+            uint16_t lo1, lo2, lo3, hi1, hi2, hi3;
+            bf16_split3f(v[a][u], lo1, lo2, lo3);
+            bf16_split3f(v[a + 1][u], hi1, hi2, hi3);
+            w[0][a / 2] = (uint32_t)lo1 | ((uint32_t)hi1 << 16);
+            w[1][a / 2] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
+            w[2][a / 2] = (uint32_t)lo3 | ((uint32_t)hi3 << 16);
+          }
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+            *reinterpret_cast<uint4*>(ys + p * BN * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(fy(s));
+      }
+    }
+    // epilogue: TMEM row -> R row (16-byte stores only)
+    const bool okacc = mbar_wait(accb, 0);
+    if (!okacc) {
+      atomicExch(&g_tc_status, 34);
+      *(volatile int*)abort_flag = 1;
+    }
+    tc_fence_after();
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    const bool vst = (P.ldr & 3) == 0;
+    for (int t = 0; t < P.mt; ++t) {
+      const int l = t * 128 + warp * 32 + lane;
+      float* dst = P.R + ((int64_t)e * ne + l) * P.ldr + c0;
+      for (int cb = 0; cb < bne; cb += 16) {
+        float acc[16];
+        __syncwarp();
+        if (run) {
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * BN + cb, acc);
+          tmem_wait_ld();
+        }
+        if (!run || l >= ne) continue;
+        if (vst && cb + 16 <= ncv) {
+#pragma unroll
+          for (int u = 0; u < 16; u += 4)
+            *reinterpret_cast<float4*>(dst + cb + u) = make_float4(acc[u], acc[u + 1], acc[u + 2], acc[u + 3]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (cb + u < ncv) dst[cb + u] = acc[u];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) tmem_dealloc(tmem, tmem_cols);
+}
+
+cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
+  if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
+  if (!d.bf) return cudaErrorInvalidValue;
+  const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  RParams P{reinterpret_cast<const float*>(d.bf), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
+            nk16, 1, nullptr, 0, 0, a.ncol, 0};
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  const BfSmem L = bf_smem(d.mt);
+  for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
+    P.e_off = e0;
+    dim3 grid((unsigned)((a.ncol + 63) / 64), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+    note_launch();
+    tc_cell_bf16_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
+  }
   return cudaGetLastError();
 }
 

@@ -15,6 +15,9 @@ struct TcCellData {
   size_t bytes = 0;        // bytes of each of hi / lo
   int64_t ncells = 0;
   int ne = 0, mt = 0, kt = 0;   // ne, row tiles of 128, K padded to a multiple of 8
+  // BF16x3 copy (three bf16 terms per value), packed on first use
+  uint16_t* bf = nullptr;
+  size_t bf_bytes = 0;
 };
 
 // Owner-computes form of one H~ Y step (no colouring): every cell writes its
@@ -80,6 +83,11 @@ cudaError_t tc_assemble_launch(const AssembleParams& P, cudaStream_t s);
 
 cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
                      cudaStream_t s, int64_t* dev_bytes);
+// Split the binary64 device cell matrices into three bf16 terms (BF16x3 layout).
+cudaError_t tc_pack_bf16_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                     int64_t* dev_bytes);
+// The BF16x3 cell kernel (same contract as tc_cell_r_launch, 64-column tiles).
+cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
 // Split the binary64 device cell matrices into the TF32 hi / lo operand layout.
 cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
                                 int64_t* dev_bytes);

@@ -54,7 +54,8 @@ def _x32(seed, m, n):
 
 @pytest.mark.parametrize("ncol,prec,tol", [(1, "tf32x3", 1e-5), (13, "tf32x3", 1e-5),
                                            (64, "tf32x3", 1e-5), (150, "tf32x3", 1e-5),
-                                           (70, "tf32", 2e-3)])
+                                           (70, "tf32", 2e-3), (1, "bf16x3", 1e-5),
+                                           (13, "bf16x3", 1e-5), (150, "bf16x3", 1e-5)])
 def test_mixed_apply(case, ncol, prec, tol):
     s, prob, ctx = case
     X0 = _x32(3, prob.ndofs, ncol)
@@ -151,6 +152,32 @@ def test_mixed_solve_meets_eigenvalue_tolerance(case):
     D, done = ctx.solve(X, iters, s.degree, b, prec="mixed")
     nw = s.n_want
     assert np.abs(D[:nw] - D_ref[:nw]).max() < 1e-7
+
+
+def test_bf16x3_solve_meets_eigenvalue_tolerance(case):
+    """ChFSI with BF16x3 cell products (kind::f16 MMAs): <= 1e-7 Ha per eigenvalue."""
+    s, prob, ctx = case
+    n = s.n_sub
+    iters = 12
+    X0 = W.start_block(s.seed, prob.ndofs, n)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(s.seed, prob.ndofs), 20)
+    D_ref, _ = och.chfsi(prob.apply_Htilde, X0, s.degree, iters, b)
+    X = torch.tensor(X0.astype(np.float32), device=DEV)
+    ctx.set_blocking(200, 8)
+    D, done = ctx.solve(X, iters, s.degree, b, prec="bf16x3")
+    assert np.abs(D[:s.n_want] - D_ref[:s.n_want]).max() < 1e-7
+
+
+def test_bf16x3_filter(case):
+    s, prob, ctx = case
+    X0 = _x32(4, prob.ndofs, 45)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(4, prob.ndofs), 15)
+    a, a0 = 0.2 * b, -3.0
+    ref = och.chebyshev_filter(prob.apply_Htilde, X0.astype(np.float64), 20, a, b, a0)
+    X = torch.tensor(X0, device=DEV)
+    ctx.set_blocking(32, 8)
+    ctx.filter(X, 20, a, b, a0, prec="bf16x3")
+    assert rel_fro(X.cpu().numpy().astype(np.float64), ref) < 1e-4
 
 
 def test_mixed_tf32_runs(case):
