@@ -499,40 +499,53 @@ cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nite
 }
 
 // ----------------------------------------------------------------- BF16x3 cell kernel
-// R_e = H~_e Y_e with both operands split into three bf16 terms and the six
-// products a3 y1 + a2 y2 + a1 y3 + a2 y1 + a1 y2 + a1 y1 (smallest first) of
-// kind::f16 MMAs (K = 16) accumulated in FP32 in TMEM.  Same warp roles,
-// bounded waits and store-only epilogue as tc_cell_r_kernel; 64-column tiles.
-struct BfSmem {
-  int stages, a_bytes, y_bytes, total;
+// R_e = H~_e Y_e computed as its transpose R_e^T = Y_e^T H~_e (H~_e is
+// symmetric): the MMA's M = 128 columns of Y (A operand, gathered and split
+// into three bf16 terms by warps 0-3), N = up to 256 rows of H~_e (B operand,
+// streamed by bulk copies from the packed three-term matrix), K = 16 cell
+// nodes per chunk, six kind::f16 MMAs per chunk (h3 y1 + h2 y2 + h1 y3 +
+// h2 y1 + h1 y2 + h1 y1, smallest first) accumulated in FP32 in TMEM.
+// Against 128-row x 64-column tiles this halves the shared-memory operand
+// bytes per flop (the tensor core's shared-memory reads bounded that form)
+// and pads the n_e rows only to a multiple of 16 per part.  A cell's rows are
+// split into np parts of nh rows (one CTA each, nh <= 256 so that two CTAs
+// share an SM's TMEM); grid x runs over (column tile, part) with the parts
+// of a tile adjacent, grid y over cells.  Warp 4 issues the copies, warp 5
+// the MMAs; warps 0-3 (two pairs, one chunk per pair, 8 rows per warp)
+// gather, then store R with lanes over consecutive columns.
+constexpr int BF_YT = 3 * 128 * BF_KC * 2;   // Y tile: three terms of 128 columns x 16
+struct BfPlan {
+  int np, nh, alloc, stages, total;
 };
-__host__ __device__ inline BfSmem bf_smem(int mt) {
-  BfSmem c;
-  c.a_bytes = mt * 3 * 4096;            // three terms x mt tiles x (128 x 16 bf16)
-  c.y_bytes = 3 * 64 * BF_KC * 2;       // three terms x (64 columns x 16 bf16)
-  const int stage = c.a_bytes + c.y_bytes;
-  const int cols = mt * 64;
-  const int alloc = cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512));
-  const int per_sm = 512 / alloc >= 3 ? 3 : 512 / alloc;
-  const int budget_kb = per_sm >= 3 ? 72 : (per_sm == 2 ? 113 : 200);
-  int S = (budget_kb * 1024 - kCellSmemTail) / stage;
+__host__ __device__ inline BfPlan bf_plan(int ne) {
+  BfPlan b;
+  b.np = (ne + 255) / 256;
+  const int nh = (ne + b.np - 1) / b.np;
+  b.nh = (nh + 15) / 16 * 16;
+  b.alloc = b.nh <= 32 ? 32 : (b.nh <= 64 ? 64 : (b.nh <= 128 ? 128 : 256));
+  const int per_sm = 512 / b.alloc >= 3 ? 3 : 512 / b.alloc;
+  const int budget = (per_sm >= 3 ? 72 : (per_sm == 2 ? 113 : 200)) * 1024;
+  const int stage = BF_YT + 3 * b.nh * 32;
+  int S = (budget - kCellSmemTail) / stage;
   S = S < 2 ? 2 : (S > 6 ? 6 : S);
-  c.stages = S;
-  c.total = S * stage + kCellSmemTail;
-  return c;
+  b.stages = S;
+  b.total = S * stage + kCellSmemTail;
+  return b;
 }
 
-__global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P) {
-  constexpr int BN = 64;
+__global__ void __launch_bounds__(CELL_THREADS, 2) tc_cell_bf16_kernel(RParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t e = P.e_off + blockIdx.y;
-  const int c0 = blockIdx.x * BN;
-  const int ncv = min(BN, P.ncol - c0);
-  const int bne = ncv <= 16 ? 16 : (ncv + 15) / 16 * 16;
-  const BfSmem L = bf_smem(P.mt);
-  const int S = L.stages;
-  const int stage_bytes = L.a_bytes + L.y_bytes;
+  const int ne = P.ne, nk = P.nk;   // nk: K-chunks of 16
+  const BfPlan B = bf_plan(ne);
+  const int h = blockIdx.x % B.np;
+  const int c0 = (blockIdx.x / B.np) * 128;
+  const int ncv = min(128, P.ncol - c0);
+  const int r0 = h * B.nh;                 // first cell row of this part
+  const int S = B.stages;
+  const int hrow = B.nh * 32;              // one term of the part's rows for one chunk
+  const int stage_bytes = BF_YT + 3 * hrow;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -542,14 +555,11 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
   auto fy = [&](int s) { return smem_u32(bars + S + s); };
   auto em = [&](int s) { return smem_u32(bars + 2 * S + s); };
   const uint32_t accb = smem_u32(bars + 3 * S);
-  const int tc_need = P.mt * BN;
-  const uint32_t tmem_cols = tc_need <= 64 ? 64 : (tc_need <= 128 ? 128 : (tc_need <= 256 ? 256 : 512));
-  const int nk = P.nk, ne = P.ne;   // nk: K-chunks of 16
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(fa(s), 1);
-      mbar_init(fy(s), 32);
+      mbar_init(fy(s), 64);
       mbar_init(em(s), 1);
     }
     mbar_init(accb, 1);
@@ -557,7 +567,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
     fence_mbar_init();
   }
   if (warp == 5) {
-    tmem_alloc(smem_u32(tmem_slot), tmem_cols);
+    tmem_alloc(smem_u32(tmem_slot), B.alloc);
     tmem_relinquish();
   }
   for (int l = tid; l < ne; l += CELL_THREADS) dm[l] = P.dofmap[e * ne + l];
@@ -568,7 +578,9 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
 
   if (warp == 4) {
     if (lane == 0) {
-      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * L.a_bytes;
+      // term p of chunk i: rows [r0, r0 + nh) are contiguous (8-row groups of 256 B)
+      const int64_t term_bytes = (int64_t)P.mt * 4096;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * 3 * term_bytes + (int64_t)r0 * 32;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
@@ -578,8 +590,11 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
           break;
         }
         if (*(volatile int*)abort_flag) break;
-        mbar_arrive_expect_tx(fa(s), L.a_bytes);
-        bulk_g2s(sbase + s * stage_bytes, Ae + (int64_t)i * L.a_bytes, L.a_bytes, fa(s));
+        const uint32_t dst = sbase + s * stage_bytes + BF_YT;
+        mbar_arrive_expect_tx(fa(s), 3 * hrow);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * 3 + p) * term_bytes, hrow, fa(s));
         ++issued;
       }
       if (*(volatile int*)abort_flag)
@@ -587,7 +602,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, bne);
+      const uint32_t idesc = idesc_bf16(128, B.nh);
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
         if (!mbar_wait(fa(s), (i / S) & 1) || !mbar_wait(fy(s), (i / S) & 1) ||
@@ -597,84 +612,72 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
           break;
         }
         tc_fence_after();
-        const uint32_t sa = sbase + s * stage_bytes;
-        const uint32_t sy = sa + L.a_bytes;
-        uint64_t y[3];
+        const uint32_t sy = sbase + s * stage_bytes;
+        const uint32_t sh = sy + BF_YT;
+        uint64_t y[3], hd[3];
 #pragma unroll
-        for (int p = 0; p < 3; ++p) y[p] = umma_desc(sy + p * BN * BF_KC * 2, 128, 256);
-        for (int t = 0; t < P.mt; ++t) {
-          const uint32_t d = tmem + t * BN;
-          uint64_t a[3];
-#pragma unroll
-          for (int p = 0; p < 3; ++p) a[p] = umma_desc(sa + (p * P.mt + t) * 4096, 128, 256);
-          mma_f16(d, a[2], y[0], idesc, i > 0);
-          mma_f16(d, a[1], y[1], idesc, 1);
-          mma_f16(d, a[0], y[2], idesc, 1);
-          mma_f16(d, a[1], y[0], idesc, 1);
-          mma_f16(d, a[0], y[1], idesc, 1);
-          mma_f16(d, a[0], y[0], idesc, 1);
+        for (int p = 0; p < 3; ++p) {
+          y[p] = umma_desc(sy + p * 4096, 128, 256);
+          hd[p] = umma_desc(sh + p * hrow, 128, 256);
         }
+        mma_f16(tmem, y[0], hd[2], idesc, i > 0);
+        mma_f16(tmem, y[1], hd[1], idesc, 1);
+        mma_f16(tmem, y[2], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[1], idesc, 1);
+        mma_f16(tmem, y[1], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[0], idesc, 1);
         umma_commit(em(s));
       }
       umma_commit(accb);
     }
   } else {
-    // gather + split into three bf16 terms: rows l = 16 i + 8 q + a (a < 8),
-    // 4 columns per lane; one 16-byte store per column and term
-    const bool vec = ((P.ld_in & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.Yin) & 15) == 0);
-    const int q = lane >> 4;
-    const int cq = (lane & 15) * 4;
-    const int G = S < 4 ? S : 4;
-    if (warp < G) {
+    // gather + split: pair (warp >> 1) takes chunks pair, pair + 2, ...; warp
+    // half q takes rows 16 i + 8 q + a (a < 8); lane holds columns lane + 32 u,
+    // so each load reads 128 contiguous bytes of a Y row and each 16-byte
+    // store of 8 lanes fills one 128-byte core matrix (no bank conflicts)
+    const int pair = warp >> 1, q = warp & 1;
+    for (int i = pair; i < nk; i += 2) {
+      const int s = i % S;
       float v[8][4];
-      for (int i = warp; i < nk; i += G) {
-        const int s = i % S;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const int l = i * BF_KC + q * 8 + a;
-          const int g = l < ne ? dm[l] : -1;
-          v[a][0] = v[a][1] = v[a][2] = v[a][3] = 0.f;
-          if (g >= 0) {
-            const float* src = P.Yin + (int64_t)g * P.ld_in + c0 + cq;
-            if (vec && cq + 4 <= ncv) {
-              const float4 t4 = __ldg(reinterpret_cast<const float4*>(src));
-              v[a][0] = t4.x; v[a][1] = t4.y; v[a][2] = t4.z; v[a][3] = t4.w;
-            } else {
-#pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (cq + u < ncv) v[a][u] = __ldg(src + u);
-            }
-          }
-        }
-        if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
-          atomicExch(&g_tc_status, 33);
-          *(volatile int*)abort_flag = 1;
-        }
-        if (*(volatile int*)abort_flag) break;
-        uint16_t* ys = reinterpret_cast<uint16_t*>(smem + s * stage_bytes + L.a_bytes);
+      for (int a = 0; a < 8; ++a) {
+        const int l = i * BF_KC + q * 8 + a;
+        const int g = l < ne ? dm[l] : -1;
+        const float* src = P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int n = cq + u;
-          const int o = bf_elem_off(n, q * 8);
-          uint32_t w[3][4];
-#pragma unroll
-          for (int a = 0; a < 8; a += 2) {
-            uint16_t lo1, lo2, lo3, hi1, hi2, hi3;
-            bf16_split3f(v[a][u], lo1, lo2, lo3);
-            bf16_split3f(v[a + 1][u], hi1, hi2, hi3);
-            w[0][a / 2] = (uint32_t)lo1 | ((uint32_t)hi1 << 16);
-            w[1][a / 2] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
-            w[2][a / 2] = (uint32_t)lo3 | ((uint32_t)hi3 << 16);
-          }
-#pragma unroll
-          for (int p = 0; p < 3; ++p)
-            *reinterpret_cast<uint4*>(ys + p * BN * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+          const int c = lane + 32 * u;
+          v[a][u] = (g >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
         }
-        fence_proxy_async_smem();
-        mbar_arrive(fy(s));
       }
+      if (i >= S && !mbar_wait(em(s), ((i / S) - 1) & 1)) {
+        atomicExch(&g_tc_status, 33);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint16_t* ys = reinterpret_cast<uint16_t*>(smem + s * stage_bytes);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = bf_elem_off(lane + 32 * u, q * 8);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int a = 0; a < 8; a += 2) {
+          uint16_t lo1, lo2, lo3, hi1, hi2, hi3;
+          bf16_split3f(v[a][u], lo1, lo2, lo3);
+          bf16_split3f(v[a + 1][u], hi1, hi2, hi3);
+          w[0][a / 2] = (uint32_t)lo1 | ((uint32_t)hi1 << 16);
+          w[1][a / 2] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
+          w[2][a / 2] = (uint32_t)lo3 | ((uint32_t)hi3 << 16);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(fy(s));
     }
-    // epilogue: TMEM row -> R row (16-byte stores only)
+    // epilogue: TMEM lane = column c0 + c, TMEM column = cell row r0 + j;
+    // for each row the warp's lanes store 32 consecutive floats
     const bool okacc = mbar_wait(accb, 0);
     if (!okacc) {
       atomicExch(&g_tc_status, 34);
@@ -682,51 +685,43 @@ __global__ void __launch_bounds__(CELL_THREADS, 1) tc_cell_bf16_kernel(RParams P
     }
     tc_fence_after();
     const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
-    const bool vst = (P.ldr & 3) == 0;
-    for (int t = 0; t < P.mt; ++t) {
-      const int l = t * 128 + warp * 32 + lane;
-      float* dst = P.R + ((int64_t)e * ne + l) * P.ldr + c0;
-      for (int cb = 0; cb < bne; cb += 16) {
-        float acc[16];
-        __syncwarp();
-        if (run) {
-          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + t * BN + cb, acc);
-          tmem_wait_ld();
-        }
-        if (!run || l >= ne) continue;
-        if (vst && cb + 16 <= ncv) {
-#pragma unroll
-          for (int u = 0; u < 16; u += 4)
-            *reinterpret_cast<float4*>(dst + cb + u) = make_float4(acc[u], acc[u + 1], acc[u + 2], acc[u + 3]);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 16; ++u)
-            if (cb + u < ncv) dst[cb + u] = acc[u];
-        }
+    const int c = warp * 32 + lane;
+    float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    for (int cb = 0; cb < B.nh; cb += 16) {
+      float acc[16];
+      __syncwarp();
+      if (run) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+        tmem_wait_ld();
       }
+      if (!run || c >= ncv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = acc[j];
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tmem_dealloc(tmem, tmem_cols);
+  if (warp == 5) tmem_dealloc(tmem, B.alloc);
 }
 
 cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.bf) return cudaErrorInvalidValue;
   const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  const BfPlan B = bf_plan(d.ne);
+  if (B.np * B.nh > d.mt * 128) return cudaErrorInvalidValue;   // parts stay inside the packed rows
   RParams P{reinterpret_cast<const float*>(d.bf), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
             nk16, 1, nullptr, 0, 0, a.ncol, 0};
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
-  const BfSmem L = bf_smem(d.mt);
   for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
     P.e_off = e0;
-    dim3 grid((unsigned)((a.ncol + 63) / 64), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+    dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
     note_launch();
-    tc_cell_bf16_kernel<<<grid, CELL_THREADS, L.total, s>>>(P);
+    tc_cell_bf16_kernel<<<grid, CELL_THREADS, B.total, s>>>(P);
   }
   return cudaGetLastError();
 }

@@ -188,3 +188,23 @@ def test_mixed_tf32_runs(case):
     X = torch.tensor(X0.astype(np.float32), device=DEV)
     D, _ = ctx.solve(X, 6, s.degree, b, prec="tf32")
     assert np.abs(D[:s.n_want] - D_ref[:s.n_want]).max() < 1e-3
+
+
+@pytest.mark.parametrize("p,ncell,ncol", [(2, 3, 70), (8, 2, 131)])
+def test_bf16x3_apply_part_sizes(p, ncell, ncol):
+    """BF16x3 cell products at the ends of the row-part sizing: p = 2 (one
+    part of 32 rows, two K-chunks) and p = 8 (three parts of 256 rows, 46
+    K-chunks), with a ragged last column tile."""
+    s = W.small_periodic(seed=30 + p, ncell=ncell, p=p, L=2.5 * ncell, n_wells=2, n_want=8)
+    prob = oracle_problem(s)
+    ctx = gpu_context(s)
+    try:
+        X0 = _x32(6, prob.ndofs, ncol)
+        X = torch.tensor(X0, device=DEV)
+        Y = torch.empty_like(X)
+        ctx.set_blocking(200, 8)
+        ctx.apply(X, Y, prec="bf16x3")
+        ref = prob.apply_Htilde(X0.astype(np.float64))
+        assert rel_fro(Y.cpu().numpy().astype(np.float64), ref) < 1e-5
+    finally:
+        ctx.destroy()
