@@ -1,8 +1,9 @@
-"""Mixed-precision (tcgen05 TF32) path against the FP64 oracle.
+"""Mixed-precision (tcgen05 BF16x3 / 3xTF32 / 1xTF32) path against the FP64 oracle.
 
 Inputs are the binary32 roundings of the seeded blocks; the oracle runs in
 binary64 on the same rounded values.  Tolerances follow from the arithmetic:
-3xTF32 products carry ~2^-22 relative error, but the cell sums accumulate
+3xTF32 products carry ~2^-22 relative error (BF16x3: ~3 x 2^-24, the dropped
+a2 y3 + a3 y2 + a3 y3 terms), but the cell sums accumulate
 n_e <= 512 products in binary32 whose magnitudes exceed the result by the
 cancellation factor of the kinetic matrix (~10-40 here), so one operator
 application is checked at 1e-5 relative Frobenius and a degree-20 filter at
