@@ -449,7 +449,7 @@ def run_ours(args):
                              "d2h": float(np.median([e[2].elapsed_time(e[3]) for e in evs]))},
                "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
 
-    # the step after RR: spectrum-splitting RR on the
+    # the step after RR (Sec. 3.5, Algorithms rr and dc): spectrum-splitting RR on the
     # orthonormal block (n_fr = 15 % of the subspace), Fermi level and the
     # electron density at the Gauss points; timed with events, not in `value`
     split = None
