@@ -146,7 +146,12 @@ chfsi_status chfsi_fill_uniform(chfsi_ctx* ctx, void* X, int64_t ldx, int64_t ro
                                 uint64_t seed, uint64_t stream, chfsi_precision prec);
 
 /* Y = H~ X on ncol vectors (one application of Eq. hep's operator, the inner
- * operation of Eq. chebFilter).  X and Y: device, M x ncol, must not overlap. */
+ * operation of Eq. chebFilter).  X and Y: device, M x ncol, must not overlap.
+ * The first call in a mixed precision packs the cell matrices for it (a
+ * library-owned device copy: three bf16 terms, 6 B per entry, for
+ * CHFSI_MIXED_BF16X3; the TF32 hi / lo pair, 8 B per entry, for the TF32
+ * forms) and returns CHFSI_ERR_OOM when that copy does not fit.  The same
+ * holds for every entry point below that takes a mixed precision. */
 chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, int64_t ldy,
                          int ncol, chfsi_precision prec);
 
