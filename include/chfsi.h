@@ -101,6 +101,18 @@ chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out);
 chfsi_status chfsi_set_potential_gaussians(chfsi_ctx* ctx, int n, const double* xyz,
                                            const double* depth, const double* width);
 
+/* General effective potential (V_eff of Eq. discreteHam, e.g. the Hartree +
+ * exchange-correlation + local pseudopotential field of an SCF step, Algorithm
+ * scf) given by its values at the Gauss points of every cell, where the V_e
+ * integrals are evaluated: v[e q^3 + a + q (b + q c)] for point (a, b, c) of
+ * cell e (cells x fastest), q = p + 2 Gauss-Legendre points per direction --
+ * the same points and layout as the output of chfsi_density.  The values are
+ * added to the Gaussian wells of chfsi_set_potential_gaussians (set no wells
+ * for a general field).  v: host, count = ncells * q^3 doubles, copied; all
+ * finite.  v = NULL with count = 0 clears.  A wrong count returns
+ * CHFSI_ERR_ARG.  Invalidates any previous chfsi_build. */
+chfsi_status chfsi_set_potential_qp(chfsi_ctx* ctx, const double* v, int64_t count);
+
 /* Separable nonlocal projectors (Eqs. nlps, nonlocalHamDiscrete): per site s,
  * four channels chi = g(r) {1, x/sigma, y/sigma, z/sigma}, g = exp(-r^2/(2 sigma^2))
  * for r <= rcut (0 beyond), r to the nearest periodic image, with couplings

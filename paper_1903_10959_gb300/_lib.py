@@ -69,6 +69,7 @@ _SIGS = {
     "chfsi_device_bytes": (_i64, [_vp]),
     "chfsi_mass_diag": (C.c_int, [_vp, _dp]),
     "chfsi_set_potential_gaussians": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp]),
+    "chfsi_set_potential_qp": (C.c_int, [_vp, _dp, _i64]),
     "chfsi_set_projectors": (C.c_int, [_vp, C.c_int, _dp, _dp, C.c_double, C.c_double]),
     "chfsi_build": (C.c_int, [_vp]),
     "chfsi_set_blocking": (C.c_int, [_vp, C.c_int, C.c_int]),
@@ -229,6 +230,16 @@ class Context:
         n = len(depths)
         c, d, w = _host(centres, 3 * n), _host(depths, n), _host(widths, n)
         self._check(self._lib.chfsi_set_potential_gaussians(self._h, n, _ptr(c), _ptr(d), _ptr(w)))
+
+    def set_potential_qp(self, values=None):
+        """General V_eff at the Gauss points (chfsi_set_potential_qp): ncells * q^3
+        values, cells x fastest, point a + q (b + q c); added to the wells.
+        None clears."""
+        if values is None:
+            self._check(self._lib.chfsi_set_potential_qp(self._h, None, 0))
+            return
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1))
+        self._check(self._lib.chfsi_set_potential_qp(self._h, _ptr(v), int(v.size)))
 
     def set_projectors(self, centres, h, sigma=0.8, rcut=3.0):
         n = len(centres)

@@ -720,6 +720,24 @@ chfsi_status chfsi_set_potential_gaussians(chfsi_ctx* ctx, int n, const double* 
   return CHFSI_OK;
 }
 
+chfsi_status chfsi_set_potential_qp(chfsi_ctx* ctx, const double* v, int64_t count) {
+  CHECK_CTX();
+  const HostMesh& m = ctx->mesh;
+  const int64_t want = m.ncells * (int64_t)m.q * m.q * m.q;
+  if (count == 0 && !v) {
+    ctx->wells.vqp.clear();
+  } else {
+    if (!v || count != want)
+      return fail(ctx, CHFSI_ERR_ARG, "potential values: need ncells * q^3 = " + std::to_string(want) +
+                                          ", got " + std::to_string(count));
+    for (int64_t i = 0; i < count; ++i)
+      if (!std::isfinite(v[i])) return fail(ctx, CHFSI_ERR_ARG, "potential values must be finite");
+    ctx->wells.vqp.assign(v, v + count);
+  }
+  ctx->built = false;
+  return CHFSI_OK;
+}
+
 chfsi_status chfsi_set_projectors(chfsi_ctx* ctx, int n, const double* xyz, const double* h,
                                   double sigma, double rcut) {
   CHECK_CTX();

@@ -71,6 +71,9 @@ void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
 
 struct Wells {
   std::vector<double> xyz, depth, width;
+  // optional potential values at the Gauss points of every cell, added to the
+  // wells (cells x fastest, point a + q (b + q c)); empty when unset
+  std::vector<double> vqp;
 };
 struct Projectors {
   std::vector<double> xyz, h;

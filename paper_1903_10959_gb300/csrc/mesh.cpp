@@ -331,11 +331,13 @@ void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>
         dd.push_back(idp[a]);
         inv2w2.push_back(1.0 / (2.0 * iw[a] * iw[a]));
       }
+      const double* vq = wl.vqp.empty() ? nullptr : wl.vqp.data() + e * (int64_t)q * q * q;
       for (int c = 0; c < q; ++c) for (int b = 0; b < q; ++b) for (int a = 0; a < q; ++a) {
         xq[0] = lo[0] + (m.gq_x[a] + 1.0) * m.h[0] / 2.0;
         xq[1] = lo[1] + (m.gq_x[b] + 1.0) * m.h[1] / 2.0;
         xq[2] = lo[2] + (m.gq_x[c] + 1.0) * m.h[2] / 2.0;
-        V[(c * q + b) * q + a] = well_sum(xq, cx, dd, inv2w2) * jac;
+        const int pt = (c * q + b) * q + a;
+        V[pt] = (well_sum(xq, cx, dd, inv2w2) + (vq ? vq[pt] : 0.0)) * jac;
       }
       // T1[c][b][il] = sum_a BB[a][il] V[c][b][a]
       for (int cb = 0; cb < q * q; ++cb)
