@@ -160,21 +160,34 @@ class CellBasis:
         return cell_origin[None, :] + (self.ref_pts + 1.0) * self.h / 2.0
 
 
+def periodic_axes(periodic) -> tuple:
+    """Per-axis periodicity (x, y, z) from one flag for all axes or three flags."""
+    if np.ndim(periodic) == 0:
+        return (bool(periodic),) * 3
+    t = tuple(bool(v) for v in periodic)
+    if len(t) != 3:
+        raise ValueError("periodic: one flag or three (x, y, z)")
+    return t
+
+
 class Mesh:
     """Uniform mesh of ncell^3 cubes of side h = L / ncell on [0, L]^3.
 
-    Periodic: global node g = (c p + i) mod (ncell p) per axis, so the nodes
-    of opposite faces are identified (periodic boundary conditions, Sec. 2.1).
-    Non-periodic: homogeneous Dirichlet, the boundary nodes g = 0 and
-    g = ncell p are removed from the unknowns (H^1_0 space, Sec. 2.2).
-    Unknowns are numbered x fastest.
+    Each axis is periodic or Dirichlet (periodic, non-periodic and
+    semi-periodic boundary conditions, Sec. 1 and Sec. 2.1-2.2).  Periodic
+    axis: global node g = (c p + i) mod (ncell p), so the nodes of opposite
+    faces are identified.  Dirichlet axis: homogeneous Dirichlet, the boundary
+    nodes g = 0 and g = ncell p are removed from the unknowns (H^1_0 along
+    that axis).  Unknowns are numbered x fastest.
     """
 
-    def __init__(self, ncell: int, p: int, L: float, periodic: bool):
-        self.ncell, self.p, self.L, self.periodic = ncell, p, L, periodic
+    def __init__(self, ncell: int, p: int, L: float, periodic):
+        self.ncell, self.p, self.L = ncell, p, L
+        self.per = periodic_axes(periodic)
+        self.periodic = all(self.per)
         self.h = L / ncell
-        self.n1d = ncell * p if periodic else ncell * p - 1
-        self.ndofs = self.n1d ** 3
+        self.nd = tuple(ncell * p if pa else ncell * p - 1 for pa in self.per)
+        self.ndofs = self.nd[0] * self.nd[1] * self.nd[2]
         self.ncells = ncell ** 3
         self.ne = (p + 1) ** 3
 
@@ -186,9 +199,9 @@ class Mesh:
         cx, cy, cz = self.cell_coords(e)
         return np.array([cx, cy, cz], dtype=np.float64) * self.h
 
-    def _global_1d(self, c: int, i: int) -> int:
+    def _global_1d(self, c: int, i: int, axis: int = 0) -> int:
         g = c * self.p + i
-        if self.periodic:
+        if self.per[axis]:
             return g % (self.ncell * self.p)
         if g == 0 or g == self.ncell * self.p:
             return -1
@@ -198,18 +211,19 @@ class Mesh:
         """Global unknown of each local node of cell e (-1: eliminated node)."""
         cx, cy, cz = self.cell_coords(e)
         p = self.p
+        nx, ny = self.nd[0], self.nd[1]
         out = np.empty(self.ne, dtype=np.int64)
         for k in range(p + 1):
-            gz = self._global_1d(cz, k)
+            gz = self._global_1d(cz, k, 2)
             for j in range(p + 1):
-                gy = self._global_1d(cy, j)
+                gy = self._global_1d(cy, j, 1)
                 for i in range(p + 1):
-                    gx = self._global_1d(cx, i)
+                    gx = self._global_1d(cx, i, 0)
                     n = local_index(p, i, j, k)
                     if gx < 0 or gy < 0 or gz < 0:
                         out[n] = -1
                     else:
-                        out[n] = gx + self.n1d * (gy + self.n1d * gz)
+                        out[n] = gx + nx * (gy + ny * gz)
         return out
 
     def dofmap(self) -> np.ndarray:
@@ -219,26 +233,26 @@ class Mesh:
         c = np.stack([e % n, (e // n) % n, e // (n * n)], axis=1)
         i = np.arange(p + 1)
         g = c[:, :, None] * p + i[None, None, :]           # (ncells, 3, p+1)
-        if self.periodic:
-            g = g % (n * p)
-        else:
-            g = np.where((g == 0) | (g == n * p), -1, g - 1)
+        for a in range(3):
+            if self.per[a]:
+                g[:, a] = g[:, a] % (n * p)
+            else:
+                g[:, a] = np.where((g[:, a] == 0) | (g[:, a] == n * p), -1, g[:, a] - 1)
         gx = g[:, 0][:, None, None, :]
         gy = g[:, 1][:, None, :, None]
         gz = g[:, 2][:, :, None, None]
-        d = gx + self.n1d * (gy + self.n1d * gz)
+        d = gx + self.nd[0] * (gy + self.nd[1] * gz)
         bad = (gx < 0) | (gy < 0) | (gz < 0)
         return np.where(bad, -1, d).reshape(self.ncells, -1)
 
     def dof_coords(self) -> np.ndarray:
         """Physical coordinates of the unknowns (periodic nodes in [0, L))."""
-        if self.periodic:
-            g = np.arange(self.n1d)
-        else:
-            g = np.arange(1, self.n1d + 1)
         nodes, _ = gll_rule(self.p)
-        x1 = (g // self.p) * self.h + (nodes[g % self.p] + 1.0) * self.h / 2.0
-        X, Y, Z = np.meshgrid(x1, x1, x1, indexing="ij")
+        x1 = []
+        for a in range(3):
+            g = np.arange(self.nd[a]) if self.per[a] else np.arange(1, self.nd[a] + 1)
+            x1.append((g // self.p) * self.h + (nodes[g % self.p] + 1.0) * self.h / 2.0)
+        X, Y, Z = np.meshgrid(x1[0], x1[1], x1[2], indexing="ij")
         return np.stack([X.T.ravel(), Y.T.ravel(), Z.T.ravel()], axis=1)
 
 

@@ -8,8 +8,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * Standard form: H~ = M^{-1/2} H M^{-1/2} (Eq. hep).
 
 The effective potential is a sum of attractive Gaussian wells
-V(x) = -sum_a D_a exp(-|x - R_a|^2 / (2 w_a^2)); with periodic boundary
-conditions every well is summed over the 27 image shifts {-1, 0, 1}^3 L.
+V(x) = -sum_a D_a exp(-|x - R_a|^2 / (2 w_a^2)); every well is summed over
+its image shifts {-1, 0, 1} L along each periodic axis (27 images when all
+three are periodic).
 Projectors are chi(r) = g(r) {1, x/s, y/s, z/s}, g = exp(-r^2 / (2 s^2)) for
 r <= r_c and 0 beyond (one s-like and three p-like channels per site, the
 l, m structure of Eq. nlps), r measured to the nearest periodic image.
@@ -21,14 +22,16 @@ import itertools
 import numpy as np
 import scipy.sparse as sp
 
-from .fe import CellBasis, Mesh, assemble_mass_diag
+from .fe import CellBasis, Mesh, assemble_mass_diag, periodic_axes
 
 
-def gaussian_wells(x: np.ndarray, centres, depths, widths, L: float, periodic: bool):
-    """V at points x (n, 3): -sum_a D_a exp(-|x - R_a - shift|^2 / (2 w_a^2))."""
+def gaussian_wells(x: np.ndarray, centres, depths, widths, L: float, periodic):
+    """V at points x (n, 3): -sum_a D_a exp(-|x - R_a - shift|^2 / (2 w_a^2)),
+    shifts over the images along the periodic axes."""
     x = np.asarray(x, dtype=np.float64)
     v = np.zeros(len(x))
-    shifts = (itertools.product((-1, 0, 1), repeat=3) if periodic else [(0, 0, 0)])
+    per = periodic_axes(periodic)
+    shifts = itertools.product(*[(-1, 0, 1) if pa else (0,) for pa in per])
     shifts = [np.array(s, dtype=np.float64) * L for s in shifts]
     for R, D, w in zip(np.asarray(centres), np.asarray(depths), np.asarray(widths)):
         for s in shifts:
@@ -150,12 +153,13 @@ class Problem:
         return (S @ H @ S).tocsr()
 
 
-def _min_image(d: np.ndarray, L: float, periodic: bool) -> np.ndarray:
-    return d - L * np.round(d / L) if periodic else d
+def _min_image(d: np.ndarray, L: float, periodic) -> np.ndarray:
+    per = np.array(periodic_axes(periodic))
+    return np.where(per[None, :], d - L * np.round(d / L), d)
 
 
 def projector_values(x: np.ndarray, centre, sigma: float, rcut: float, L: float,
-                     periodic: bool) -> np.ndarray:
+                     periodic) -> np.ndarray:
     """chi_{s,k}(x) for the 4 channels at points x: (n, 4) (Eq. nlps form)."""
     d = _min_image(np.asarray(x) - np.asarray(centre), L, periodic)
     r2 = np.sum(d * d, axis=1)
@@ -175,7 +179,7 @@ def projector_matrix(prob: Problem, centres, sigma, rcut, h):
         d = mesh.cell_dofs(e)
         ok = d >= 0
         for s in range(ns):
-            chi = projector_values(xq, centres[s], sigma, rcut, mesh.L, mesh.periodic)
+            chi = projector_values(xq, centres[s], sigma, rcut, mesh.L, mesh.per)
             if not np.any(chi):
                 continue
             ce = (basis.W[:, None, None] * basis.N[:, :, None] * chi[:, None, :]).sum(0)  # (ne, 4)

@@ -31,9 +31,9 @@ def test_dropped_half_in_kinetic_term_is_caught(monkeypatch):
 
 
 def test_wrong_periodic_wrap_is_caught(monkeypatch):
-    def bad_global(self, c, i):
+    def bad_global(self, c, i, axis=0):
         g = c * self.p + i
-        if self.periodic:
+        if self.per[axis]:
             return g if g < self.ncell * self.p else 1   # should wrap to 0
         return -1 if g in (0, self.ncell * self.p) else g - 1
     monkeypatch.setattr(fe.Mesh, "_global_1d", bad_global)
@@ -120,3 +120,14 @@ def test_wrong_sign_of_fractional_correction_is_caught(monkeypatch):
     rho_full = od.density(prob, XR * np.sqrt(f)[None, :])
     rho_bad = od.density(prob, X, X_fr, 2.0 - occ)          # planted: f - 1 -> 1 - f
     assert np.abs(rho_bad - rho_full).max() > 1e-3 * np.abs(rho_full).max()
+
+
+def test_periodic_images_along_a_dirichlet_axis_are_caught(monkeypatch):
+    """Semi-periodic systems: a well summed over images along every axis,
+    the Dirichlet one included, must fail the image pin."""
+    monkeypatch.setattr(ham, "periodic_axes", lambda per: (True, True, True))
+    c, d, w = np.array([[0.5, 0.5, 3.0]]), np.array([2.0]), np.array([1.0])
+    b = np.array([[0.5, 0.5, 5.8]])
+    v_slab = ham.gaussian_wells(b, c, d, w, 6.0, (True, True, False))[0]
+    v_open = -2.0 * np.exp(-2.8 ** 2 / 2.0)          # the well itself; no z image
+    assert abs(v_slab - v_open) > 1e-3
