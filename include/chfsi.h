@@ -69,15 +69,19 @@ typedef enum {
 
 /* Uniform mesh of ncell[0] x ncell[1] x ncell[2] boxes on [0,len[0]] x ... .
  * p: FE degree (1..8), n_e = (p+1)^3 nodes per cell, GLL nodes (Sec. 2.4).
- * periodic != 0: periodic in all three directions (requires ncell[d] >= 2);
- * otherwise homogeneous Dirichlet (boundary nodes eliminated).
+ * periodic[d] != 0: axis d periodic (opposite faces identified; requires
+ * ncell[d] >= 2); otherwise homogeneous Dirichlet on the two faces normal to
+ * axis d (boundary nodes eliminated; requires ncell[d] p >= 2).  All three
+ * set: a periodic crystal; none: an isolated system; some: a semi-periodic
+ * system such as a slab (the paper's periodic, non-periodic and
+ * semi-periodic boundary conditions, Sec. 1).
  * quad_points: Gauss-Legendre points per direction for the Hamiltonian
  * integrals (0 selects p + 2); the mass always uses the GLL rule. */
 typedef struct {
   int ncell[3];
   double len[3];
   int p;
-  int periodic;
+  int periodic[3];
   int quad_points;
 } chfsi_mesh_desc;
 
@@ -88,15 +92,16 @@ chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx**
 chfsi_status chfsi_destroy(chfsi_ctx* ctx);
 const char*  chfsi_last_error(const chfsi_ctx* ctx);
 
-/* Number of unknowns M: (n p)^3 periodic, (n p - 1)^3 Dirichlet (per axis). */
+/* Number of unknowns M: the product over the axes of n p (periodic axis) or
+ * n p - 1 (Dirichlet axis). */
 int64_t      chfsi_num_dofs(const chfsi_ctx* ctx);
 
 /* Global diagonal mass M_jj (GLL quadrature; text after Eq. hep) -> host_out[M]. */
 chfsi_status chfsi_mass_diag(chfsi_ctx* ctx, double* host_out);
 
 /* Effective potential V(x) = -sum_a depth[a] exp(-|x - R_a|^2 / (2 width[a]^2)),
- * R_a = xyz[3a..3a+2]; with periodic meshes each well is summed over the 27
- * image shifts {-1,0,1}^3 * len.  Arrays are host, copied.  Invalidates any
+ * R_a = xyz[3a..3a+2]; each well is summed over its image shifts
+ * {-1,0,1} len[d] along every periodic axis d (27 images when all three are).  Arrays are host, copied.  Invalidates any
  * previous chfsi_build. */
 chfsi_status chfsi_set_potential_gaussians(chfsi_ctx* ctx, int n, const double* xyz,
                                            const double* depth, const double* width);
@@ -115,7 +120,7 @@ chfsi_status chfsi_set_potential_qp(chfsi_ctx* ctx, const double* v, int64_t cou
 
 /* Separable nonlocal projectors (Eqs. nlps, nonlocalHamDiscrete): per site s,
  * four channels chi = g(r) {1, x/sigma, y/sigma, z/sigma}, g = exp(-r^2/(2 sigma^2))
- * for r <= rcut (0 beyond), r to the nearest periodic image, with couplings
+ * for r <= rcut (0 beyond), r to the nearest image along the periodic axes, with couplings
  * h[4 s + k] (Ha).  H_nl = sum C^T h C, C_{k,j} = int chi_k N_j.  n = 0 clears. */
 chfsi_status chfsi_set_projectors(chfsi_ctx* ctx, int n, const double* xyz, const double* h,
                                   double sigma, double rcut);

@@ -32,7 +32,17 @@ class ChfsiError(RuntimeError):
 
 class MeshDesc(C.Structure):
     _fields_ = [("ncell", C.c_int * 3), ("len", C.c_double * 3), ("p", C.c_int),
-                ("periodic", C.c_int), ("quad_points", C.c_int)]
+                ("periodic", C.c_int * 3), ("quad_points", C.c_int)]
+
+
+def _axes(periodic):
+    """Per-axis periodic flags (x, y, z) from one flag or three."""
+    if np.ndim(periodic) == 0:
+        return (int(bool(periodic)),) * 3
+    t = tuple(int(bool(v)) for v in periodic)
+    if len(t) != 3:
+        raise ValueError("periodic: one flag or three (x, y, z)")
+    return t
 
 
 MAX_SOLVES = 16
@@ -176,13 +186,15 @@ class Context:
     """One discretised problem on the current CUDA device (chfsi_ctx)."""
 
     def __init__(self, ncell, length, p, periodic=True, quad_points=0, stream=None):
+        """``periodic``: one flag for all axes or three (x, y, z); a Dirichlet
+        axis drops the nodes of its two faces."""
         lib = load()
         if np.isscalar(ncell):
             ncell = (ncell,) * 3
         if np.isscalar(length):
             length = (float(length),) * 3
-        d = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p), int(bool(periodic)),
-                     int(quad_points))
+        d = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p),
+                     (C.c_int * 3)(*_axes(periodic)), int(quad_points))
         h = _vp()
         s = _vp(stream.cuda_stream) if stream is not None else _vp(None)
         self._lib = lib
@@ -462,8 +474,8 @@ def _request(mesh, n, centres, depths, widths, depth_seq=(), degree=30, iters=20
         raise ValueError("inconsistent well arrays")
     resolves = seq.size // nw if nw else len(depth_seq)
     ncell, length, p, periodic = mesh[:4]
-    md = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p), int(bool(periodic)),
-                  int(mesh[4]) if len(mesh) > 4 else 0)
+    md = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p),
+                  (C.c_int * 3)(*_axes(periodic)), int(mesh[4]) if len(mesh) > 4 else 0)
     r = Request(md, int(n), nw, _ptr(xyz), _ptr(dep), _ptr(wid), int(resolves),
                 _ptr(seq) if seq.size else None, int(degree), int(iters), int(warm_iters),
                 float(tol), int(n_check), _prec(prec), int(seed))

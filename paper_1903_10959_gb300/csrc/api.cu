@@ -605,13 +605,13 @@ chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx**
   if (desc->p < 1 || desc->p > 8) return CHFSI_ERR_ARG;
   for (int a = 0; a < 3; ++a) {
     if (desc->ncell[a] < 1 || !(desc->len[a] > 0.0)) return CHFSI_ERR_ARG;
-    if (desc->periodic && desc->ncell[a] < 2) return CHFSI_ERR_ARG;
-    if (!desc->periodic && desc->ncell[a] * desc->p < 2) return CHFSI_ERR_ARG;
+    if (desc->periodic[a] && desc->ncell[a] < 2) return CHFSI_ERR_ARG;
+    if (!desc->periodic[a] && desc->ncell[a] * desc->p < 2) return CHFSI_ERR_ARG;
   }
   if (desc->quad_points < 0 || desc->quad_points > 16) return CHFSI_ERR_ARG;
   int64_t nd = 1;
-  for (int a = 0; a < 3; ++a) nd *= desc->periodic ? (int64_t)desc->ncell[a] * desc->p
-                                                   : (int64_t)desc->ncell[a] * desc->p - 1;
+  for (int a = 0; a < 3; ++a) nd *= desc->periodic[a] ? (int64_t)desc->ncell[a] * desc->p
+                                                      : (int64_t)desc->ncell[a] * desc->p - 1;
   if (nd >= (int64_t)1 << 31) return CHFSI_ERR_ARG;
   chfsi_ctx* ctx = new chfsi_ctx();
   ctx->stream = (cudaStream_t)stream;

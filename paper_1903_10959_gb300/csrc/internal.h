@@ -30,7 +30,7 @@ struct HostMesh {
   int n[3];
   double len[3], h[3];
   int p, n1, ne, q;            // degree, nodes per direction, nodes per cell, quad points
-  bool periodic;
+  bool per[3];                 // axis periodic (else Dirichlet)
   int64_t nd[3];               // unknowns per direction
   int64_t ndofs;
   int64_t ncells;

@@ -127,13 +127,13 @@ static void basis_at(const std::vector<double>& xn, const std::vector<double>& t
 
 static int64_t global_1d(const HostMesh& m, int axis, int c, int i) {
   int64_t g = (int64_t)c * m.p + i;
-  if (m.periodic) return g % ((int64_t)m.n[axis] * m.p);
+  if (m.per[axis]) return g % ((int64_t)m.n[axis] * m.p);
   if (g == 0 || g == (int64_t)m.n[axis] * m.p) return -1;
   return g - 1;
 }
 
 static int colour_1d(const HostMesh& m, int axis, int c) {
-  if (m.periodic && (m.n[axis] % 2 == 1) && c == m.n[axis] - 1) return 2;
+  if (m.per[axis] && (m.n[axis] % 2 == 1) && c == m.n[axis] - 1) return 2;
   return c % 2;
 }
 
@@ -142,12 +142,12 @@ void build_mesh(const chfsi_mesh_desc& d, HostMesh& m) {
   m.n1 = d.p + 1;
   m.ne = m.n1 * m.n1 * m.n1;
   m.q = d.quad_points > 0 ? d.quad_points : d.p + 2;
-  m.periodic = d.periodic != 0;
   for (int a = 0; a < 3; ++a) {
+    m.per[a] = d.periodic[a] != 0;
     m.n[a] = d.ncell[a];
     m.len[a] = d.len[a];
     m.h[a] = d.len[a] / d.ncell[a];
-    m.nd[a] = m.periodic ? (int64_t)d.ncell[a] * d.p : (int64_t)d.ncell[a] * d.p - 1;
+    m.nd[a] = m.per[a] ? (int64_t)d.ncell[a] * d.p : (int64_t)d.ncell[a] * d.p - 1;
   }
   m.ndofs = m.nd[0] * m.nd[1] * m.nd[2];
   m.ncells = (int64_t)m.n[0] * m.n[1] * m.n[2];
@@ -294,12 +294,13 @@ void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>
     for (int i = 0; i < n1; ++i)
       for (int l = 0; l < n1; ++l) BB[a * nn + i * n1 + l] = m.gq_w[a] * m.B[a * n1 + i] * m.B[a * n1 + l];
 
-  // wells: periodic images as explicit centres; cut off where the Gaussian is < 1e-18 D
+  // wells: images along the periodic axes as explicit centres; cut off where
+  // the Gaussian is < 1e-18 D
   std::vector<double> ic, idp, iw;
   const int nw = (int)wl.depth.size();
   for (int a = 0; a < nw; ++a) {
     for (int sz = -1; sz <= 1; ++sz) for (int sy = -1; sy <= 1; ++sy) for (int sx = -1; sx <= 1; ++sx) {
-      if (!m.periodic && (sx || sy || sz)) continue;
+      if ((!m.per[0] && sx) || (!m.per[1] && sy) || (!m.per[2] && sz)) continue;
       ic.push_back(wl.xyz[3 * a] + sx * m.len[0]);
       ic.push_back(wl.xyz[3 * a + 1] + sy * m.len[1]);
       ic.push_back(wl.xyz[3 * a + 2] + sz * m.len[2]);
@@ -407,7 +408,7 @@ void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& o
           double lo = c3[ax] * m.h[ax], hi = lo + m.h[ax];
           double best = 1e300;
           for (int sh = -1; sh <= 1; ++sh) {
-            if (!m.periodic && sh) continue;
+            if (!m.per[ax] && sh) continue;
             double c = R[ax] + sh * m.len[ax];
             double dl = c < lo ? lo - c : (c > hi ? c - hi : 0.0);
             best = std::min(best, dl);
@@ -424,7 +425,7 @@ void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& o
           double d[3], rr = 0.0;
           for (int ax = 0; ax < 3; ++ax) {
             d[ax] = x[ax] - R[ax];
-            if (m.periodic) d[ax] -= m.len[ax] * std::nearbyint(d[ax] / m.len[ax]);
+            if (m.per[ax]) d[ax] -= m.len[ax] * std::nearbyint(d[ax] / m.len[ax]);
             rr += d[ax] * d[ax];
           }
           int qi = (c * q + b) * q + a;

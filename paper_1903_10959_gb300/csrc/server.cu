@@ -80,7 +80,7 @@ size_t estimate_bytes(const chfsi_request& r) {
   size_t ncells = 1, M = 1;
   for (int a = 0; a < 3; ++a) {
     ncells *= (size_t)d.ncell[a];
-    M *= d.periodic ? (size_t)d.ncell[a] * p : (size_t)d.ncell[a] * p - 1;
+    M *= d.periodic[a] ? (size_t)d.ncell[a] * p : (size_t)d.ncell[a] * p - 1;
   }
   const bool mixed = r.prec != CHFSI_FP64;
   const size_t es = mixed ? 4 : 8, n = (size_t)r.n, B = std::min<size_t>(200, n);
