@@ -21,6 +21,9 @@ Every function cites the passage of arXiv:1903.10959 (DFT-FE) it follows:
                      bound estimate, residuals and the iteration loop.
 * ``density``     -- spectrum-splitting Rayleigh-Ritz (Algorithm rr), Fermi
                      level and electron density (Algorithm dc, Eq. elecDensSP).
+* ``matrix_free`` -- the cell action of Eq. discreteHam by sum factorisation
+                     (the matrix-free alternative named in Sec. 3.3.1) and its
+                     exact flop count.
 
 Parity status: every function is pinned by ``-m "not gpu"`` tests against
 closed forms, textbook rules, brute-force dense diagonalisation or
