@@ -1,13 +1,16 @@
 // Mixed-precision kernels on the 5th-generation tensor cores (tcgen05,
-// kind::tf32, FP32 accumulation in TMEM) for sm_103a.
+// kind::tf32 and kind::f16, FP32 accumulation in TMEM) for sm_103a.
 //
-// Precision scheme (the mixed strategy of Secs. 3.4.1 and 3.5.2 of
+// Precision scheme (the mixed strategy of Secs. 3.4.2 and 3.5.2 of
 // arXiv:1903.10959, moved onto tensor cores): every operand x is split into
 // x_hi = tf32(x) and x_lo = tf32(x - x_hi); a product a.b is evaluated as
 // a_lo.b_hi + a_hi.b_lo + a_hi.b_hi ("3xTF32", binary32-level accuracy) or
-// as a_hi.b_hi alone ("1xTF32").  Wavefunction blocks are stored in
-// binary32.  Diagonal blocks of the overlap / projected matrices and of the
-// CholGS factor are evaluated in binary64 (the paper's S_d and L^{-1}_d).
+// as a_hi.b_hi alone ("1xTF32").  The cell products can instead split both
+// operands into three bf16 terms (exact for binary32) and keep the six
+// products down to 2^-24 ("BF16x3", kind::f16).  Wavefunction blocks are
+// stored in binary32.  Diagonal blocks of the overlap / projected matrices
+// and of the CholGS factor are evaluated in binary64 (the paper's S_d and
+// L^{-1}_d).
 //
 //  tc_cell_r    : the cell-by-cell products H~_e Y_e of Sec. 3.3.1 for all
 //                 cells in one launch, one CTA per (cell, 64-column tile);
@@ -15,6 +18,8 @@
 //                 with bulk async copies, warps 0-3 gather + split the cell
 //                 block of Y into shared memory and later store the result
 //                 block, warp 5 issues the MMAs.
+//  tc_cell_bf16 : the same products in BF16x3 as R_e^T = Y_e^T H~_e, one CTA
+//                 per (cell, 128-column tile, part of <= 256 cell rows).
 //  tc_assemble  : owner-computes sum of the cell blocks per unknown fused with
 //                 the Chebyshev three-term update (Eq. chebFilter).
 //  tc_gram      : lower tiles of A^T B over the unknowns (Algorithm CholGS
