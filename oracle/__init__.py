@@ -24,6 +24,8 @@ Every function cites the passage of arXiv:1903.10959 (DFT-FE) it follows:
 * ``matrix_free`` -- the cell action of Eq. discreteHam by sum factorisation
                      (the matrix-free alternative named in Sec. 3.3.1) and its
                      exact flop count.
+* ``kpoints``     -- the Bloch-periodic Hamiltonian H~(k) of Eq. evp
+                     (Eq. ksproblemPer), local part.
 
 Parity status: every function is pinned by ``-m "not gpu"`` tests against
 closed forms, textbook rules, brute-force dense diagonalisation or

@@ -131,3 +131,24 @@ def test_periodic_images_along_a_dirichlet_axis_are_caught(monkeypatch):
     v_slab = ham.gaussian_wells(b, c, d, w, 6.0, (True, True, False))[0]
     v_open = -2.0 * np.exp(-2.8 ** 2 / 2.0)          # the well itself; no z image
     assert abs(v_slab - v_open) > 1e-3
+
+
+def test_dropped_k_squared_term_is_caught(monkeypatch):
+    """Bloch Hamiltonian: without the 1/2 |k|^2 term the free-particle bands
+    shift away from 1/2 |2 pi n / L + k|^2."""
+    from oracle import kpoints as kp
+    orig = kp.BlochProblem.__init__
+
+    def bad(self, prob, k):
+        orig(self, prob, k)
+        kG = sum(self.k[d] * self.G[d] for d in range(3))
+        self.shift = -1j * kG                        # 1/2 |k|^2 A dropped
+    monkeypatch.setattr(kp.BlochProblem, "__init__", bad)
+    L, k = 6.0, np.array([0.25, -0.4, 0.1])
+    prob = ham.Problem(3, 4, L, True, lambda x: np.zeros(len(x)))
+    ev = np.linalg.eigvalsh(kp.BlochProblem(prob, k).dense_Htilde())
+    g = 2 * np.pi / L
+    n = np.arange(-3, 4)
+    G = np.stack(np.meshgrid(n, n, n, indexing="ij"), -1).reshape(-1, 3) * g
+    ref = np.sort(0.5 * np.sum((G + k) ** 2, axis=1))
+    assert not np.allclose(ev[:12], ref[:12], rtol=2e-3)
