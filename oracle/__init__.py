@@ -26,6 +26,9 @@ Every function cites the passage of arXiv:1903.10959 (DFT-FE) it follows:
                      exact flop count.
 * ``kpoints``     -- the Bloch-periodic Hamiltonian H~(k) of Eq. evp
                      (Eq. ksproblemPer), local part.
+* ``scf``         -- Algorithm scf on Gaussian-charge systems: periodic
+                     Poisson solve (Eq. ksproblemPer), LDA exchange, ChFSI
+                     passes, Fermi-Dirac density and Anderson mixing (Sec. 3.6).
 
 Parity status: every function is pinned by ``-m "not gpu"`` tests against
 closed forms, textbook rules, brute-force dense diagonalisation or

@@ -152,3 +152,21 @@ def test_dropped_k_squared_term_is_caught(monkeypatch):
     G = np.stack(np.meshgrid(n, n, n, indexing="ij"), -1).reshape(-1, 3) * g
     ref = np.sort(0.5 * np.sum((G + k) ** 2, axis=1))
     assert not np.allclose(ev[:12], ref[:12], rtol=2e-3)
+
+
+def test_dropped_four_pi_in_poisson_is_caught(monkeypatch):
+    """SCF electrostatics: -(1/4 pi) lap phi = f solved without the 4 pi
+    misses the single-Fourier-mode closed form."""
+    from oracle import scf
+    orig = scf.load_vector
+
+    def bad(prob, fq):
+        return orig(prob, fq) / (4.0 * np.pi)
+    monkeypatch.setattr(scf, "load_vector", bad)
+    L, amp = 6.0, 0.7
+    prob = scf.FieldProblem(3, 4, L, True)
+    xq = scf.gauss_points(prob)
+    k = 2 * np.pi / L
+    phi = scf.poisson_periodic(prob, amp * np.cos(k * xq[..., 0]))
+    exact = 4 * np.pi * amp / k ** 2 * np.cos(k * prob.mesh.dof_coords()[:, 0])
+    assert np.abs(phi - exact).max() > 0.5 * np.abs(exact).max()
