@@ -59,6 +59,7 @@ def fermi_level(evals_fr, n_oc: int, n_electrons: float, kT: float):
     eps = np.asarray(evals_fr, dtype=np.float64)
 
     def count(mu):
+        """Electron count 2 (n_oc + sum f) at Fermi level mu."""
         return 2.0 * (n_oc + fermi_dirac(eps, mu, kT).sum())
 
     lo = eps.min() - 60.0 * kT

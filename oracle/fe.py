@@ -192,10 +192,12 @@ class Mesh:
         self.ne = (p + 1) ** 3
 
     def cell_coords(self, e: int):
+        """(cx, cy, cz) of cell e, x fastest."""
         n = self.ncell
         return e % n, (e // n) % n, e // (n * n)
 
     def cell_origin(self, e: int) -> np.ndarray:
+        """Lower corner of cell e (cells of side h on the uniform mesh, Sec. 3.1)."""
         cx, cy, cz = self.cell_coords(e)
         return np.array([cx, cy, cz], dtype=np.float64) * self.h
 

@@ -66,6 +66,7 @@ class Problem:
 
     @property
     def ndofs(self):
+        """Number of unknowns M (size of Eq. hep)."""
         return self.mesh.ndofs
 
     def cell_hamiltonian(self, e: int) -> np.ndarray:
@@ -131,6 +132,7 @@ class Problem:
         return H
 
     def dense_Htilde(self) -> np.ndarray:
+        """Assembled H~ = M^{-1/2} H M^{-1/2} (Eq. hep; small meshes only)."""
         s = self.minv_sqrt
         return s[:, None] * self.dense_H() * s[None, :]
 

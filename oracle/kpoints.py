@@ -46,9 +46,11 @@ class BlochProblem:
 
     @property
     def ndofs(self):
+        """Number of unknowns M."""
         return self.prob.ndofs
 
     def cell_hamiltonian(self, e: int) -> np.ndarray:
+        """H_e(k) = H_e(0) - i k.G + 1/2 |k|^2 A (Eq. evp in FE form)."""
         return self.prob.cell_hamiltonian(e) + self.shift
 
     def apply_Htilde(self, X: np.ndarray) -> np.ndarray:

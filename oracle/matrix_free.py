@@ -31,6 +31,8 @@ _EIN = {0: "ai,kjic->kjac", 1: "aj,kjic->kaic", 2: "ak,kjic->ajic"}   # axis 0 =
 
 
 class Counter:
+    """Running flop count of the contractions of one apply."""
+
     def __init__(self):
         self.flops = 0
 

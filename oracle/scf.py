@@ -44,10 +44,12 @@ class FieldProblem(Problem):
         self.vq = np.zeros((self.mesh.ncells, self.basis.N.shape[0]))
 
     def set_vq(self, vq):
+        """New V_eff at the Gauss points (step 5 of Algorithm scf); drops cached H_e."""
         self.vq = np.asarray(vq, dtype=np.float64).reshape(self.mesh.ncells, -1)
         self._cellH = {}
 
     def cell_hamiltonian(self, e: int) -> np.ndarray:
+        """H_e = 1/2 K_e + V_e with V_e from the Gauss-point values (Eq. discreteHam)."""
         if e not in self._cellH:
             self._cellH[e] = 0.5 * self.K + self.basis.potential_matrix(self.vq[e])
         return self._cellH[e]
@@ -144,6 +146,7 @@ class Anderson:
         self.xs, self.rs = [], []
 
     def step(self, x, gx):
+        """Next iterate from the current x and g(x)."""
         x = np.asarray(x, dtype=np.float64).ravel()
         r = np.asarray(gx, dtype=np.float64).ravel() - x
         self.xs.append(x)
