@@ -184,9 +184,11 @@ chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, in
  * until the process exits.  Limit: M * ncol * 8 bytes (twice that plus
  * 4 * nsite * ncol * 8 with projectors) must fit in 64 MiB; larger requests
  * return CHFSI_ERR_ARG with the sizes in chfsi_last_error, so split the
- * columns over several calls.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and nothing in it needs to
+ * columns over several calls.  The context's device must be the current
+ * device (CHFSI_ERR_STATE otherwise).  The first call on a context looks up
+ * the array's device address (cudaGetSymbolAddress) and keeps it in the
+ * context; make that first call before any stream capture.  A failed lookup
+ * returns CHFSI_ERR_CUDA without latching the context.  All calls share the array and nothing in it needs to
  * start at zero (each call writes every scratch entry it reads); calls whose
  * work overlaps on the GPU (other streams, other contexts on the device)
  * race on it, so serialise them.  Asynchronous on the context's stream. */

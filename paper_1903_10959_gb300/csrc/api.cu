@@ -160,6 +160,7 @@ void free_device_data(chfsi_ctx* ctx) {
   release(ctx, ctx->d_site_c32, ctx->hproj.site_c.size() * 4);
   release(ctx, ctx->d_dof_c32, ctx->hproj.dof_c.size() * 4);
   ctx->built = false;
+  ++ctx->build_gen;   // device pointers captured elsewhere (batch graphs) are now stale
 }
 
 // One recurrence step over the ncol columns of a block:
@@ -560,25 +561,19 @@ constexpr size_t kNoallocScratchBytes = size_t(64) << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {nullptr};   // device address of the scratch, per device ordinal
-
-// Device address of the scratch on the current device.  The first call on a
-// device resolves it with cudaGetSymbolAddress (the array's host-side name is
-// only a stand-in and must never be handed to a kernel).
-cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+// Device address of the scratch for the context, resolved on the context's
+// first allocation-free call with cudaGetSymbolAddress (the array's host-side
+// name is only a stand-in and must never be handed to a kernel).  It is kept
+// in the context, so it lives exactly as long as the context's other device
+// pointers (a cudaDeviceReset invalidates both).
+cudaError_t noalloc_scratch(chfsi_ctx* ctx, void** out) {
+  if (!ctx->noalloc_scratch) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = p;
+    ctx->noalloc_scratch = p;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = ctx->noalloc_scratch;
   return cudaSuccess;
 }
 }  // namespace
@@ -786,6 +781,7 @@ chfsi_status chfsi_build(chfsi_ctx* ctx) {
   }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->built = true;
+  ++ctx->build_gen;
   return CHFSI_OK;
 }
 
@@ -906,10 +902,21 @@ chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, d
                 "chfsi_apply_noalloc: needs " + std::to_string(need) + " bytes of scratch for " +
                     std::to_string(ncol) + " columns, more than the fixed " +
                     std::to_string(kNoallocScratchBytes) + " bytes; use fewer columns per call");
+  // the scratch address belongs to the context's device, which must be current
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device) {
+    cudaGetLastError();
+    ctx->err = "chfsi_apply_noalloc: the context's device (" + std::to_string(ctx->device) +
+               ") is not the current device (" + std::to_string(cur) + ")";
+    return CHFSI_ERR_STATE;
+  }
   void* scratch = nullptr;
-  cudaError_t se = noalloc_scratch(&scratch);
-  if (se != cudaSuccess)
-    return fail(ctx, CHFSI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(se));
+  cudaError_t se = noalloc_scratch(ctx, &scratch);
+  if (se != cudaSuccess) {   // reported, not latched: the context stays usable
+    cudaGetLastError();
+    ctx->err = std::string("chfsi_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(se);
+    return CHFSI_ERR_CUDA;
+  }
   double* W = (double*)scratch;                       // written before read (MODE_STORE first)
   double* NL = nsite > 0 ? W + (size_t)m.ndofs * ncol : nullptr;
   double* Z = nsite > 0 ? NL + (size_t)m.ndofs * ncol : nullptr;

@@ -402,6 +402,8 @@ struct chfsi_batch {
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> g_x;
   std::vector<int> g_ncol;
+  std::vector<int64_t> g_ldx;
+  std::vector<uint64_t> g_gen;   // build generation of each member context at capture
   int g_degree = -1, g_split3 = -1, g_bn = -1, g_S = -1;
   // tile choice: BN (32 / 64) and stages; set by the autotuner
   int bn = 64, S = -1;             // S < 0: the non-persistent multi-system kernel
@@ -539,6 +541,10 @@ chfsi_status bfail(chfsi_batch* b, chfsi_status st, const std::string& m) {
 
 chfsi_status batch_check(chfsi_batch* b, float* const* X, const int64_t* ldx, const int* ncol) {
   for (size_t i = 0; i < b->ctx.size(); ++i) {
+    const chfsi_ctx* c = b->ctx[i];
+    if (!c->built || c->hproj.nsite > 0 || c->latched != CHFSI_OK)
+      return bfail(b, CHFSI_ERR_STATE, "system " + std::to_string(i) +
+                                           " is not built, has projectors or has a latched error");
     if (!X || !X[i] || !ldx || !ncol || ncol[i] < 1 || ldx[i] < ncol[i])
       return bfail(b, CHFSI_ERR_ARG, "bad X / ldx / ncol for system " + std::to_string(i));
   }
@@ -671,10 +677,14 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
   const int bn = b->bn;
   const int S = b->S != 0 ? b->S : default_stages(b, bn, split3);
   if (b->own_stream) cudaDeviceSynchronize();   // order after the caller's work on any stream
-  // the graph is valid while pointers, widths, degree and tile choice stay the same
+  // the graph is valid while pointers, widths, strides, degree and tile choice stay the
+  // same and no member context has been rebuilt (a rebuild frees the cell data and
+  // the dof map the graph's descriptors point to)
   bool same = b->gexec && b->g_degree == degree && b->g_split3 == split3 && b->g_bn == bn &&
               b->g_S == S && (int)b->g_x.size() == n;
-  for (int i = 0; same && i < n; ++i) same = b->g_x[i] == X[i] && b->g_ncol[i] == ncol[i];
+  for (int i = 0; same && i < n; ++i)
+    same = b->g_x[i] == X[i] && b->g_ncol[i] == ncol[i] && b->g_ldx[i] == ldx[i] &&
+           b->g_gen[i] == b->ctx[i]->build_gen;
   cudaStreamSynchronize(b->stream);            // h_coef may still feed the previous replay
   if (!same) {
     batch_free_graph(b);
@@ -699,6 +709,9 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
     }
     b->g_x.assign(X, X + n);
     b->g_ncol.assign(ncol, ncol + n);
+    b->g_ldx.assign(ldx, ldx + n);
+    b->g_gen.resize(n);
+    for (int i = 0; i < n; ++i) b->g_gen[i] = b->ctx[i]->build_gen;
     b->g_degree = degree;
     b->g_split3 = split3;
     b->g_bn = bn;

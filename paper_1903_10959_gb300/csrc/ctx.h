@@ -17,6 +17,8 @@ struct chfsi_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   bool built = false;
+  uint64_t build_gen = 0;
+  void* noalloc_scratch = nullptr; // device address of the fixed no-allocation scratch          // bumped whenever the device cell data is rebuilt or freed
   chfsi_status latched = CHFSI_OK;
   std::string err;
   int filter_block = 200, diag_block = 1;

@@ -151,3 +151,57 @@ def test_batched_solve_with_tf32x3_orthogonalisation(batch_setup):
     ev1 = B1.solve(X1, iters, m, bnd[1:2], orth_prec="mixed")
     B1.destroy()
     assert np.abs(ev1[0] - evs[1]).max() <= 1e-10
+
+
+def test_graph_replay_after_rebuild_and_new_stride():
+    """The captured graph must not be replayed when a member context was
+    rebuilt (new potential: its cell data and dof map are new allocations) or
+    when only a block's leading dimension changed (same pointer, same width):
+    both cases re-describe the batch, and every system then matches the
+    single-system filter at 1e-6."""
+    systems = _systems()[:3]
+    ctxs = [gpu_context(s) for s in systems]
+    try:
+        B = Batch(ctxs)
+        n = len(ctxs)
+        X0 = [W.start_block(51 + i, c.ndofs, s.n_sub).astype(np.float32) for i, (s, c) in
+              enumerate(zip(systems, ctxs))]
+        a, b, a0 = np.full(n, 5.0), np.full(n, 60.0), np.full(n, -3.0)
+        M0, n0 = ctxs[0].ndofs, systems[0].n_sub
+        buf = torch.zeros(M0 * (n0 + 8), device=DEV)      # member 0 lives in this buffer
+        dense0 = buf[:M0 * n0].view(M0, n0)               # ldx = n0
+        X = [dense0] + [torch.tensor(x, device=DEV) for x in X0[1:]]
+
+        def reset(views):
+            buf.zero_()
+            for i in range(n):
+                views[i].copy_(torch.tensor(X0[i], device=DEV))
+
+        def check(views):
+            for i, c in enumerate(ctxs):
+                Xs = torch.tensor(X0[i], device=DEV)
+                c.filter(Xs, 6, a[i], b[i], a0[i], prec="mixed")
+                assert rel_fro(views[i].cpu().numpy(), Xs.cpu().numpy()) < 1e-6
+
+        reset(X)
+        B.filter(X, 6, a, b, a0)                          # captures the graph
+        check(X)
+        # rebuild member 1 with deeper wells, then filter the same buffers again
+        s1 = systems[1]
+        ctxs[1].set_potential_gaussians(s1.centres, 1.7 * s1.depths, s1.widths)
+        ctxs[1].build()
+        reset(X)
+        B.filter(X, 6, a, b, a0)
+        check(X)
+        # same pointers and widths; member 0 now strided with ldx = n0 + 8
+        strided0 = buf.view(M0, n0 + 8)[:, :n0]
+        assert strided0.data_ptr() == dense0.data_ptr()
+        X2 = [strided0] + X[1:]
+        reset(X2)
+        B.filter(X2, 6, a, b, a0)
+        check(X2)
+        assert float(buf.view(M0, n0 + 8)[:, n0:].abs().max()) == 0.0   # padding untouched
+        B.destroy()
+    finally:
+        for c in ctxs:
+            c.destroy()
