@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps (median wall time reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side-arms", action="store_true",
+                    help="skip the binary64 / polished arm and the 20^3-cell p=7 arm")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
     ap.add_argument("--block", type=int, default=0,
                     help="wavefunction block of the filter (0: chosen by the autotuner)")
@@ -246,11 +248,17 @@ def host_cores():
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  Each step is one
+    bounded sample of the workload (the same sample as the GPU arm's
+    cpu_baseline: all columns in one block), extrapolated to one ChFSI
+    iteration by exact operation counts; the value is the mean over the
+    timed samples."""
     import dataclasses
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     s = workload(args.small)
+    s = dataclasses.replace(s, block=s.n_sub)
     times = []
     sample = ""
     for i in range(args.warmup + args.steps):
@@ -262,15 +270,222 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        # the GPU arm's configuration (its autotuner filters all columns in one
-        # block); the oracle's arithmetic does not depend on the blocking
-        "config": workload_config(dataclasses.replace(s, block=s.n_sub), "host memory"),
+        "data": "synthetic", "extrapolated": True,
+        "step_note": "each step is one bounded oracle sample extrapolated to one ChFSI iteration",
+        "config": workload_config(s, "host memory"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "extrapolated": True},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ rooflines
+# Binary64 rate of GB300 from its unit counts: 152 SMs x 2 FP64 FMA per clock
+# x 2 flops x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# MMA passes the cell kernel issues per algorithmic multiply-add, by precision.
+MMA_PASSES = {"bf16x3": 6, "mixed": 3, "tf32": 1}
+# Cell-matrix bytes per element each precision's cell kernel reads.
+CELL_MATRIX_BYTES = {"bf16x3": 6, "mixed": 8, "tf32": 4, "fp64": 8}
+CELL_KERNEL = {"bf16x3": "tc_cell_bf16_kernel", "mixed": "tc_cell_r_kernel",
+               "tf32": "tc_cell_r_kernel", "fp64": "cell_fp64_kernel"}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        pk["source"] = "of measured"
+        return pk
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "of fallback"}
+
+
+def dtype_peak(prec, peaks):
+    """Dense peak of the MMA's own operand type, sustained (the cell kernel is
+    timed inside a seconds-long step): BF16 measured; TF32 = measured BF16 x
+    the nominal 1.1 / 2.25 ratio; binary64 from unit counts and clock."""
+    bf = peaks.get("bf16_tflops_sustained", 1700.0)
+    if prec == "bf16x3":
+        return bf, "BF16 dense, measured sustained (MEASURED_PEAKS.json), %s" % peaks["source"]
+    if prec in ("mixed", "tf32"):
+        return bf * 1.1 / 2.25, ("TF32 dense = measured BF16 sustained x 1.1/2.25 nominal ratio, %s"
+                                 % peaks["source"])
+    return FP64_PEAK_TFLOPS, "binary64: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (unit counts and clock)"
+
+
+def rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks, cell_ms, cell_n, asm_ms, asm_n):
+    """Cell-kernel, assembly and filter-step rooflines from the per-launch event times.
+
+    Cell kernel: algorithmic work = N_c 2 n_e^2 flops per vector and
+    application (the dense cell products of Sec. 3.3.1), against the dense
+    peak of the MMA's operand type; the MMA passes the split-precision scheme
+    executes per algorithmic flop are reported beside it, not folded into the
+    peak.  Algorithmic bytes per launch = the cell matrices (N_c n_e^2 s_H) +
+    the block read (M nb s_X) + the dense cell blocks written (N_c n_e nb s_X).
+    Assembly: the cell blocks read, Y_in / Y_prev read and Y_out written
+    (3 M nb s_X) and the unknown -> cell-row table ((M + 1 + N_c n_e) 4 B).
+    Filter step: cell kernel + assembly against the fused-recurrence minimum
+    (3 s_X per unknown and vector + the cell matrices at s_H)."""
+    ne = (s.p + 1) ** 3
+    ncells = s.ncell ** 3
+    sx = 8 if prec == "fp64" else 4
+    s_h = CELL_MATRIX_BYTES[prec]
+    alg_flops = col_steps * ncells * 2 * ne * ne
+    peak, note = dtype_peak(prec, peaks)
+    achieved = alg_flops / (cell_ms / 1e3) / 1e12
+    kern = CELL_KERNEL[prec]
+    roof = {"bound": "alu" if prec == "fp64" else "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(kern, s, n) if prec != "fp64" else None,
+            "kernel": kern, "launches": int(cell_n), "avg_launch_ms": cell_ms / max(cell_n, 1),
+            "flops_per_launch": alg_flops / max(cell_n, 1),
+            "peak_note": note + "; achieved = algorithmic flops (N_c 2 n_e^2 per vector) / event time"}
+    if prec == "fp64":
+        return roof, None, None
+    cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * s_h
+                  + col_steps * M * sx + col_steps * ncells * ne * sx)
+    passes = MMA_PASSES[prec]
+    roof["bytes_per_launch"] = cell_bytes / max(cell_n, 1)
+    roof["hbm_gbs"] = cell_bytes / (cell_ms / 1e3) / 1e9
+    roof["executed_mma"] = {"passes_per_flop": passes, "tflops": passes * achieved,
+                            "frac_of_peak": passes * achieved / peak,
+                            "note": "MMA work the split-precision scheme issues (not the method's work)"}
+    asm_bytes = (col_steps * ncells * ne * sx + col_steps * 3 * M * sx
+                 + steps_blocks * nblocks * (M + 1 + ncells * ne) * 4)
+    if len(s.nl_centres):
+        asm_bytes += col_steps * M * sx          # the projector term read by the assembly
+    asm_roof = {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernel": "tc_assemble_kernel",
+                "launches": int(asm_n), "avg_launch_ms": asm_ms / max(asm_n, 1),
+                "bytes_per_launch": asm_bytes / max(asm_n, 1),
+                "traffic": profiled_traffic("tc_assemble_kernel", s, n),
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), %s" % peaks["source"]}
+    asm_roof["frac"] = asm_roof["achieved"] / peaks["hbm_gbs"]
+    step_bytes = col_steps * 3 * sx * M + steps_blocks * nblocks * ncells * ne * ne * s_h
+    step_roof = {"bound": "hbm", "achieved": step_bytes / ((cell_ms + asm_ms) / 1e3) / 1e9,
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernels": kern + " + tc_assemble_kernel",
+                 "note": "filter degree step against the fused-recurrence minimum "
+                         "(3 s_X per unknown and vector + the cell matrices at %d B)" % s_h}
+    step_roof["frac"] = step_roof["achieved"] / peaks["hbm_gbs"]
+    return roof, asm_roof, step_roof
+
+
+# ------------------------------------------------------------------ side arms
+def ev_seconds(stream, fn):
+    """Device seconds of fn() on the stream (CUDA events, synchronised)."""
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def fp64_polish_arm(ctx, s, X, b, D_mixed, stream, mixed_s_per_iter):
+    """Binary64 ChFSI iteration on the same workload and GPU, which is also
+    the binary64 polish of the mixed block (chfsi_solve_polish's step 3):
+    the benchmark's binary32 block (after its mixed iterations) is copied to
+    binary64, one binary64 iteration of degree 1 grows the scratch, then one
+    timed binary64 iteration {filter of the workload's degree, CholGS, RR}.
+    Reports the binary64 s/iter, the polished solve's s/iter over the
+    workload's iteration count, and the generalized residuals of the wanted
+    pairs before and after the polish."""
+    import torch
+    n, k = s.n_sub, s.n_want
+    X64 = X.double()
+    res_mixed = ctx.residuals(X64[:, :k], D_mixed[:k], prec="fp64")[1]
+    D = D_mixed
+
+    def iteration(deg, D):
+        ctx.filter(X64, deg, float(D[-1]), b, float(D[0]), prec="fp64")
+        ctx.cholgs(X64, prec="fp64")
+        return ctx.rayleigh_ritz(X64, prec="fp64")
+
+    D = iteration(1, D)                     # grows the binary64 scratch
+    out = {}
+    t0 = time.perf_counter()
+    t = ev_seconds(stream, lambda: out.update(D=iteration(s.degree, D)))
+    wall = time.perf_counter() - t0
+    D = out["D"]
+    res_pol = ctx.residuals(X64[:, :k], D[:k], prec="fp64")[1]
+    res_pol32 = ctx.residuals(X64[:, :k].float().double(), D[:k], prec="fp64")[1]
+    del X64
+    torch.cuda.empty_cache()
+    return {
+        "fp64_s_per_iter": t, "fp64_wall_s": wall,
+        "fp64_vs_mixed_ratio": t / mixed_s_per_iter,
+        "polished_s_per_iter": (s.iters * mixed_s_per_iter + t) / s.iters,
+        "polished_note": "%d mixed iterations + 1 binary64 polish iteration of degree %d, per "
+                         "iteration of the workload" % (s.iters, s.degree),
+        "max_gres_mixed": float(np.max(res_mixed)), "max_gres_polished": float(np.max(res_pol)),
+        "max_gres_polished_stored_binary32": float(np.max(res_pol32)),
+        "max_abs_eval_change_mixed_to_polished": float(np.abs(D[:k] - D_mixed[:k]).max()),
+        "n_checked": k,
+    }
+
+
+def c3_arm(stream, steps=1):
+    """The largest single-GPU workload (20^3 cells, p = 7, 1,000 projector
+    sites, N = 3,000 + 300, block 1,100, degree 50): one warm-up and `steps`
+    timed mixed (BF16x3) ChFSI iterations, with the cell-kernel roofline."""
+    import torch
+    from paper_1903_10959_gb300 import Context
+    from paper_1903_10959_gb300 import workloads as W
+    s = W.cubic_sites_nonlocal(block=1100)
+    t0 = time.perf_counter()
+    ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
+    ctx.set_potential_gaussians(s.centres, s.depths, s.widths)
+    ctx.set_projectors(s.nl_centres, s.nl_h, s.nl_sigma, s.nl_rcut)
+    ctx.build()
+    ctx.set_blocking(s.block, 1)
+    n, M = s.n_sub, ctx.ndofs
+    b = ctx.bounds(20, s.seed)
+    X = torch.empty((M, n), dtype=torch.float32, device="cuda")
+    ctx.fill_uniform(X, s.seed, prec="bf16x3")
+    ctx.cholgs(X, prec="bf16x3")
+    state = {"D": ctx.rayleigh_ritz(X, prec="bf16x3")}
+    setup_s = time.perf_counter() - t0
+    phase = np.zeros(3)
+
+    def step():
+        D = state["D"]
+        ctx.filter(X, s.degree, float(D[-1]), b, float(D[0]), prec="bf16x3")
+        phase[0] += ctx.last_timings()[0]
+        ctx.cholgs(X, prec="bf16x3")
+        phase[1] += ctx.last_timings()[1]
+        state["D"] = ctx.rayleigh_ritz(X, prec="bf16x3")
+        phase[2] += ctx.last_timings()[2]
+
+    step()
+    phase[:] = 0
+    ctx.set_kernel_timing(True)
+    ctx.kernel_timings()
+
+    def timed():
+        for _ in range(steps):
+            step()
+    t = ev_seconds(stream, timed) / steps
+    kt = [float(v) for v in ctx.kernel_timings()]
+    ctx.set_kernel_timing(False)
+    nblocks = -(-n // s.block)
+    steps_blocks = steps * (s.degree + 1)
+    roof, asm_roof, _ = rooflines("bf16x3", s, n, M, load_peaks(), steps_blocks * n, steps_blocks,
+                                  nblocks, kt[0], kt[2], kt[1], kt[3])
+    ctx.destroy()
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "nonlocal-periodic 20^3 cells p=7 L=40, %d unknowns, 1000 wells + 1000 "
+                        "sites x 4 projectors, N=%d (+%d buffer), block %d, degree %d"
+                        % (M, s.n_want, s.n_buffer, s.block, s.degree),
+            "s_per_iter": t, "steps": steps, "warmup": 1, "setup_s": setup_s,
+            "phases_ms_per_step": {"filter": phase[0] / steps, "cholgs": phase[1] / steps,
+                                   "rr": phase[2] / steps},
+            "projector_kernels_ms_per_step": kt[4] / steps,
+            "roofline": roof, "roofline_assembly": asm_roof, "precision": "bf16x3"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -350,15 +565,6 @@ def run_ours(args):
     t, value = job_seconds_per_iter(t, args.steps, dist, "cuda")
 
     # Rooflines (per-launch CUDA events on the context stream).
-    # Cell-product kernel, algorithmic work per launch (one block of nb
-    # columns): 2 n_e^2 flops per cell and vector; bytes = the split cell
-    # matrices (N_c n_e^2 x s_H: 8 B for TF32 hi + lo, 6 B for three bf16
-    # terms) + the block of Y (M nb s_X) + the dense cell blocks written
-    # (N_c n_e nb s_X).  3xTF32 takes three TF32 MMA passes per flop (peak =
-    # TF32 peak / 3), BF16x3 six BF16 passes (peak = BF16 peak / 6).
-    # Assembly kernel, bytes per launch: the cell blocks read (N_c n_e nb s_X),
-    # Y_in, Y_prev read and Y_out written (3 M nb s_X) and the unknown -> cell
-    # row table ((M + 1 + N_c n_e) x 4 B).
     nblocks = -(-n // s.block)
     ne = (s.p + 1) ** 3
     ncells = s.ncell ** 3
@@ -368,57 +574,11 @@ def run_ours(args):
     # application, each over one column block
     steps_blocks = args.steps * (s.degree + 1)
     col_steps = steps_blocks * n                  # (vector, application) units
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    peaks = load_peaks()
     cell_ms, asm_ms, cell_n, asm_n, nl_ms, nl_n = [float(v) for v in kt]
-    alg_flops = col_steps * ncells * 2 * ne * ne          # dense cell products, one per vector
-    tf32_peak = peaks.get("bf16_tflops_sustained", 1672.5) * 1.1 / 2.25
-    if prec == "fp64":
-        roof = {"bound": "alu", "achieved": alg_flops / (cell_ms / 1e3) / 1e12, "peak": 1.25,
-                "unit": "TFLOP/s", "kernel": "cell_fp64_kernel", "launches": int(cell_n),
-                "avg_launch_ms": cell_ms / max(cell_n, 1),
-                "peak_note": "nominal binary64 rate of GB300 (1.25 TFLOP/s)"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
-        step_roof = asm_roof = None
-    else:
-        passes = {"mixed": 3, "tf32": 1, "bf16x3": 6}[prec]
-        s_h = {"mixed": 8, "tf32": 4, "bf16x3": 6}[prec]     # cell-matrix bytes per element read
-        cell_bytes = (steps_blocks * nblocks * ncells * ne * ne * s_h
-                      + col_steps * M * sx + col_steps * ncells * ne * sx)
-        bf16_peak = peaks.get("bf16_tflops_sustained", 1672.5)
-        tpeak = (bf16_peak if prec == "bf16x3" else tf32_peak) / passes
-        achieved = alg_flops / (cell_ms / 1e3) / 1e12
-        cell_kernel = "tc_cell_bf16_kernel" if prec == "bf16x3" else "tc_cell_r_kernel"
-        traffic = profiled_traffic(cell_kernel, s, n) if prec in ("mixed", "bf16x3") else None
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
-                "frac": achieved / tpeak, "traffic": traffic, "kernel": cell_kernel,
-                "launches": int(cell_n), "avg_launch_ms": cell_ms / cell_n,
-                "flops_per_launch": alg_flops / cell_n, "bytes_per_launch": cell_bytes / cell_n,
-                "hbm_gbs": cell_bytes / (cell_ms / 1e3) / 1e9,
-                "peak_note": ("BF16 dense peak (measured sustained, MEASURED_PEAKS.json) / %d MMA "
-                              "passes per flop; of measured" % passes) if prec == "bf16x3" else
-                             ("TF32 dense peak = measured bf16 sustained (MEASURED_PEAKS.json) x "
-                              "1.1/2.25 nominal ratio, / %d MMA passes per flop; of measured" % passes)}
-        asm_bytes = (col_steps * ncells * ne * sx + col_steps * 3 * M * sx
-                     + steps_blocks * nblocks * (M + 1 + ncells * ne) * 4)
-        if len(s.nl_centres):
-            asm_bytes += col_steps * M * sx          # the projector term read by the assembly
-        asm_roof = {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9,
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernel": "tc_assemble_kernel",
-                    "launches": int(asm_n), "avg_launch_ms": asm_ms / max(asm_n, 1),
-                    "bytes_per_launch": asm_bytes / max(asm_n, 1),
-                    "traffic": profiled_traffic("tc_assemble_kernel", s, n)
-                    if prec in ("mixed", "bf16x3") else None,
-                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"}
-        asm_roof["frac"] = asm_roof["achieved"] / peaks["hbm_gbs"]
-        step_bytes = col_steps * 3 * sx * M + steps_blocks * nblocks * ncells * ne * ne * 8
-        step_roof = {"bound": "hbm", "achieved": step_bytes / ((cell_ms + asm_ms) / 1e3) / 1e9,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "kernels": "tc_cell_r_kernel + tc_assemble_kernel",
-                     "note": "filter degree step against the fused-recurrence minimum "
-                             "(3 s_X per unknown and vector + the cell matrices)"}
-        step_roof["frac"] = step_roof["achieved"] / peaks["hbm_gbs"]
+    roof, asm_roof, step_roof = rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks,
+                                          cell_ms, cell_n, asm_ms, asm_n)
+    alg_flops = col_steps * ncells * 2 * ne * ne
     phase_timed = phase.copy()
     # end to end through host buffers: H2D of X, one iteration, D2H of X and the Ritz values
     e2e = None
@@ -490,13 +650,24 @@ def run_ours(args):
                                                    "precision; peak from unit counts and clock"}}
         del Xfr, rho
 
+    # side arms (N = 1 only): the binary64 iteration / polish on this workload,
+    # then the 20^3-cell p = 7 workload with projectors
+    side = {}
+    if world == 1 and not args.no_side_arms and args.workload == "chfsi" and prec != "fp64" \
+            and not args.small:
+        side["fp64_and_polish"] = fp64_polish_arm(ctx, s, X, b, state["D"], stream, value)
+        ctx.destroy()
+        del X
+        torch.cuda.empty_cache()
+        side["c3"] = c3_arm(stream)
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        tcpu, sample, parts = oracle_sample_seconds(s)
+        # the same sample as the reference arm: all columns in one block
+        tcpu, sample, parts = oracle_sample_seconds(dataclasses.replace(s, block=s.n_sub))
         cpu = {"value": tcpu, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": sample, "phases_s": parts}
+               "sample": sample, "phases_s": parts, "extrapolated": True}
     line = {
         "metric": METRIC if args.workload == "chfsi" else
         "ChFSI s/iter (filter + CholGS + RR), %s %d^3 cells p=%d" % (s.name.rsplit("-", 2)[0],
@@ -512,17 +683,17 @@ def run_ours(args):
                                "cholgs": phase_timed[1] / args.steps,
                                "rr": phase_timed[2] / args.steps},
         "filter_tflops": {"algorithmic_per_filter_time": alg_flops / filter_s / 1e12,
-                          "cell_kernel_executed_tensor": {"mixed": 3, "tf32": 1, "bf16x3": 6}.get(prec, 1) * alg_flops
-                          / (cell_ms / 1e3) / 1e12 if prec != "fp64" else None,
-                          "tf32_peak_derived": tf32_peak if prec != "fp64" else None},
+                          "algorithmic_per_cell_kernel_time": alg_flops / (cell_ms / 1e3) / 1e12},
         "roofline": roof, "roofline_assembly": asm_roof, "roofline_filter_step": step_roof,
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "autotune": tuned, "spectrum_split_and_density": split,
         "projector_kernels_ms_per_step": nl_ms / args.steps if nl_n else None,
         "clocks": clk, "precision": prec, "parallelism": "replicas" if world > 1 else "single",
     }
+    line.update(side)
     print(json.dumps(line), flush=True)
-    ctx.destroy()
+    if not side:
+        ctx.destroy()
 
 
 # ------------------------------------------------------------------ serving
@@ -692,7 +863,8 @@ def run_batch(args):
     t_solve = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02), 1)
     t_solve_mixed = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02, orth_prec="mixed"), 1)
     clk = clocks.stop()
-    tf32_peak = 1672.5 * 1.1 / 2.25
+    tf32_peak, tf32_note = dtype_peak("mixed", load_peaks())
+    achieved = flops / t_batch / 1e12
     line = {
         "metric": "batched Chebyshev filter aggregate TFLOP/s (64 Dirichlet systems, p=5)",
         "value": flops / t_batch / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
@@ -706,7 +878,11 @@ def run_batch(args):
                                                                  for c, t in zip(cands, cand_ms)}},
         "filter_s_batched": t_batch, "filter_s_sequential": t_seq,
         "speedup_vs_sequential": t_seq / t_batch,
-        "tensor_frac_of_3xtf32_peak": flops / t_batch / 1e12 / (tf32_peak / 3),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / tf32_peak, "traffic": None,
+                     "kernel": "tc_cell_r_kernel<64, true> (multi-system)",
+                     "peak_note": tf32_note + "; algorithmic flops N_c 2 n_e^2 per vector",
+                     "executed_mma": {"passes_per_flop": 3, "frac_of_peak": 3 * achieved / tf32_peak}},
         "batched_chfsi_iteration_s": t_solve,
         "batched_chfsi_iteration_s_tf32x3_orth": t_solve_mixed,
         "clocks": clk,

@@ -242,6 +242,31 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
                          double b, double tol, int n_check, chfsi_precision prec,
                          double* evals_host, int* iters_done);
 
+/* Mixed-precision ChFSI followed by a binary64 polish (the residual side of
+ * the mixed-precision strategy, Secs. 3.4.2 and 3.5.2: binary32 arithmetic
+ * where the subspace is still converging, binary64 where accuracy is set).
+ * The binary32 filter's storage and FP32 accumulation leave the subspace with
+ * a generalized residual near 1e-6; a few binary64 iterations from that
+ * subspace remove it.  Steps:
+ *  1. chfsi_solve on X (binary32, M x n) in precision prec (a mixed one),
+ *     with iters, degree, b, tol, n_check as there, except that its last
+ *     Rayleigh-Ritz stays in the tensor-core arithmetic;
+ *  2. the binary64 copy X64 <- X (X64: caller-owned device block, M x n,
+ *     leading dimension ldx64 >= n, not overlapping X; NULL: a library-owned
+ *     staging block of M n 8 bytes);
+ *  3. polish_iters binary64 iterations {filter of degree polish_degree with
+ *     a = max Ritz, b, a0 = min Ritz of the previous Rayleigh-Ritz; CholGS;
+ *     Rayleigh-Ritz} on X64;
+ *  4. X <- the binary32 rounding of X64.
+ * evals_host[n] receives the binary64 Ritz values of the last polish
+ * iteration, iters_done (may be NULL) the mixed iterations run.  A polish
+ * degree near the solve's degree damps the binary32 noise by the same factor
+ * as one solve iteration; much lower degrees leave most of it.  Synchronises. */
+chfsi_status chfsi_solve_polish(chfsi_ctx* ctx, float* X, int64_t ldx, int n, int iters, int degree,
+                                double b, double tol, int n_check, chfsi_precision prec,
+                                int polish_iters, int polish_degree, double* X64, int64_t ldx64,
+                                double* evals_host, int* iters_done);
+
 /* Spectrum-splitting Rayleigh-Ritz (Algorithm rr, Sec. 3.5): H^ = X^T H~ X for
  * the CholGS output X (M x n, not modified), its n_fr largest eigenpairs in
  * binary64 (cuSOLVER syevdx, index range n-n_fr+1..n), and the partial

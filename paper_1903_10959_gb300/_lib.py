@@ -97,6 +97,9 @@ _SIGS = {
     "chfsi_bounds": (C.c_int, [_vp, C.c_int, C.c_uint64, _dp]),
     "chfsi_solve": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                               C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]),
+    "chfsi_solve_polish": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double,
+                                     C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _i64,
+                                     _dp, C.POINTER(C.c_int)]),
     "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
     "chfsi_rayleigh_ritz_split": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, _vp, _i64, C.c_int, _dp]),
     "chfsi_fermi_level": (C.c_int, [C.c_int, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp]),
@@ -339,6 +342,26 @@ class Context:
         done = C.c_int(0)
         self._check(self._lib.chfsi_solve(self._h, px, ldx, n, int(iters), int(degree), float(b),
                                           float(tol), int(n_check), pr, _ptr(ev), C.byref(done)))
+        return ev, done.value
+
+    def solve_polish(self, X, iters, degree, b, polish_iters=1, polish_degree=None, X64=None,
+                     tol=0.0, n_check=0, prec="bf16x3"):
+        """Mixed-precision solve on the binary32 block X, then ``polish_iters``
+        binary64 iterations (degree ``polish_degree``, default ``degree``) on a
+        binary64 copy (``X64`` when given, a CUDA float64 tensor of X's shape);
+        X receives the polished block rounded to binary32."""
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        p64, ld64 = None, 0
+        if X64 is not None:
+            p64, ld64, n64 = _dev(X64, FP64)
+            if n64 != n:
+                raise ValueError("X64 needs %d columns" % n)
+        ev = np.empty(n)
+        done = C.c_int(0)
+        self._check(self._lib.chfsi_solve_polish(
+            self._h, px, ldx, n, int(iters), int(degree), float(b), float(tol), int(n_check), pr,
+            int(polish_iters), int(polish_degree or degree), p64, ld64, _ptr(ev), C.byref(done)))
         return ev, done.value
 
     def rayleigh_ritz_split(self, X, Xfr, prec="fp64") -> np.ndarray:

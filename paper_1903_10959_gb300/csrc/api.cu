@@ -550,6 +550,62 @@ chfsi_status residual_impl(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, ch
   return CHFSI_OK;
 }
 
+// The ChFSI loop of chfsi_solve (step 7 of Algorithm scf, repeated): CholGS +
+// RR on the start block, then `iters` x {filter, CholGS, RR}, with the
+// adaptive early stop on the binary64 generalized residual.  final_fp64_rr:
+// for the mixed precisions, evaluate the last RR with binary64 cell products
+// (second-order eigenvalue error); a caller that refines the block afterwards
+// passes false.  D receives the Ritz values, *it_out the iterations run.
+chfsi_status solve_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters, int degree, double b,
+                        double tol, int n_check, chfsi_precision prec, bool final_fp64_rr,
+                        std::vector<double>& D, int* it_out) {
+  chfsi_status st;
+  if (n_check <= 0 || n_check > n) n_check = n;
+  std::vector<double> res(n);
+  const bool fp64_last = final_fp64_rr && is_mixed(prec);
+  tic(ctx);
+  if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
+  toc(ctx, 1);
+  tic(ctx);
+  if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), iters == 0 && fp64_last)) != CHFSI_OK) return st;
+  toc(ctx, 2);
+  int it = 0;
+  for (; it < iters; ++it) {
+    double a = D[n - 1], a0 = D[0];
+    if (!(a < b)) return fail(ctx, CHFSI_ERR_ARG, "upper bound b must exceed the largest Ritz value");
+    if (!(a0 < a)) a0 = a - 1e-3 * std::max(1.0, std::fabs(a));
+    tic(ctx);
+    if ((st = filter_impl(ctx, X, ldx, n, degree, a, b, a0, prec)) != CHFSI_OK) return st;
+    toc(ctx, 0);
+    tic(ctx);
+    if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
+    toc(ctx, 1);
+    tic(ctx);
+    const bool last = (it + 1 == iters);
+    if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), last && fp64_last)) != CHFSI_OK) return st;
+    toc(ctx, 2);
+    if (tol > 0.0) {
+      tic(ctx);
+      if ((st = residual_impl(ctx, X, ldx, n_check, prec, D.data(), nullptr, res.data(),
+                              is_mixed(prec))) != CHFSI_OK)
+        return st;
+      toc(ctx, 3);
+      double mx = *std::max_element(res.begin(), res.begin() + n_check);
+      if (mx < tol) {
+        ++it;
+        if (!last && fp64_last) {   // stopping early: redo the last RR with binary64 products
+          tic(ctx);
+          if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), true)) != CHFSI_OK) return st;
+          toc(ctx, 2);
+        }
+        break;
+      }
+    }
+  }
+  *it_out = it;
+  return CHFSI_OK;
+}
+
 }  // namespace
 
 // ================================================== apply without device allocation
@@ -642,7 +698,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_node_ptr, m.node_ptr.size() * 4);
   release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
-                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db})
+                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol})
     dfree(ctx, b->ptr, b->bytes);
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)
@@ -1164,49 +1220,71 @@ chfsi_status chfsi_solve(chfsi_ctx* ctx, void* X, int64_t ldx, int n, int iters,
   chfsi_status st = check_x(ctx, X, ldx, n, prec);
   if (st != CHFSI_OK) return st;
   if (n < 1 || iters < 0 || degree < 1 || !evals_host) return fail(ctx, CHFSI_ERR_ARG, "bad solve arguments");
-  if (n_check <= 0 || n_check > n) n_check = n;
   std::fill(ctx->times, ctx->times + 4, 0.0);
-  std::vector<double> D(n), res(n);
-  tic(ctx);
-  if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
-  toc(ctx, 1);
-  tic(ctx);
-  if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), iters == 0)) != CHFSI_OK) return st;
-  toc(ctx, 2);
+  std::vector<double> D(n);
   int it = 0;
-  for (; it < iters; ++it) {
+  if ((st = solve_impl(ctx, X, ldx, n, iters, degree, b, tol, n_check, prec, true, D, &it)) != CHFSI_OK)
+    return st;
+  if ((st = check_device_status(ctx, prec)) != CHFSI_OK) return st;
+  std::memcpy(evals_host, D.data(), (size_t)n * 8);
+  if (iters_done) *iters_done = it;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_solve_polish(chfsi_ctx* ctx, float* X, int64_t ldx, int n, int iters, int degree,
+                                double b, double tol, int n_check, chfsi_precision prec,
+                                int polish_iters, int polish_degree, double* X64, int64_t ldx64,
+                                double* evals_host, int* iters_done) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (!is_mixed(prec)) return fail(ctx, CHFSI_ERR_ARG, "the polish follows a mixed-precision solve");
+  if (n < 1 || iters < 0 || degree < 1 || polish_iters < 1 || polish_degree < 1 || !evals_host ||
+      (X64 && ldx64 < n))
+    return fail(ctx, CHFSI_ERR_ARG, "bad polished-solve arguments");
+  const HostMesh& m = ctx->mesh;
+  if (X64) {   // the binary64 block must not overlap the binary32 one
+    const char* x0 = (const char*)X;
+    const char* x1 = x0 + ((m.ndofs - 1) * ldx + n) * 4;
+    const char* y0 = (const char*)X64;
+    const char* y1 = y0 + ((m.ndofs - 1) * ldx64 + n) * 8;
+    if (y0 < x1 && x0 < y1) return fail(ctx, CHFSI_ERR_ARG, "X64 overlaps X");
+  }
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  std::vector<double> D(n);
+  int it = 0;
+  // 1. the mixed-precision iterations; their last Rayleigh-Ritz stays in the
+  //    tensor-core arithmetic (the polish recomputes the Ritz pairs)
+  if ((st = solve_impl(ctx, X, ldx, n, iters, degree, b, tol, n_check, prec, false, D, &it)) != CHFSI_OK)
+    return st;
+  if ((st = check_device_status(ctx, prec)) != CHFSI_OK) return st;
+  // 2. binary64 copy of the block (caller's X64, else library staging)
+  double* P = X64;
+  int64_t ldp = ldx64;
+  if (!P) {
+    if ((st = grow(ctx, ctx->pol, (size_t)m.ndofs * n * 8)) != CHFSI_OK) return st;
+    P = (double*)ctx->pol.ptr;
+    ldp = n;
+  }
+  CK(launch_copy_cols(X, ldx, P, ldp, m.ndofs, n, 0, 1, ctx->stream));
+  // 3. binary64 ChFSI iterations from the mixed subspace (bounds from its last RR)
+  for (int k = 0; k < polish_iters; ++k) {
     double a = D[n - 1], a0 = D[0];
     if (!(a < b)) return fail(ctx, CHFSI_ERR_ARG, "upper bound b must exceed the largest Ritz value");
     if (!(a0 < a)) a0 = a - 1e-3 * std::max(1.0, std::fabs(a));
     tic(ctx);
-    if ((st = filter_impl(ctx, X, ldx, n, degree, a, b, a0, prec)) != CHFSI_OK) return st;
+    if ((st = filter_impl(ctx, P, ldp, n, polish_degree, a, b, a0, CHFSI_FP64)) != CHFSI_OK) return st;
     toc(ctx, 0);
     tic(ctx);
-    if ((st = cholgs_impl(ctx, X, ldx, n, prec)) != CHFSI_OK) return st;
+    if ((st = cholgs_impl(ctx, P, ldp, n, CHFSI_FP64)) != CHFSI_OK) return st;
     toc(ctx, 1);
     tic(ctx);
-    const bool last = (it + 1 == iters);
-    if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), last)) != CHFSI_OK) return st;
+    if ((st = rr_impl(ctx, P, ldp, n, CHFSI_FP64, D.data())) != CHFSI_OK) return st;
     toc(ctx, 2);
-    if (tol > 0.0) {
-      tic(ctx);
-      if ((st = residual_impl(ctx, X, ldx, n_check, prec, D.data(), nullptr, res.data(),
-                              is_mixed(prec))) != CHFSI_OK)
-        return st;
-      toc(ctx, 3);
-      double mx = *std::max_element(res.begin(), res.begin() + n_check);
-      if (mx < tol) {
-        ++it;
-        if (!last && is_mixed(prec)) {   // stopping early: redo the last RR with binary64 products
-          tic(ctx);
-          if ((st = rr_impl(ctx, X, ldx, n, prec, D.data(), true)) != CHFSI_OK) return st;
-          toc(ctx, 2);
-        }
-        break;
-      }
-    }
   }
-  if ((st = check_device_status(ctx, prec)) != CHFSI_OK) return st;
+  // 4. the polished block rounded back into the caller's binary32 block
+  CK(launch_copy_cols(P, ldp, X, ldx, m.ndofs, n, 1, 0, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   std::memcpy(evals_host, D.data(), (size_t)n * 8);
   if (iters_done) *iters_done = it;
   return CHFSI_OK;

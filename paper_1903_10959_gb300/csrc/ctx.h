@@ -43,6 +43,7 @@ struct chfsi_ctx {
   float* d_dof_c32 = nullptr;
   // grown scratch
   chfsi::DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
+  chfsi::DevBuf pol;               // binary64 staging block of the polish
   chfsi::DevBuf Db;                // density tables: M^{-1/2}, basis at Gauss points, weights
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
