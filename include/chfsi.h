@@ -328,6 +328,44 @@ chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out6);
  * monotonic counter for accounting, e.g. launches per ChFSI iteration). */
 int64_t      chfsi_kernel_launches(void);
 
+/* ---------------------------------------------------------- domain decomposition
+ * Partition of the mesh's cells over nranks ranks (the paper's primary level
+ * of parallelism, Sec. 3.7: subdomains of the FE mesh on separate tasks; since
+ * each basis function lives on the cells sharing its node, only unknowns on
+ * subdomain boundaries are communicated).  Host-only (no device, no context):
+ * every rank calls it for itself and all ranks agree on every list.
+ * The ranks form a grid px x py x pz = nranks (the factorisation with the
+ * smallest interface area, each factor at most the cells on its axis); rank
+ * ix + px (iy + py iz) owns the cell block [ix n_x / px, (ix + 1) n_x / px) x ...
+ * For rank `rank`:
+ *  cells[ncells]        its cells (global index, cells x fastest), ascending;
+ *  l2g[nlocal]          the global unknowns its cells touch, ascending: the
+ *                       local numbering of its rows of X;
+ *  owner[nlocal]        per local unknown the lowest rank whose cells touch it
+ *                       (the rank that counts the row in sums over unknowns,
+ *                       e.g. the overlap S = X^T X, Algorithm CholGS step 1);
+ *  neighbors[nneighbors] the other ranks sharing unknowns with it, ascending;
+ *  halo_ptr[nneighbors + 1], halo[nhalo]: for neighbor k, the local indices
+ *                       halo[halo_ptr[k] .. halo_ptr[k+1]) of the shared
+ *                       unknowns, in ascending global order (the same order on
+ *                       both ranks, so exchanged rows line up).
+ * A cell apply over the rank's cells gives partial sums on its local rows;
+ * adding the partial sums that each neighbor sends for the shared rows gives
+ * rows of H~ X (the halo sum).  Arrays are caller-owned host memory sized by
+ * chfsi_partition_sizes.  CHFSI_ERR_ARG for an invalid mesh, rank outside
+ * [0, nranks), or no factorisation fitting the cells. */
+typedef struct {
+  int64_t ncells, nlocal, nhalo;
+  int nneighbors;
+  int grid[3];
+} chfsi_partition_info;
+
+chfsi_status chfsi_partition_sizes(const chfsi_mesh_desc* desc, int nranks, int rank,
+                                   chfsi_partition_info* out);
+chfsi_status chfsi_partition_fill(const chfsi_mesh_desc* desc, int nranks, int rank, int32_t* cells,
+                                  int32_t* l2g, int32_t* owner, int32_t* neighbors,
+                                  int64_t* halo_ptr, int32_t* halo);
+
 /* ---------------------------------------------------------------- batching
  * Many independent systems of the same FE degree (typically small and of
  * uneven size) filtered together on the tensor cores.  Per Chebyshev degree

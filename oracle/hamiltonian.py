@@ -95,6 +95,21 @@ class Problem:
         s = self.minv_sqrt if X.ndim == 1 else self.minv_sqrt[:, None]
         return s * self.apply_H(s * X)
 
+    def apply_Htilde_cells(self, cells, X: np.ndarray) -> np.ndarray:
+        """Local part of H~ X over a subset of cells (the cell loop one task of a
+        domain decomposition runs on its own cells, Sec. 3.7):
+        M^{-1/2} sum_{e in cells} P_e^T H_e P_e M^{-1/2} X.  Summed over a
+        partition of the cells it gives the local part of apply_Htilde."""
+        s = self.minv_sqrt[:, None]
+        Xs = s * np.asarray(X, dtype=np.float64)
+        out = np.zeros_like(Xs)
+        for e in cells:
+            d = self.mesh.cell_dofs(int(e))
+            ok = d >= 0
+            He = self.cell_hamiltonian(int(e))[np.ix_(ok, ok)]
+            out[d[ok]] += He @ Xs[d[ok]]
+        return s * out
+
     def apply_Htilde_rows(self, rows, X: np.ndarray) -> np.ndarray:
         """Rows ``rows`` of H~ X, summing only the cells that contain them (for
         sampled checks on meshes too large for a full oracle apply)."""

@@ -48,6 +48,11 @@ def _axes(periodic):
 MAX_SOLVES = 16
 
 
+class PartitionInfo(C.Structure):
+    _fields_ = [("ncells", C.c_int64), ("nlocal", C.c_int64), ("nhalo", C.c_int64),
+                ("nneighbors", C.c_int), ("grid", C.c_int * 3)]
+
+
 class Request(C.Structure):
     _fields_ = [("mesh", MeshDesc), ("n", C.c_int), ("nwells", C.c_int),
                 ("xyz", C.POINTER(C.c_double)), ("depth", C.POINTER(C.c_double)),
@@ -123,6 +128,10 @@ _SIGS = {
     "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_partition_sizes": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int,
+                                        C.POINTER(PartitionInfo)]),
+    "chfsi_partition_fill": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int, _vp, _vp, _vp, _vp,
+                                       _vp, _vp]),
     "chfsi_kernel_timings": (C.c_int, [_vp, _dp]),
 }
 
@@ -584,3 +593,35 @@ def fermi_level(evals, n_oc, n_electrons, kT):
     if st != 0:
         raise ChfsiError(st, "chfsi_fermi_level: the states cannot hold that many electrons")
     return mu.value, occ
+
+
+def partition(ncell, length, p, periodic, nranks, rank):
+    """Domain decomposition of the mesh for one rank (chfsi_partition_sizes /
+    chfsi_partition_fill): dict with cells, l2g, owner, neighbors, halo (list
+    of local-index arrays, one per neighbor) and the rank grid."""
+    lib = load()
+    if np.isscalar(ncell):
+        ncell = (ncell,) * 3
+    if np.isscalar(length):
+        length = (float(length),) * 3
+    d = MeshDesc((C.c_int * 3)(*ncell), (C.c_double * 3)(*length), int(p),
+                 (C.c_int * 3)(*_axes(periodic)), 0)
+    info = PartitionInfo()
+    st = lib.chfsi_partition_sizes(C.byref(d), int(nranks), int(rank), C.byref(info))
+    if st != 0:
+        raise ChfsiError(st, "chfsi_partition_sizes: no partition of this mesh over %d ranks" % nranks)
+    cells = np.empty(info.ncells, np.int32)
+    l2g = np.empty(info.nlocal, np.int32)
+    owner = np.empty(info.nlocal, np.int32)
+    nbr = np.empty(max(info.nneighbors, 1), np.int32)
+    hptr = np.empty(info.nneighbors + 1, np.int64)
+    halo = np.empty(max(info.nhalo, 1), np.int32)
+    vp = lambda a: a.ctypes.data_as(_vp)  # noqa: E731
+    st = lib.chfsi_partition_fill(C.byref(d), int(nranks), int(rank), vp(cells), vp(l2g), vp(owner),
+                                  vp(nbr), vp(hptr), vp(halo))
+    if st != 0:
+        raise ChfsiError(st, "chfsi_partition_fill failed")
+    k = info.nneighbors
+    return {"cells": cells, "l2g": l2g, "owner": owner, "neighbors": nbr[:k].copy(),
+            "halo": [halo[hptr[i]:hptr[i + 1]].copy() for i in range(k)],
+            "grid": tuple(info.grid)}
