@@ -580,34 +580,41 @@ def run_ours(args):
                                           cell_ms, cell_n, asm_ms, asm_n)
     alg_flops = col_steps * ncells * 2 * ne * ne
     phase_timed = phase.copy()
-    # end to end through host buffers: H2D of X, one iteration, D2H of X and the Ritz values
+    # end to end through host buffers, inside the library (chfsi_step_host):
+    # H2D of the pinned host block, one iteration, D2H of the block and the
+    # Ritz values; wall time of the C-ABI call per step
     e2e = None
     if args.e2e_steps > 0:
         Xh = torch.empty((M, n), dtype=dt, pin_memory=True)
         Xh.copy_(X)
         torch.cuda.synchronize()
-        evs, walls = [], []
-        for _ in range(args.e2e_steps):
+
+        def host_step(mode):
+            D = state["D"]
             t0 = time.perf_counter()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            X.copy_(Xh, non_blocking=True)
-            ev[1].record(stream)
-            step()
-            ev[2].record(stream)
-            Xh.copy_(X, non_blocking=True)
-            ev[3].record(stream)
-            torch.cuda.synchronize()
-            walls.append(time.perf_counter() - t0)
-            evs.append(ev)
-        te = float(np.median(walls))
+            ev, ms = ctx.step_host(Xh, X, s.degree, float(D[-1]), b, float(D[0]), prec=prec,
+                                   copy_mode=mode)
+            wall = time.perf_counter() - t0
+            state["D"] = ev
+            return wall, ms
+
+        walls, dms = [], []
+        for _ in range(args.e2e_steps):
+            w, ms = host_step(0)
+            walls.append(w)
+            dms.append(ms)
+        wce, msce = host_step(1)                     # the same call with the copy engines
         nbytes = M * n * X.element_size()
-        e2e = {"value": te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        med = np.median(np.array(dms), axis=0)
+        e2e = {"value": float(np.median(walls)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes + n * 8,
-               "device_ms": {"h2d": float(np.median([e[0].elapsed_time(e[1]) for e in evs])),
-                             "step": float(np.median([e[1].elapsed_time(e[2]) for e in evs])),
-                             "d2h": float(np.median([e[2].elapsed_time(e[3]) for e in evs]))},
-               "note": "Context API with pinned host X: H2D, filter+CholGS+RR, D2H of X and Ritz values"}
+               "device_ms": {"h2d": float(med[0]), "step": float(med[1]), "d2h": float(med[2])},
+               "copy_gbs": {"h2d": nbytes / med[0] / 1e6, "d2h": nbytes / med[2] / 1e6},
+               "copy_engine_step": {"wall_s": wce, "h2d_ms": float(msce[0]), "d2h_ms": float(msce[2])},
+               "note": "chfsi_step_host on a pinned host block: the SMs move the rows over the "
+                       "host link (copy_mode 0); copy_engine_step is the same call with the DMA "
+                       "copy engines"}
+        del Xh
 
     # the step after RR (Sec. 3.5, Algorithms rr and dc): spectrum-splitting RR on the
     # orthonormal block (n_fr = 15 % of the subspace), Fermi level and the

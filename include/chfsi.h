@@ -195,6 +195,16 @@ chfsi_status chfsi_apply(chfsi_ctx* ctx, const void* X, int64_t ldx, void* Y, in
 chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, double* Y,
                                  int64_t ldy, int ncol);
 
+/* Test hook of the bounded device waits (no counterpart in the paper; off by
+ * default).  on != 0: in later BF16x3 cell-kernel launches on this device, one
+ * gather warp of the first thread block withholds its arrival on the first
+ * K-chunk's barrier, so the MMA warp's bounded wait (2 s) runs out; the
+ * kernel unwinds (waits for its own copies in flight, frees its TMEM) and the
+ * call returns CHFSI_ERR_TIMEOUT without latching the context.  on = 0
+ * restores normal operation; the next call gives the normal result.  For
+ * tests of the error path only.  Synchronises the stream. */
+chfsi_status chfsi_debug_withhold_arrival(chfsi_ctx* ctx, int on);
+
 /* Degree-m Chebyshev filter (Eq. chebFilter) in the scaled form of Zhou &
  * Saad, in place on X (M x ncol): X <- T_m((H~ - c)/e) X / T_m((a0 - c)/e),
  * c = (a + b)/2, e = (b - a)/2; [a, b] is the damped interval, a0 < a the
@@ -266,6 +276,23 @@ chfsi_status chfsi_solve_polish(chfsi_ctx* ctx, float* X, int64_t ldx, int n, in
                                 double b, double tol, int n_check, chfsi_precision prec,
                                 int polish_iters, int polish_degree, double* X64, int64_t ldx64,
                                 double* evals_host, int* iters_done);
+
+/* One ChFSI iteration (step 7 of Algorithm scf: filter of degree `degree`
+ * with bounds a, b, a0, then CholGS and Rayleigh-Ritz) on a block held in HOST
+ * memory, the transfers included: X_host (host, M x n, leading dimension
+ * ldh, element type of prec) is copied into the caller's device block X
+ * (M x n, ldx), the iteration runs on X, and the result is copied back into
+ * X_host; evals_host[n] receives the Ritz values.  copy_mode: 0 = the SMs
+ * move the rows over the coherent host link when X_host is pinned
+ * (device-mapped, e.g. cudaHostAlloc or cudaHostRegister), else the copy
+ * engines; 1 = always the copy engines (cudaMemcpy2DAsync); 2 = always the
+ * SMs (CHFSI_ERR_ARG when X_host is not device-mapped).  ms3 (may be NULL)
+ * receives the device times of the host-to-device copy, the iteration and
+ * the device-to-host copy (ms, CUDA events on the context stream).
+ * Synchronises. */
+chfsi_status chfsi_step_host(chfsi_ctx* ctx, void* X_host, int64_t ldh, void* X, int64_t ldx, int n,
+                             int degree, double a, double b, double a0, chfsi_precision prec,
+                             int copy_mode, double* evals_host, double* ms3);
 
 /* Spectrum-splitting Rayleigh-Ritz (Algorithm rr, Sec. 3.5): H^ = X^T H~ X for
  * the CholGS output X (M x n, not modified), its n_fr largest eigenpairs in
@@ -438,7 +465,9 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
  * solves: solve 0 starts from chfsi_fill_uniform(seed, stream 1) and runs
  * `iters` ChFSI iterations, every re-solve rebuilds the cell matrices and
  * runs `warm_iters` iterations from the previous X (warm start).  Each solve
- * uses chfsi_solve (tol, n_check as there) and then chfsi_residuals on the
+ * uses chfsi_solve (tol, n_check as there), or chfsi_solve_polish when
+ * polish_iters > 0 (mixed precisions: the polished block, rounded to
+ * binary32, is the next solve's start), and then chfsi_residuals on the
  * lowest n_check pairs.  Requests share no device data, so a request's
  * results do not depend on what else runs.  A request whose estimate exceeds
  * the whole budget completes with CHFSI_ERR_OOM; one that only has to wait
@@ -464,6 +493,8 @@ typedef struct {
   int n_check;            /* pairs checked by the early stop and reported residuals     */
   chfsi_precision prec;   /* filter / orthogonalisation precision                       */
   uint64_t seed;          /* start block and Lanczos seed                              */
+  int polish_iters;       /* mixed precisions: > 0 runs every solve through           */
+  int polish_degree;      /*   chfsi_solve_polish (degree 0 = the request's degree)      */
 } chfsi_request;
 
 typedef struct {

@@ -59,7 +59,8 @@ class Request(C.Structure):
                 ("width", C.POINTER(C.c_double)), ("resolves", C.c_int),
                 ("depth_seq", C.POINTER(C.c_double)), ("degree", C.c_int), ("iters", C.c_int),
                 ("warm_iters", C.c_int), ("tol", C.c_double), ("n_check", C.c_int),
-                ("prec", C.c_int), ("seed", C.c_uint64)]
+                ("prec", C.c_int), ("seed", C.c_uint64), ("polish_iters", C.c_int),
+                ("polish_degree", C.c_int)]
 
 
 class Result(C.Structure):
@@ -105,6 +106,8 @@ _SIGS = {
     "chfsi_solve_polish": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _i64,
                                      _dp, C.POINTER(C.c_int)]),
+    "chfsi_step_host": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int, C.c_int, C.c_double,
+                                  C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp]),
     "chfsi_unscale": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int]),
     "chfsi_rayleigh_ritz_split": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, _vp, _i64, C.c_int, _dp]),
     "chfsi_fermi_level": (C.c_int, [C.c_int, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp]),
@@ -128,6 +131,7 @@ _SIGS = {
     "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_debug_withhold_arrival": (C.c_int, [_vp, C.c_int]),
     "chfsi_partition_sizes": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int,
                                         C.POINTER(PartitionInfo)]),
     "chfsi_partition_fill": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int, _vp, _vp, _vp, _vp,
@@ -314,6 +318,10 @@ class Context:
         py, ldy, _ = _dev(Y, FP64)
         self._check(self._lib.chfsi_apply_noalloc(self._h, px, ldx, py, ldy, n))
 
+    def debug_withhold_arrival(self, on):
+        """Test hook of the bounded device waits (chfsi_debug_withhold_arrival)."""
+        self._check(self._lib.chfsi_debug_withhold_arrival(self._h, int(bool(on))))
+
     def filter(self, X, degree, a, b, a0, prec="fp64"):
         pr = _prec(prec)
         px, ldx, n = _dev(X, pr)
@@ -372,6 +380,23 @@ class Context:
             self._h, px, ldx, n, int(iters), int(degree), float(b), float(tol), int(n_check), pr,
             int(polish_iters), int(polish_degree or degree), p64, ld64, _ptr(ev), C.byref(done)))
         return ev, done.value
+
+    def step_host(self, X_host, X, degree, a, b, a0, prec="bf16x3", copy_mode=0):
+        """One ChFSI iteration on a block in host memory (chfsi_step_host):
+        ``X_host`` a CPU tensor (pinned for the fast path), ``X`` a CUDA tensor
+        of the same shape used as the device copy.  Returns (Ritz values,
+        [h2d_ms, step_ms, d2h_ms])."""
+        import torch
+        pr = _prec(prec)
+        px, ldx, n = _dev(X, pr)
+        if not isinstance(X_host, torch.Tensor) or X_host.is_cuda or X_host.dim() != 2 \
+                or X_host.stride(1) != 1 or X_host.dtype != X.dtype or X_host.shape != X.shape:
+            raise ValueError("X_host: a CPU tensor with X's shape, dtype and unit column stride")
+        ev, ms = np.empty(n), np.zeros(3)
+        self._check(self._lib.chfsi_step_host(self._h, _vp(X_host.data_ptr()), X_host.stride(0), px,
+                                              ldx, n, int(degree), float(a), float(b), float(a0),
+                                              pr, int(copy_mode), _ptr(ev), _ptr(ms)))
+        return ev, ms
 
     def rayleigh_ritz_split(self, X, Xfr, prec="fp64") -> np.ndarray:
         """Algorithm rr: the n_fr = Xfr.shape[1] largest Ritz pairs; Xfr <- X Q_fr."""
@@ -496,7 +521,7 @@ class Batch:
 
 
 def _request(mesh, n, centres, depths, widths, depth_seq=(), degree=30, iters=20, warm_iters=4,
-             tol=0.0, n_check=0, prec="mixed", seed=1):
+             tol=0.0, n_check=0, prec="mixed", seed=1, polish_iters=0, polish_degree=0):
     """ctypes Request plus the numpy arrays it points into (kept alive by the caller)."""
     xyz = _host(centres).reshape(-1)
     dep, wid = _host(depths), _host(widths)
@@ -510,7 +535,8 @@ def _request(mesh, n, centres, depths, widths, depth_seq=(), degree=30, iters=20
                   (C.c_int * 3)(*_axes(periodic)), int(mesh[4]) if len(mesh) > 4 else 0)
     r = Request(md, int(n), nw, _ptr(xyz), _ptr(dep), _ptr(wid), int(resolves),
                 _ptr(seq) if seq.size else None, int(degree), int(iters), int(warm_iters),
-                float(tol), int(n_check), _prec(prec), int(seed))
+                float(tol), int(n_check), _prec(prec), int(seed), int(polish_iters),
+                int(polish_degree))
     return r, (xyz, dep, wid, seq)
 
 

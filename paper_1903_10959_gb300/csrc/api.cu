@@ -1000,6 +1000,12 @@ chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, d
   return CHFSI_OK;
 }
 
+chfsi_status chfsi_debug_withhold_arrival(chfsi_ctx* ctx, int on) {
+  CHECK_CTX();
+  CK(tc_set_withhold(on, ctx->stream));
+  return CHFSI_OK;
+}
+
 chfsi_status chfsi_filter(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
                           double b, double a0, chfsi_precision prec) {
   CHECK_CTX();
@@ -1288,6 +1294,77 @@ chfsi_status chfsi_solve_polish(chfsi_ctx* ctx, float* X, int64_t ldx, int n, in
   std::memcpy(evals_host, D.data(), (size_t)n * 8);
   if (iters_done) *iters_done = it;
   return CHFSI_OK;
+}
+
+chfsi_status chfsi_step_host(chfsi_ctx* ctx, void* X_host, int64_t ldh, void* X, int64_t ldx, int n,
+                             int degree, double a, double b, double a0, chfsi_precision prec,
+                             int copy_mode, double* evals_host, double* ms3) {
+  CHECK_CTX();
+  chfsi_status st = check_x(ctx, X, ldx, n, prec);
+  if (st != CHFSI_OK) return st;
+  if (n < 1 || !X_host || ldh < n || degree < 1 || !(a0 < a) || !(a < b) || !evals_host ||
+      copy_mode < 0 || copy_mode > 2)
+    return fail(ctx, CHFSI_ERR_ARG, "bad host-step arguments");
+  const HostMesh& m = ctx->mesh;
+  const size_t es = esize(prec);
+  // the SMs move the rows over the coherent host link when the host block is
+  // device-mapped (pinned); otherwise, or when asked, the copy engines do
+  void* hdev = nullptr;
+  bool mapped = false;
+  if (copy_mode != 1) {
+    mapped = cudaHostGetDevicePointer(&hdev, X_host, 0) == cudaSuccess;
+    if (!mapped) cudaGetLastError();
+  }
+  if (copy_mode == 2 && !mapped)
+    return fail(ctx, CHFSI_ERR_ARG, "SM copies need a pinned (device-mapped) host block");
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  auto destroy = [&] {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  auto move = [&](const void* src, int64_t lds, void* dst, int64_t ldd, bool to_dev) -> cudaError_t {
+    if (mapped)
+      return launch_copy2d(to_dev ? hdev : src, lds * es, to_dev ? dst : hdev, ldd * es, m.ndofs,
+                           (int64_t)n * es, nsm, ctx->stream);
+    return cudaMemcpy2DAsync(dst, ldd * es, src, lds * es, n * es, m.ndofs,
+                             to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+  };
+  std::fill(ctx->times, ctx->times + 4, 0.0);
+  cudaError_t ce = cudaEventRecord(ev[0], ctx->stream);
+  if (ce == cudaSuccess) ce = move(X_host, ldh, X, ldx, true);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[1], ctx->stream);
+  if (ce != cudaSuccess) {
+    destroy();
+    return fail(ctx, CHFSI_ERR_CUDA, std::string("host-to-device copy: ") + cudaGetErrorString(ce));
+  }
+  std::vector<double> D(n);
+  st = filter_impl(ctx, X, ldx, n, degree, a, b, a0, prec);
+  if (st == CHFSI_OK) st = cholgs_impl(ctx, X, ldx, n, prec);
+  if (st == CHFSI_OK) st = rr_impl(ctx, X, ldx, n, prec, D.data());
+  if (st != CHFSI_OK) {
+    destroy();
+    return st;
+  }
+  ce = cudaEventRecord(ev[2], ctx->stream);
+  if (ce == cudaSuccess) ce = move(X, ldx, X_host, ldh, false);
+  if (ce == cudaSuccess) ce = cudaEventRecord(ev[3], ctx->stream);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(ev[3]);
+  if (ce != cudaSuccess) {
+    destroy();
+    return fail(ctx, CHFSI_ERR_CUDA, std::string("device-to-host copy: ") + cudaGetErrorString(ce));
+  }
+  if (ms3)
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      ms3[k] = t;
+    }
+  destroy();
+  std::memcpy(evals_host, D.data(), (size_t)n * 8);
+  return check_device_status(ctx, prec);
 }
 
 chfsi_status chfsi_unscale(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, chfsi_precision prec) {

@@ -130,6 +130,9 @@ cudaError_t launch_fill_uniform(void* X, int64_t ldx, int64_t rows, int ncol, ui
                                 int is_double, cudaStream_t s);
 cudaError_t launch_copy_cols(const void* src, int64_t lds, void* dst, int64_t ldd, int64_t rows,
                              int ncol, int src_double, int dst_double, cudaStream_t s);
+// Pitched 2-D byte copy by the SMs (src / dst device or device-mapped host).
+cudaError_t launch_copy2d(const void* src, int64_t src_pitch, void* dst, int64_t dst_pitch,
+                          int64_t rows, int64_t row_bytes, int nsm, cudaStream_t s);
 cudaError_t launch_scale_rows(void* X, int64_t ldx, int64_t rows, int ncol, const double* sv,
                               int is_double, cudaStream_t s);
 

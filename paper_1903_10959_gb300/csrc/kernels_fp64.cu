@@ -1,3 +1,4 @@
+#include <algorithm>
 // Binary64 kernels of the ChFSI step (CUDA-core DFMA; GB300 runs binary64 at
 // ~1 TFLOP/s, so these kernels are arithmetic-bound and kept simple), plus
 // the precision-independent helpers (seeded fill, copies, scaling).
@@ -446,6 +447,39 @@ cudaError_t launch_copy_cols(const void* src, int64_t lds, void* dst, int64_t ld
   note_launch();
   copy_cols_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, lds, dst, ldd, rows, ncol,
                                                                   src_double, dst_double);
+  return cudaGetLastError();
+}
+
+// Row-by-row byte copy between two pitched 2-D buffers (either may be a
+// device-mapped host buffer: the SMs then move the rows over the coherent
+// host link).  16-byte vectors when every pointer, pitch and row length is a
+// multiple of 16 bytes, else 4-byte words (row lengths are multiples of 4).
+__global__ void copy2d_kernel(const char* __restrict__ src, int64_t sp, char* __restrict__ dst,
+                              int64_t dp, int64_t rows, int64_t rb, int vec) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t w = vec ? 16 : 4;
+  const int64_t per = rb / w, tot = rows * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += stride) {
+    const int64_t r = i / per, c = i - r * per;
+    if (vec)
+      reinterpret_cast<uint4*>(dst + r * dp)[c] = reinterpret_cast<const uint4*>(src + r * sp)[c];
+    else
+      reinterpret_cast<uint32_t*>(dst + r * dp)[c] = reinterpret_cast<const uint32_t*>(src + r * sp)[c];
+  }
+}
+
+cudaError_t launch_copy2d(const void* src, int64_t src_pitch, void* dst, int64_t dst_pitch,
+                          int64_t rows, int64_t row_bytes, int nsm, cudaStream_t s) {
+  if (rows == 0 || row_bytes == 0) return cudaSuccess;
+  if (row_bytes % 4 || src_pitch % 4 || dst_pitch % 4 || ((uintptr_t)src & 3) || ((uintptr_t)dst & 3))
+    return cudaErrorInvalidValue;
+  const int vec = (row_bytes % 16 == 0 && src_pitch % 16 == 0 && dst_pitch % 16 == 0 &&
+                   ((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0);
+  const int64_t tot = rows * (row_bytes / (vec ? 16 : 4));
+  const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)std::max(nsm, 1) * 8);
+  note_launch();
+  copy2d_kernel<<<(unsigned)blocks, 256, 0, s>>>((const char*)src, src_pitch, (char*)dst, dst_pitch,
+                                                 rows, row_bytes, vec);
   return cudaGetLastError();
 }
 

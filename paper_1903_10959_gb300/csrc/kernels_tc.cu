@@ -40,6 +40,10 @@ namespace chfsi {
 using namespace ptx;
 
 __device__ int g_tc_status = 0;   // nonzero after a bounded wait gave up
+// Test hook of the bounded waits (0 = off, the default): when set, gather warp
+// 0 of the first CTA of the BF16x3 cell kernel withholds its arrival on the
+// first chunk's full barrier, so that the MMA warp's wait on it runs out.
+__device__ int g_tc_withhold = 0;
 
 constexpr int CELL_BN = 64;       // default columns per CTA (128 selectable)
 constexpr int CELL_KC = 8;        // K per pipeline stage (one MMA K-step)
@@ -641,6 +645,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 2) tc_cell_bf16_kernel(RParams P
     // so each load reads 128 contiguous bytes of a Y row and each 16-byte
     // store of 8 lanes fills one 128-byte core matrix (no bank conflicts)
     const int pair = warp >> 1, q = warp & 1;
+    const bool withhold = g_tc_withhold != 0 && blockIdx.x == 0 && blockIdx.y == 0 && P.e_off == 0;
     for (int i = pair; i < nk; i += 2) {
       const int s = i % S;
       float v[8][4];
@@ -679,7 +684,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 2) tc_cell_bf16_kernel(RParams P
           *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
       }
       fence_proxy_async_smem();
-      mbar_arrive(fy(s));
+      if (!(withhold && warp == 0 && i == 0)) mbar_arrive(fy(s));
     }
     // epilogue: TMEM lane = column c0 + c, TMEM column = cell row r0 + j;
     // for each row the warp's lanes store 32 consecutive floats
@@ -826,6 +831,13 @@ cudaError_t tc_assemble_launch(const AssembleParams& P0, cudaStream_t s) {
   else
     tc_assemble_kernel<false><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P);
   return cudaGetLastError();
+}
+
+cudaError_t tc_set_withhold(int on, cudaStream_t s) {
+  const int v = on ? 1 : 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_tc_withhold, &v, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
 }
 
 int tc_read_status(cudaStream_t s) {

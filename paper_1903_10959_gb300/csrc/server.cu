@@ -95,6 +95,8 @@ size_t estimate_bytes(const chfsi_request& r) {
   b += std::max(n * n * 64 + (mixed ? ((size_t)64 << 20) : 0), n * 12288);  // Gram partials
   b += n * n * 8 * 4 + n * 64 + 4096;                               // N x N, solver workspace
   b += M * 24 + ((size_t)16 << 20);                                 // vectors, library slack
+  if (mixed && r.polish_iters > 0)                                  // binary64 polish: staging
+    b += M * n * 8 + M * n * 4 + M * B * 4;                         //  block, rotation, filter
   return b;
 }
 
@@ -107,6 +109,7 @@ void run_job(chfsi_server* sv, std::shared_ptr<Job> job) {
   chfsi_ctx* ctx = nullptr;
   void* X = nullptr;
   const size_t es = r.prec == CHFSI_FP64 ? 8 : 4;
+  const bool polish = r.polish_iters > 0 && r.prec != CHFSI_FP64;
   auto finish = [&](chfsi_status s, const std::string& msg) {
     J.status = s;
     J.err = msg;
@@ -134,9 +137,14 @@ void run_job(chfsi_server* sv, std::shared_ptr<Job> job) {
           if (s == CHFSI_OK) s = chfsi_fill_uniform(ctx, X, n, M, n, r.seed, 1, r.prec);
         }
         int done = 0;
-        if (s == CHFSI_OK)
-          s = chfsi_solve(ctx, X, n, n, k == 0 ? r.iters : r.warm_iters, r.degree, b, r.tol,
-                          r.n_check, r.prec, J.evals.data() + (size_t)k * n, &done);
+        const int its = k == 0 ? r.iters : r.warm_iters;
+        double* ev = J.evals.data() + (size_t)k * n;
+        if (s == CHFSI_OK && polish)
+          s = chfsi_solve_polish(ctx, (float*)X, n, n, its, r.degree, b, r.tol, r.n_check, r.prec,
+                                 r.polish_iters, r.polish_degree > 0 ? r.polish_degree : r.degree,
+                                 nullptr, 0, ev, &done);
+        else if (s == CHFSI_OK)
+          s = chfsi_solve(ctx, X, n, n, its, r.degree, b, r.tol, r.n_check, r.prec, ev, &done);
         J.iters.push_back(done);
         double mx = 0.0, gmx = 0.0;
         if (s == CHFSI_OK && r.n_check > 0) {
@@ -224,7 +232,7 @@ chfsi_status chfsi_server_submit(chfsi_server* sv, const chfsi_request* r, uint6
   if (!sv || !r || !ticket || r->n < 1 || r->nwells < 0 || r->resolves < 0 || r->degree < 1 ||
       r->iters < 0 || r->warm_iters < 0 || (r->nwells > 0 && (!r->xyz || !r->depth || !r->width)) ||
       (r->resolves > 0 && r->nwells > 0 && !r->depth_seq) || r->resolves + 1 > CHFSI_MAX_SOLVES ||
-      r->mesh.p < 1 || r->n_check > r->n)
+      r->mesh.p < 1 || r->n_check > r->n || r->polish_iters < 0 || r->polish_degree < 0)
     return CHFSI_ERR_ARG;
   auto job = std::make_shared<Job>();
   job->req = *r;

@@ -93,6 +93,8 @@ cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s
                                 int64_t* dev_bytes);
 // Read and clear the device status word of the bounded waits (0: no timeout).
 int tc_read_status(cudaStream_t s);
+// Test hook: withhold one gather arrival in the BF16x3 cell kernel (see kernels_tc.cu).
+cudaError_t tc_set_withhold(int on, cudaStream_t s);
 size_t tc_tallgemm_work_bytes(int n1, int n2);
 void tc_free(TcCellData& d);
 size_t tc_gram_partial_bytes(int64_t M, int n1, int n2);

@@ -41,7 +41,8 @@ def requests(small):
                                            n_range=(12, 40), degree=DEGREE, resolves=2)
 
 
-def _run(requests, max_active, budget=1 << 36, prec="mixed", tol=0.0, iters=ITERS, warm=WARM):
+def _run(requests, max_active, budget=1 << 36, prec="mixed", tol=0.0, iters=ITERS, warm=WARM,
+         polish=0):
     out, t_sub = [], []
     with Server(budget, max_active) as sv:
         tickets = []
@@ -50,7 +51,7 @@ def _run(requests, max_active, budget=1 << 36, prec="mixed", tol=0.0, iters=ITER
             tickets.append(sv.submit(_mesh(s), s.n_sub, s.centres, s.depths, s.widths,
                                      depth_seq=seq, degree=s.degree, iters=iters,
                                      warm_iters=warm, tol=tol, n_check=s.n_want, prec=prec,
-                                     seed=s.seed))
+                                     seed=s.seed, polish_iters=polish))
         for t in tickets:
             out.append(sv.poll(t, wait=True))
     for r, t0 in zip(out, t_sub):
@@ -112,6 +113,25 @@ def test_eigenvalues_match_dense_oracle(mix, small):
         err = np.abs(r["evals"][j][:s.n_want] - exact[j][:s.n_want]).max()
         assert err < 1e-7, (j, err)
         assert r["max_gresidual"][j] < MIXED_GRES_FLOOR, (j, r["max_gresidual"][j])
+
+
+POLISHED_GRES = 1e-6
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16x3"])
+def test_polished_solves_meet_the_residual_target(small, prec):
+    """With the binary64 polish (one binary64 iteration of the request's
+    degree after the mixed iterations, chfsi_solve_polish) every solve of the
+    small request -- cold and warm, original and perturbed potentials --
+    meets the generalized-residual target <= 1e-6 and <= 1e-7 Ha against the
+    oracle's dense diagonalisation."""
+    s, seq, exact = small
+    r, = _run([(s, seq)], max_active=1, prec=prec, polish=1)
+    assert r["status"] == 0, r["error"]
+    for j in range(len(seq) + 1):
+        assert r["max_gresidual"][j] <= POLISHED_GRES, (j, r["max_gresidual"][j])
+        err = np.abs(r["evals"][j][:s.n_want] - exact[j][:s.n_want]).max()
+        assert err <= 1e-7, (j, err)
 
 
 def test_budget_admits_one_at_a_time(requests):
