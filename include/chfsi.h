@@ -142,6 +142,19 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
  * do not depend on it. */
 chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
 
+/* Cell operator of the binary64 path (every CHFSI_FP64 apply, and the
+ * binary64 products of the mixed precisions' last Rayleigh-Ritz, residuals
+ * and polish): 0 = the stored cell matrices H~_e (dense n_e x n_e products,
+ * Sec. 3.3.1); 1 = matrix-free, H_e applied by sum factorisation over the
+ * tensor-product cell (1-D mass / stiffness / Gauss-point factors, the
+ * alternative the paper notes for the cell-level products), 3.2x (p = 6) to
+ * 5.5x (p = 8) fewer flops; -1 = the library's default.  The matrix-free form
+ * needs 2 <= p <= 8 and quad_points = p + 2 (CHFSI_ERR_ARG otherwise).  Both
+ * give the same operator to rounding.  chfsi_fp64_operator returns the one in
+ * use (0 or 1). */
+chfsi_status chfsi_set_fp64_operator(chfsi_ctx* ctx, int op);
+int          chfsi_fp64_operator(const chfsi_ctx* ctx);
+
 /* Autotuner of the filter's blocking: times a degree-2 filter on a scratch
  * copy of X (M x n, device; X itself is not modified) for every candidate
  * (wavefunction block 200, ceil(n/2) and n, times cell tile 64 and 128 for
@@ -283,10 +296,12 @@ chfsi_status chfsi_solve_polish(chfsi_ctx* ctx, float* X, int64_t ldx, int n, in
  * ldh, element type of prec) is copied into the caller's device block X
  * (M x n, ldx), the iteration runs on X, and the result is copied back into
  * X_host; evals_host[n] receives the Ritz values.  copy_mode: 0 = the SMs
- * move the rows over the coherent host link when X_host is pinned
- * (device-mapped, e.g. cudaHostAlloc or cudaHostRegister), else the copy
- * engines; 1 = always the copy engines (cudaMemcpy2DAsync); 2 = always the
- * SMs (CHFSI_ERR_ARG when X_host is not device-mapped).  ms3 (may be NULL)
+ * move the rows over the coherent host link when the GPU can address X_host
+ * (cudaHostGetDevicePointer succeeds: pinned memory from cudaHostAlloc or
+ * cudaHostRegister, and on hosts whose GPU reaches pageable memory directly,
+ * such as Grace, any host memory), else the copy engines; 1 = always the
+ * copy engines (cudaMemcpy2DAsync); 2 = always the SMs (CHFSI_ERR_ARG when
+ * the GPU cannot address X_host).  ms3 (may be NULL)
  * receives the device times of the host-to-device copy, the iteration and
  * the device-to-host copy (ms, CUDA events on the context stream).
  * Synchronises. */

@@ -131,6 +131,8 @@ _SIGS = {
     "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_set_fp64_operator": (C.c_int, [_vp, C.c_int]),
+    "chfsi_fp64_operator": (C.c_int, [_vp]),
     "chfsi_debug_withhold_arrival": (C.c_int, [_vp, C.c_int]),
     "chfsi_partition_sizes": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int,
                                         C.POINTER(PartitionInfo)]),
@@ -317,6 +319,16 @@ class Context:
         px, ldx, n = _dev(X, FP64)
         py, ldy, _ = _dev(Y, FP64)
         self._check(self._lib.chfsi_apply_noalloc(self._h, px, ldx, py, ldy, n))
+
+    def set_fp64_operator(self, op):
+        """Binary64 cell operator: "cells" (stored cell matrices), "matrix-free"
+        (sum factorisation) or "default" (chfsi_set_fp64_operator)."""
+        code = {"default": -1, "cells": 0, "matrix-free": 1}[op]
+        self._check(self._lib.chfsi_set_fp64_operator(self._h, code))
+
+    @property
+    def fp64_operator(self):
+        return ("cells", "matrix-free")[self._lib.chfsi_fp64_operator(self._h)]
 
     def debug_withhold_arrival(self, on):
         """Test hook of the bounded device waits (chfsi_debug_withhold_arrival)."""

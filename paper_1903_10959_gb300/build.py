@@ -21,7 +21,8 @@ LIB = os.path.join(HERE, "libchfsi.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["kernels_fp64.cu", "kernels_tc.cu", "api.cu", "batch.cu", "server.cu", "density.cu"]
+CUDA_SOURCES = ["kernels_fp64.cu", "kernels_tc.cu", "kernels_mf.cu", "api.cu", "batch.cu", "server.cu",
+                "density.cu"]
 CXX_SOURCES = ["mesh.cpp", "partition.cpp"]
 
 

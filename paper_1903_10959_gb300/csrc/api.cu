@@ -132,6 +132,9 @@ bool is_mixed(chfsi_precision p) {
 int split3_of(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_BF16X3; }
 // Columns per block of the binary64 staging copies (residuals, binary64 RR apply).
 constexpr int kStage64 = 512;
+// Whether the binary64 path uses the matrix-free cell apply when the context
+// leaves the choice open (chfsi_set_fp64_operator(-1)).
+constexpr bool kMatrixFreeDefault = false;
 // Free the per-call scratch that grows with the column block (filter, cell
 // blocks, projector and binary64 staging buffers); later calls regrow it.
 void release_scratch(chfsi_ctx* ctx) {
@@ -146,9 +149,24 @@ void release_scratch(chfsi_ctx* ctx) {
 bool valid_prec(chfsi_precision p) { return p == CHFSI_FP64 || is_mixed(p); }
 size_t esize(chfsi_precision p) { return p == CHFSI_FP64 ? 8 : 4; }
 
+std::vector<double> minv_sqrt(const HostMesh& m) {
+  std::vector<double> s(m.mass.size());
+  for (size_t j = 0; j < s.size(); ++j) s[j] = 1.0 / std::sqrt(m.mass[j]);
+  return s;
+}
+
+// Binary64 cell operator of this context: the sum-factorised (matrix-free)
+// apply when selected, or by default when it exists for the degree and rule.
+bool use_matrix_free(const chfsi_ctx* ctx) {
+  if (!mf_supported(ctx->mesh.p, ctx->mesh.q)) return false;
+  return ctx->fp64_op == 1 || (ctx->fp64_op < 0 && kMatrixFreeDefault);
+}
+
 void free_device_data(chfsi_ctx* ctx) {
   const HostMesh& m = ctx->mesh;
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
+  release(ctx, ctx->d_wv, ctx->wv.size() * 8);
+  release(ctx, ctx->d_fac, ctx->fac.size() * 8);
   ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes);   // packed copies (0 when never packed)
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
@@ -186,7 +204,30 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
       CK(launch_nl_expand_fp64(ctx->d_dof_ptr, ctx->d_dof_site, ctx->d_dof_c, m.ndofs,
                                (const double*)ctx->Zb.ptr, ncol, (double*)ctx->NLb.ptr, B, ctx->stream));
     }
+    const bool mf = use_matrix_free(ctx);
     for (int c = 0; c < ncolour; ++c) {
+      KTimer kt(ctx, 0);
+      if (mf) {
+        MfLaunch L{};
+        L.fac = ctx->d_fac;
+        L.wv = ctx->d_wv;
+        L.minv_sqrt = ctx->d_msq;
+        L.dofmap = ctx->d_dofmap;
+        L.modes = ctx->d_modes;
+        L.cells = ctx->d_cells + m.colour_offsets[c];
+        L.ncells_colour = m.colour_offsets[c + 1] - m.colour_offsets[c];
+        L.p = m.p;
+        L.q = m.q;
+        L.ncol = ncol;
+        L.ld_in = ld_in;
+        L.ld_out = ld_out;
+        L.ld_prev = ld_prev;
+        L.ld_w = B;
+        CK(launch_mf_cell_fp64(L, (const double*)Yin, (double*)Yout, (const double*)Yprev,
+                               (double*)ctx->Wb.ptr, nl ? (const double*)ctx->NLb.ptr : nullptr,
+                               FilterStep{alpha, beta, shift}, ctx->stream));
+        continue;
+      }
       CellLaunch L{};
       L.Ht = ctx->d_Ht;
       L.dofmap = ctx->d_dofmap;
@@ -198,7 +239,6 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
       L.ld_in = ld_in;
       L.ld_out = ld_out;
       L.ld_prev = ld_prev;
-      KTimer kt(ctx, 0);
       CK(launch_cell_fp64(L, (const double*)Yin, (double*)Yout, (const double*)Yprev,
                           (double*)ctx->Wb.ptr, nl ? (const double*)ctx->NLb.ptr : nullptr, B,
                           FilterStep{alpha, beta, shift}, ctx->stream));
@@ -676,6 +716,7 @@ chfsi_status chfsi_create(const chfsi_mesh_desc* desc, void* stream, chfsi_ctx**
       (e = upload(ctx, &ctx->d_mass, m.mass)) != cudaSuccess ||
       (e = upload(ctx, &ctx->d_node_ptr, m.node_ptr)) != cudaSuccess ||
       (e = upload(ctx, &ctx->d_node_ent, m.node_ent)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_msq, minv_sqrt(m))) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev[0])) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev[1])) != cudaSuccess ||
       (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
@@ -697,6 +738,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_mass, m.mass.size() * 8);
   release(ctx, ctx->d_node_ptr, m.node_ptr.size() * 4);
   release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
+  release(ctx, ctx->d_msq, m.mass.size() * 8);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol})
     dfree(ctx, b->ptr, b->bytes);
@@ -808,10 +850,13 @@ chfsi_status chfsi_build(chfsi_ctx* ctx) {
   free_device_data(ctx);
   const HostMesh& m = ctx->mesh;
   std::vector<double> Ht;
-  build_cell_matrices(m, ctx->wells, Ht);
+  build_cell_matrices(m, ctx->wells, Ht, &ctx->wv);
+  build_mf_factors(m, ctx->fac);
   build_projectors(m, ctx->proj, ctx->hproj);
   cudaError_t e;
-  if ((e = upload(ctx, &ctx->d_Ht, Ht)) != cudaSuccess) {
+  if ((e = upload(ctx, &ctx->d_Ht, Ht)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_wv, ctx->wv)) != cudaSuccess ||
+      (e = upload(ctx, &ctx->d_fac, ctx->fac)) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, e == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
                 std::string("cell matrices: ") + cudaGetErrorString(e));
@@ -855,6 +900,17 @@ chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile) {
   ctx->cell_tile = tile;
   return CHFSI_OK;
 }
+
+chfsi_status chfsi_set_fp64_operator(chfsi_ctx* ctx, int op) {
+  CHECK_CTX();
+  if (op < -1 || op > 1) return fail(ctx, CHFSI_ERR_ARG, "operator: -1 default, 0 cell matrices, 1 matrix-free");
+  if (op == 1 && !mf_supported(ctx->mesh.p, ctx->mesh.q))
+    return fail(ctx, CHFSI_ERR_ARG, "the matrix-free apply needs 2 <= p <= 8 and p + 2 Gauss points");
+  ctx->fp64_op = op;
+  return CHFSI_OK;
+}
+
+int chfsi_fp64_operator(const chfsi_ctx* ctx) { return ctx ? (use_matrix_free(ctx) ? 1 : 0) : -1; }
 
 chfsi_status chfsi_autotune(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, chfsi_precision prec,
                             int* block_out, int* tile_out, double* ms_out) {

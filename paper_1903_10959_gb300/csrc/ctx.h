@@ -26,6 +26,12 @@ struct chfsi_ctx {
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices
+  double* d_wv = nullptr;          // matrix-free apply: w jac V at the Gauss points per cell
+  double* d_fac = nullptr;         // matrix-free apply: 1-D factors
+  double* d_msq = nullptr;         // M^{-1/2} per unknown
+  std::vector<double> wv;          // host copy of d_wv (sizes)
+  std::vector<double> fac;
+  int fp64_op = -1;                // binary64 cell operator: 0 cell matrices, 1 matrix-free, -1 auto
   chfsi::TcCellData tc;                   // tensor-core copies (mixed precisions)
   int32_t* d_dofmap = nullptr;
   uint8_t* d_modes = nullptr;

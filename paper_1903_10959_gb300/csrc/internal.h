@@ -80,8 +80,14 @@ struct Projectors {
   double sigma = 0.8, rcut = 3.0;
 };
 
-// Cell matrices H~_e (binary64, row-major ne x ne per cell) for all cells.
-void build_cell_matrices(const HostMesh& m, const Wells& w, std::vector<double>& Ht);
+// Cell matrices H~_e (binary64, row-major ne x ne per cell) for all cells;
+// wv (optional): per cell, w_a w_b w_c jac V at the q^3 Gauss points (the
+// potential factor of the matrix-free apply).
+void build_cell_matrices(const HostMesh& m, const Wells& w, std::vector<double>& Ht,
+                         std::vector<double>* wv = nullptr);
+// 1-D factors of the matrix-free apply: A_x, A_y, A_z, S_x, S_y, S_z (n1 x n1,
+// consistent mass and stiffness by the Gauss rule), B (q x n1) and B^T.
+void build_mf_factors(const HostMesh& m, std::vector<double>& fac);
 
 // Scaled projector matrix C~ = C M^{-1/2} in two compressed forms:
 //  by site: for site s, rows [site_ptr[s], site_ptr[s+1]) of (dof, c[4]);
@@ -125,6 +131,24 @@ struct CellLaunch {
 cudaError_t launch_cell_fp64(const CellLaunch& L, const double* Yin, double* Yout,
                              const double* Yprev, double* W, const double* NL, int64_t ld_w,
                              FilterStep st, cudaStream_t s);
+
+// Matrix-free binary64 cell apply (kernels_mf.cu): same contract as
+// launch_cell_fp64 for one colour, with H~_e applied by sum factorisation.
+struct MfLaunch {
+  const double* fac;          // 1-D factors: A_x, A_y, A_z, S_x, S_y, S_z (n1 x n1), B (q x n1), B^T
+  const double* wv;           // per cell, w_a w_b w_c jac V at the q^3 Gauss points
+  const double* minv_sqrt;    // M^{-1/2} per unknown
+  const int32_t* dofmap;
+  const uint8_t* modes;
+  const int32_t* cells;       // cells of this colour
+  int64_t ncells_colour;
+  int p, q, ncol;
+  int64_t ld_in, ld_out, ld_prev, ld_w;
+};
+bool mf_supported(int p, int q);
+cudaError_t launch_mf_cell_fp64(const MfLaunch& L, const double* Yin, double* Yout,
+                                const double* Yprev, double* W, const double* NL, FilterStep st,
+                                cudaStream_t s);
 
 cudaError_t launch_fill_uniform(void* X, int64_t ldx, int64_t rows, int ncol, uint64_t key,
                                 int is_double, cudaStream_t s);

@@ -258,10 +258,12 @@ static inline double well_sum(const double* x, const std::vector<double>& cx,
   return v;
 }
 
-void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>& Ht) {
+void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>& Ht,
+                         std::vector<double>* wv) {
   const int n1 = m.n1, ne = m.ne, q = m.q;
   const int nn = n1 * n1;
   Ht.assign((size_t)m.ncells * ne * ne, 0.0);
+  if (wv) wv->assign((size_t)m.ncells * q * q * q, 0.0);
 
   // 1-D consistent mass A and stiffness S per axis (Gauss rule, exact)
   std::vector<double> A[3], S[3];
@@ -339,6 +341,7 @@ void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>
         xq[2] = lo[2] + (m.gq_x[c] + 1.0) * m.h[2] / 2.0;
         const int pt = (c * q + b) * q + a;
         V[pt] = (well_sum(xq, cx, dd, inv2w2) + (vq ? vq[pt] : 0.0)) * jac;
+        if (wv) (*wv)[(size_t)e * q * q * q + pt] = V[pt] * m.gq_w[a] * m.gq_w[b] * m.gq_w[c];
       }
       // T1[c][b][il] = sum_a BB[a][il] V[c][b][a]
       for (int cb = 0; cb < q * q; ++cb)
@@ -382,6 +385,29 @@ void build_cell_matrices(const HostMesh& m, const Wells& wl, std::vector<double>
       }
     }
   }
+}
+
+void build_mf_factors(const HostMesh& m, std::vector<double>& fac) {
+  const int n1 = m.n1, q = m.q, nn = n1 * n1;
+  fac.assign((size_t)6 * nn + 2 * q * n1, 0.0);
+  for (int ax = 0; ax < 3; ++ax)
+    for (int i = 0; i < n1; ++i)
+      for (int l = 0; l < n1; ++l) {
+        double sa = 0.0, ss = 0.0;
+        for (int a = 0; a < q; ++a) {
+          sa += m.gq_w[a] * m.B[a * n1 + i] * m.B[a * n1 + l];
+          ss += m.gq_w[a] * m.D[a * n1 + i] * m.D[a * n1 + l];
+        }
+        fac[(size_t)ax * nn + i * n1 + l] = sa * m.h[ax] / 2.0;          // A_ax
+        fac[(size_t)(3 + ax) * nn + i * n1 + l] = ss * 2.0 / m.h[ax];    // S_ax
+      }
+  double* B = fac.data() + 6 * nn;
+  double* Bt = B + q * n1;
+  for (int a = 0; a < q; ++a)
+    for (int i = 0; i < n1; ++i) {
+      B[a * n1 + i] = m.B[a * n1 + i];
+      Bt[i * q + a] = m.B[a * n1 + i];
+    }
 }
 
 void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& out) {
