@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps (median wall time reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gather", default="async", choices=["async", "registers"],
+                    help="BF16x3 cell kernel gather (bulk async copies or register loads)")
+    ap.add_argument("--fp64-op", default="default", choices=["default", "cells", "matrix-free"],
+                    help="binary64 cell operator")
     ap.add_argument("--no-side-arms", action="store_true",
                     help="skip the binary64 / polished arm and the 20^3-cell p=7 arm")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
@@ -515,6 +519,8 @@ def run_ours(args):
     ctx.build()
     ctx.set_blocking(s.block, 1)
     ctx.set_cell_tile(args.tile)
+    ctx.set_cell_gather(args.gather)
+    ctx.set_fp64_operator(args.fp64_op)
     n, M = s.n_sub, ctx.ndofs
     b = ctx.bounds(20, s.seed)
     X = torch.empty((M, n), dtype=dt, device="cuda")

@@ -142,6 +142,13 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
  * do not depend on it. */
 chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
 
+/* Gather of the BF16x3 cell kernel: 1 (default) = the cell's rows of Y are
+ * staged in shared memory by bulk async copies, several K-chunks ahead of the
+ * tensor-core products (used when the block is 16-byte aligned with a
+ * leading dimension and a column count that are multiples of 4); 0 = warps
+ * load the rows into registers.  Results are bit-identical. */
+chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode);
+
 /* Cell operator of the binary64 path (every CHFSI_FP64 apply, and the
  * binary64 products of the mixed precisions' last Rayleigh-Ritz, residuals
  * and polish): 0 = the stored cell matrices H~_e (dense n_e x n_e products,

@@ -132,6 +132,7 @@ _SIGS = {
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "chfsi_set_fp64_operator": (C.c_int, [_vp, C.c_int]),
+    "chfsi_set_cell_gather": (C.c_int, [_vp, C.c_int]),
     "chfsi_fp64_operator": (C.c_int, [_vp]),
     "chfsi_debug_withhold_arrival": (C.c_int, [_vp, C.c_int]),
     "chfsi_partition_sizes": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int,
@@ -319,6 +320,10 @@ class Context:
         px, ldx, n = _dev(X, FP64)
         py, ldy, _ = _dev(Y, FP64)
         self._check(self._lib.chfsi_apply_noalloc(self._h, px, ldx, py, ldy, n))
+
+    def set_cell_gather(self, mode):
+        """BF16x3 cell kernel gather: "async" (bulk copies) or "registers"."""
+        self._check(self._lib.chfsi_set_cell_gather(self._h, {"registers": 0, "async": 1}[mode]))
 
     def set_fp64_operator(self, op):
         """Binary64 cell operator: "cells" (stored cell matrices), "matrix-free"

@@ -280,6 +280,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.R = (float*)ctx->Rb.ptr;
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
   ra.tile = ctx->cell_tile;
+  ra.gather = ctx->cell_gather;
   {
     KTimer kt(ctx, 0);
     if (bf16) CK(tc_cell_bf16_launch(ctx->tc, ra, ctx->stream));
@@ -898,6 +899,13 @@ chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile) {
   CHECK_CTX();
   if (tile != 64 && tile != 128) return fail(ctx, CHFSI_ERR_ARG, "cell tile must be 64 or 128");
   ctx->cell_tile = tile;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode) {
+  CHECK_CTX();
+  if (mode != 0 && mode != 1) return fail(ctx, CHFSI_ERR_ARG, "gather: 0 register loads, 1 bulk async copies");
+  ctx->cell_gather = mode;
   return CHFSI_OK;
 }
 

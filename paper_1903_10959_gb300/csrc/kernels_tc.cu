@@ -715,6 +715,259 @@ __global__ void __launch_bounds__(CELL_THREADS, 2) tc_cell_bf16_kernel(RParams P
   if (warp == 5) tmem_dealloc(tmem, B.alloc);
 }
 
+// ----------------------------------------------------------------- BF16x3 cell kernel, async gather
+// The same product, tiling and arithmetic as tc_cell_bf16_kernel (bit-identical
+// results), with the gather of the cell's rows of Y done by bulk async copies
+// instead of register loads: warp 6 copies the 16 rows of each K-chunk (one
+// copy of ncv * 4 bytes per row) into a ring of S_y binary32 staging slots,
+// up to S_y chunks ahead; warps 0-3 split a staged chunk into its three bf16
+// terms in the MMA layout (pairs on alternate chunks, as before) and release
+// the slot.  The register gather keeps two chunks in flight per CTA; here
+// S_y chunks are, so the gather's latency hides behind the MMAs.  Needs
+// 16-byte aligned rows: Y 16-byte aligned, ld_in and ncol multiples of 4.
+constexpr int BFA_THREADS = 224;
+constexpr int BFA_ROWB = 128 * 4;             // one staged row: 128 binary32 columns
+constexpr int BFA_SLOT = BF_KC * BFA_ROWB;    // one staged K-chunk (8 KB)
+struct BfaPlan {
+  int np, nh, alloc, st, sy, total;
+};
+__host__ __device__ inline BfaPlan bfa_plan(int ne) {
+  const BfPlan b = bf_plan(ne);
+  BfaPlan a;
+  a.np = b.np;
+  a.nh = b.nh;
+  a.alloc = b.alloc;
+  const int per_sm = 512 / b.alloc >= 3 ? 3 : 512 / b.alloc;
+  const int budget = (per_sm >= 3 ? 72 : (per_sm == 2 ? 110 : 200)) * 1024 - kCellSmemTail;
+  const int stage = BF_YT + 3 * b.nh * 32;
+  a.st = 2;
+  a.sy = (budget - a.st * stage) / BFA_SLOT;
+  if (a.sy > 8) a.sy = 8;
+  if (a.sy >= 6 && budget - 3 * stage >= 3 * BFA_SLOT) {   // room for a third term stage
+    a.st = 3;
+    a.sy = (budget - a.st * stage) / BFA_SLOT;
+    if (a.sy > 8) a.sy = 8;
+  }
+  if (a.sy < 2) a.sy = 2;
+  a.total = a.st * stage + a.sy * BFA_SLOT + kCellSmemTail;
+  return a;
+}
+
+__global__ void __launch_bounds__(BFA_THREADS, 2) tc_cell_bf16_async_kernel(RParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.e_off + blockIdx.y;
+  const int ne = P.ne, nk = P.nk;   // nk: K-chunks of 16
+  const BfaPlan B = bfa_plan(ne);
+  const int h = blockIdx.x % B.np;
+  const int c0 = (blockIdx.x / B.np) * 128;
+  const int ncv = min(128, P.ncol - c0);
+  const int r0 = h * B.nh;
+  const int ST = B.st, SY = B.sy;
+  const int hrow = B.nh * 32;
+  const int stage_bytes = BF_YT + 3 * hrow;
+  unsigned char* stg = smem + ST * stage_bytes;             // staging ring
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + SY * BFA_SLOT);
+  // barriers: fa[ST], fy[ST], em[ST], sf[SY], se[SY], acc  (<= 3*3 + 2*8 + 1 = 26 x 8 B)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * ST + 2 * SY + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t gbase = smem_u32(stg);
+  auto fa = [&](int s) { return smem_u32(bars + s); };
+  auto fy = [&](int s) { return smem_u32(bars + ST + s); };
+  auto em = [&](int s) { return smem_u32(bars + 2 * ST + s); };
+  auto sf = [&](int s) { return smem_u32(bars + 3 * ST + s); };
+  auto se = [&](int s) { return smem_u32(bars + 3 * ST + SY + s); };
+  const uint32_t accb = smem_u32(bars + 3 * ST + 2 * SY);
+
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(fa(s), 1);
+      mbar_init(fy(s), 64);
+      mbar_init(em(s), 1);
+    }
+    for (int s = 0; s < SY; ++s) {
+      mbar_init(sf(s), 1);
+      mbar_init(se(s), 2);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(smem_u32(tmem_slot), B.alloc);
+    tmem_relinquish();
+  }
+  for (int l = tid; l < ne; l += BFA_THREADS) dm[l] = P.dofmap[e * ne + l];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 6) {
+    // ---------------- producer of the staged rows of Y (bulk async copies)
+    const uint32_t rowb = (uint32_t)ncv * 4;
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % SY;
+      bool ok = true;
+      if (lane == 0 && i >= SY) ok = mbar_wait(se(s), ((i / SY) - 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok && lane == 0) {
+        atomicExch(&g_tc_status, 35);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (__shfl_sync(0xffffffffu, *(volatile int*)abort_flag, 0)) break;
+      const int l = i * BF_KC + lane;
+      const int g = (lane < BF_KC && l < ne) ? dm[l] : -1;
+      const unsigned vmask = __ballot_sync(0xffffffffu, g >= 0);
+      if (lane == 0) mbar_arrive_expect_tx(sf(s), (uint32_t)__popc(vmask) * rowb);
+      __syncwarp();
+      if (g >= 0)
+        bulk_g2s(gbase + s * BFA_SLOT + lane * BFA_ROWB, P.Yin + (int64_t)g * P.ld_in + c0, rowb, sf(s));
+      ++issued;
+    }
+    if (lane == 0 && *(volatile int*)abort_flag)   // let the copies in flight land before exit
+      for (int i = max(0, issued - SY); i < issued; ++i) mbar_wait(sf(i % SY), (i / SY) & 1);
+  } else if (warp == 4) {
+    // ---------------- producer of the cell-matrix chunks (as tc_cell_bf16_kernel)
+    if (lane == 0) {
+      const int64_t term_bytes = (int64_t)P.mt * 4096;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * 3 * term_bytes + (int64_t)r0 * 32;
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ST;
+        if (i >= ST && !mbar_wait(em(s), ((i / ST) - 1) & 1)) {
+          atomicExch(&g_tc_status, 31);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        const uint32_t dst = sbase + s * stage_bytes + BF_YT;
+        mbar_arrive_expect_tx(fa(s), 3 * hrow);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * 3 + p) * term_bytes, hrow, fa(s));
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag)
+        for (int i = max(0, issued - ST); i < issued; ++i) mbar_wait(fa(i % ST), (i / ST) & 1);
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer (as tc_cell_bf16_kernel)
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, B.nh);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % ST;
+        if (!mbar_wait(fa(s), (i / ST) & 1) || !mbar_wait(fy(s), (i / ST) & 1) ||
+            *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 32);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sy = sbase + s * stage_bytes;
+        const uint32_t sh = sy + BF_YT;
+        uint64_t y[3], hd[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          y[p] = umma_desc(sy + p * 4096, 128, 256);
+          hd[p] = umma_desc(sh + p * hrow, 128, 256);
+        }
+        mma_f16(tmem, y[0], hd[2], idesc, i > 0);
+        mma_f16(tmem, y[1], hd[1], idesc, 1);
+        mma_f16(tmem, y[2], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[1], idesc, 1);
+        mma_f16(tmem, y[1], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[0], idesc, 1);
+        umma_commit(em(s));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    // ---------------- warps 0-3: split staged chunks into the three bf16 terms.
+    // Pair (warp >> 1) takes chunks pair, pair + 2, ...; warp half q takes rows
+    // 16 i + 8 q + a (a < 8), lane the columns lane + 32 u (u < 4), exactly as
+    // the register gather, so the terms are the same bits.
+    const int pair = warp >> 1, q = warp & 1;
+    for (int i = pair; i < nk; i += 2) {
+      const int s = i % ST, sl = i % SY;
+      bool ok = mbar_wait(sf(sl), (i / SY) & 1);
+      if (ok && i >= ST) ok = mbar_wait(em(s), ((i / ST) - 1) & 1);
+      if (!ok) {
+        atomicExch(&g_tc_status, 33);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      const float* rows = reinterpret_cast<const float*>(stg + sl * BFA_SLOT);
+      float v[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int r = q * 8 + a;
+        const int l = i * BF_KC + r;
+        const int g = l < ne ? dm[l] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = lane + 32 * u;
+          v[a][u] = (g >= 0 && c < ncv) ? rows[r * 128 + c] : 0.f;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(se(sl));      // the staged rows are in registers: free the slot
+      uint16_t* ys = reinterpret_cast<uint16_t*>(smem + s * stage_bytes);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = bf_elem_off(lane + 32 * u, q * 8);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int a = 0; a < 8; a += 2) {
+          uint16_t lo1, lo2, lo3, hi1, hi2, hi3;
+          bf16_split3f(v[a][u], lo1, lo2, lo3);
+          bf16_split3f(v[a + 1][u], hi1, hi2, hi3);
+          w[0][a / 2] = (uint32_t)lo1 | ((uint32_t)hi1 << 16);
+          w[1][a / 2] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
+          w[2][a / 2] = (uint32_t)lo3 | ((uint32_t)hi3 << 16);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(fy(s));
+    }
+    // epilogue (as tc_cell_bf16_kernel)
+    const bool okacc = mbar_wait(accb, 0);
+    if (!okacc) {
+      atomicExch(&g_tc_status, 34);
+      *(volatile int*)abort_flag = 1;
+    }
+    tc_fence_after();
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    const int c = warp * 32 + lane;
+    float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    for (int cb = 0; cb < B.nh; cb += 16) {
+      float acc[16];
+      __syncwarp();
+      if (run) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+        tmem_wait_ld();
+      }
+      if (!run || c >= ncv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = acc[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) tmem_dealloc(tmem, B.alloc);
+}
+
+bool tc_cell_bf16_async_ok(const TcApplyArgs& a) {
+  return ((reinterpret_cast<uintptr_t>(a.Yin) & 15) == 0) && (a.ld_in % 4 == 0) && (a.ncol % 4 == 0);
+}
+
 cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.bf) return cudaErrorInvalidValue;
@@ -726,12 +979,18 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
+  const bool async = a.gather == 1 && tc_cell_bf16_async_ok(a);
+  const BfaPlan BA = bfa_plan(d.ne);
   for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
     P.e_off = e0;
     dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
     note_launch();
-    tc_cell_bf16_kernel<<<grid, CELL_THREADS, B.total, s>>>(P);
+    if (async)
+      tc_cell_bf16_async_kernel<<<grid, BFA_THREADS, BA.total, s>>>(P);
+    else
+      tc_cell_bf16_kernel<<<grid, CELL_THREADS, B.total, s>>>(P);
   }
   return cudaGetLastError();
 }
