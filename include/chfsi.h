@@ -142,11 +142,13 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
  * do not depend on it. */
 chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
 
-/* Gather of the BF16x3 cell kernel: 1 (default) = the cell's rows of Y are
- * staged in shared memory by bulk async copies, several K-chunks ahead of the
- * tensor-core products (used when the block is 16-byte aligned with a
- * leading dimension and a column count that are multiples of 4); 0 = warps
- * load the rows into registers.  Results are bit-identical. */
+/* Gather of the BF16x3 cell kernel: 0 (default) = warps load the cell's rows
+ * of Y into registers, two K-chunks in flight per thread block; 1 = the rows
+ * are staged in shared memory by bulk async copies, several K-chunks ahead of
+ * the tensor-core products (used when the block is 16-byte aligned with a
+ * leading dimension and a column count that are multiples of 4, else the
+ * register loads).  Results are bit-identical; on the 16^3-cell p = 6
+ * workload the staged form measured 3% slower, so it is not the default. */
 chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode);
 
 /* Cell operator of the binary64 path (every CHFSI_FP64 apply, and the
@@ -155,7 +157,8 @@ chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode);
  * Sec. 3.3.1); 1 = matrix-free, H_e applied by sum factorisation over the
  * tensor-product cell (1-D mass / stiffness / Gauss-point factors, the
  * alternative the paper notes for the cell-level products), 3.2x (p = 6) to
- * 5.5x (p = 8) fewer flops; -1 = the library's default.  The matrix-free form
+ * 5.5x (p = 8) fewer flops; -1 = the library's default: matrix-free where it
+ * exists, else the cell matrices.  The matrix-free form
  * needs 2 <= p <= 8 and quad_points = p + 2 (CHFSI_ERR_ARG otherwise).  Both
  * give the same operator to rounding.  chfsi_fp64_operator returns the one in
  * use (0 or 1). */

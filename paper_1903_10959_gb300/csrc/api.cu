@@ -134,7 +134,7 @@ int split3_of(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_
 constexpr int kStage64 = 512;
 // Whether the binary64 path uses the matrix-free cell apply when the context
 // leaves the choice open (chfsi_set_fp64_operator(-1)).
-constexpr bool kMatrixFreeDefault = false;
+constexpr bool kMatrixFreeDefault = true;
 // Free the per-call scratch that grows with the column block (filter, cell
 // blocks, projector and binary64 staging buffers); later calls regrow it.
 void release_scratch(chfsi_ctx* ctx) {

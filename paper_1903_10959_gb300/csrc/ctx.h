@@ -23,7 +23,7 @@ struct chfsi_ctx {
   std::string err;
   int filter_block = 200, diag_block = 1;
   int cell_tile = 64;              // columns per CTA of the tensor-core cell kernel
-  int cell_gather = 1;             // BF16x3 cell kernel: 1 async bulk-copy gather, 0 register loads
+  int cell_gather = 0;             // BF16x3 cell kernel: 0 register loads, 1 async bulk-copy gather
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices

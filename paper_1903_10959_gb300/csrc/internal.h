@@ -144,6 +144,7 @@ struct MfLaunch {
   int64_t ncells_colour;
   int p, q, ncol;
   int64_t ld_in, ld_out, ld_prev, ld_w;
+  int kinetic_only;           // 1: 1/2 K_e only (the scaled stiffness of the Poisson solve)
 };
 bool mf_supported(int p, int q);
 cudaError_t launch_mf_cell_fp64(const MfLaunch& L, const double* Yin, double* Yout,

@@ -200,21 +200,25 @@ __global__ void __launch_bounds__(256) mf_cell_fp64_kernel(MfLaunch P, const dou
   __syncthreads();
   kinetic_x<N1, T>(b3, kb, b1, Ax, Sx);
   __syncthreads();
-  // potential part
-  contract<N1, Q, T>(u, b2, Bq, nullptr, nullptr, 2, N1, N1, N1);    // (N1, N1, Q)
-  __syncthreads();
-  contract<N1, Q, T>(b2, b3, Bq, nullptr, nullptr, 1, N1, N1, Q);    // (N1, Q, Q)
-  __syncthreads();
-  contract<N1, Q, T>(b3, b2, Bq, nullptr, nullptr, 0, N1, Q, Q);     // (Q, Q, Q)
-  __syncthreads();
-  const double* wv = P.wv + e * (int64_t)NQ;
-  for (int idx = threadIdx.x; idx < NQ * T; idx += blockDim.x) b2[idx] *= __ldg(wv + idx / T);
-  __syncthreads();
-  contract<Q, N1, T>(b2, b3, Bt, nullptr, nullptr, 0, Q, Q, Q);      // (N1, Q, Q)
-  __syncthreads();
-  contract<Q, N1, T>(b3, b2, Bt, nullptr, nullptr, 1, N1, Q, Q);     // (N1, N1, Q)
-  __syncthreads();
-  contract<Q, N1, T>(b2, kb, Bt, nullptr, nullptr, 2, N1, N1, Q);    // (N1, N1, N1)
+  // potential part (skipped for the stiffness operator alone)
+  if (P.kinetic_only) {
+    for (int idx = threadIdx.x; idx < NE * T; idx += blockDim.x) kb[idx] = 0.0;
+  } else {
+    contract<N1, Q, T>(u, b2, Bq, nullptr, nullptr, 2, N1, N1, N1);    // (N1, N1, Q)
+    __syncthreads();
+    contract<N1, Q, T>(b2, b3, Bq, nullptr, nullptr, 1, N1, N1, Q);    // (N1, Q, Q)
+    __syncthreads();
+    contract<N1, Q, T>(b3, b2, Bq, nullptr, nullptr, 0, N1, Q, Q);     // (Q, Q, Q)
+    __syncthreads();
+    const double* wv = P.wv + e * (int64_t)NQ;
+    for (int idx = threadIdx.x; idx < NQ * T; idx += blockDim.x) b2[idx] *= __ldg(wv + idx / T);
+    __syncthreads();
+    contract<Q, N1, T>(b2, b3, Bt, nullptr, nullptr, 0, Q, Q, Q);      // (N1, Q, Q)
+    __syncthreads();
+    contract<Q, N1, T>(b3, b2, Bt, nullptr, nullptr, 1, N1, Q, Q);     // (N1, N1, Q)
+    __syncthreads();
+    contract<Q, N1, T>(b2, kb, Bt, nullptr, nullptr, 2, N1, N1, Q);    // (N1, N1, N1)
+  }
   __syncthreads();
   // r = M^{-1/2} (1/2 kin + pot); node-mode assembly fused with the update
   for (int idx = threadIdx.x; idx < NE * T; idx += blockDim.x) {

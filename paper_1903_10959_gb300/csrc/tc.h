@@ -33,7 +33,7 @@ struct TcApplyArgs {
   float* R;                 // ncells * ne * ncol scratch
   int split3;
   int tile = 64;            // columns per CTA of the cell kernel: 64 or 128
-  int gather = 1;           // BF16x3: 1 = rows staged by bulk async copies (when aligned), 0 = register loads
+  int gather = 0;           // BF16x3: 0 = register loads, 1 = rows staged by bulk async copies (when aligned)
 };
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
 
