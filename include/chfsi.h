@@ -380,6 +380,67 @@ chfsi_status chfsi_kernel_timings(chfsi_ctx* ctx, double* out6);
  * monotonic counter for accounting, e.g. launches per ChFSI iteration). */
 int64_t      chfsi_kernel_launches(void);
 
+/* ------------------------------------------------------------------- SCF
+ * The self-consistent field loop around the ChFSI step (Algorithm scf,
+ * Sec. 3.2), for periodic systems of Gaussian nuclear charges, on the device
+ * with the matrix-free binary64 operator (needs 2 <= p <= 8 and
+ * quad_points = p + 2, all three axes periodic). */
+
+/* V_eff at the Gauss points given on the DEVICE (v: ncells * q^3 doubles,
+ * the layout of chfsi_set_potential_qp), taken by the matrix-free operator
+ * directly: the wells and any host values are replaced, the stored cell
+ * matrices are released, and until the next chfsi_build only the binary64
+ * precision is available (the mixed precisions return CHFSI_ERR_STATE).
+ * Projectors set by an earlier chfsi_build stay.  Synchronises. */
+chfsi_status chfsi_set_potential_qp_device(chfsi_ctx* ctx, const double* v);
+
+/* Electrostatic potential (step 4 of Algorithm scf): phi with
+ * -(1 / 4 pi) lap phi = f in the periodic box (Eq. ksproblemPer), in FE form
+ * K phi = 4 pi F, F_j = int N_j f by the cells' Gauss rule, the net charge of
+ * f neutralised by a uniform background, int phi = 0.  f: device, at the
+ * Gauss points (ncells * q^3, chfsi_density layout); phi: device, M nodal
+ * values.  Conjugate gradients on M^{-1/2} K M^{-1/2} (the matrix-free
+ * stiffness) to relative residual tol, at most max_iter iterations;
+ * iters / rel_residual (may be NULL) receive the count and the residual.
+ * CHFSI_ERR_EIG when tol is not reached.  Synchronises. */
+chfsi_status chfsi_poisson(chfsi_ctx* ctx, const double* f, double* phi, double tol, int max_iter,
+                           int* iters, double* rel_residual);
+
+typedef struct {
+  int nnuclei;            /* Gaussian nuclear charges b = -sum Z_I g_I (normalised Gaussians) */
+  const double* xyz;      /* host, 3 * nnuclei centres (bohr)                              */
+  const double* Z;        /* host, nnuclei charges (N_e = sum Z)                            */
+  const double* sigma;    /* host, nnuclei widths (bohr)                                    */
+  int n_states;           /* states in the subspace (columns of X); 2 n_states >= N_e      */
+  double kT;              /* Fermi-Dirac smearing (Ha)                                      */
+  int degree;             /* Chebyshev degree of each ChFSI pass                            */
+  int passes;             /* ChFSI passes per SCF step                                      */
+  double tol;             /* stop when |rho_out - rho|_W < tol (quadrature-weighted L2)     */
+  int max_iter;           /* SCF steps at most                                              */
+  double beta;            /* Anderson mixing: step on the residual                          */
+  int depth;              /* Anderson mixing: history length (1..16)                        */
+  uint64_t seed;          /* start block (chfsi_fill_uniform stream 1) and Lanczos starts   */
+  double poisson_tol;     /* relative residual of the Poisson CG                            */
+  int lanczos_steps;      /* steps of the upper-bound estimate per SCF step                 */
+} chfsi_scf_params;
+
+/* The SCF loop: initial density = the nuclei widened to 1 bohr, scaled to N_e;
+ * per step: phi (chfsi_poisson of rho + b), V_eff = phi + V_x(rho) with the
+ * LDA exchange V_x = -(3 rho / pi)^{1/3} at the Gauss points
+ * (chfsi_set_potential_qp_device), the upper bound (chfsi_bounds), a
+ * Rayleigh-Ritz step and `passes` ChFSI passes on X (binary64, warm-started),
+ * the Fermi level of all states (chfsi_fermi_level, n_oc = 0), the density
+ * (chfsi_density), and n-stage Anderson mixing of rho weighted by the
+ * quadrature weights.  X: device, M x n_states, binary64, caller-owned: filled
+ * with the seeded start, returns the last eigenvectors.  Outputs (host; NULL
+ * allowed except evals_host): rho_host[ncells q^3] the converged density,
+ * evals_host / occ_host[n_states], mu_out, res_hist[max_iter] the residual of
+ * every step, iters_out the steps run.  CHFSI_ERR_EIG when tol is not reached
+ * in max_iter steps (the outputs then hold the last step).  Synchronises. */
+chfsi_status chfsi_scf(chfsi_ctx* ctx, const chfsi_scf_params* prm, double* X, int64_t ldx,
+                       double* rho_host, double* evals_host, double* occ_host, double* mu_out,
+                       double* res_hist, int* iters_out);
+
 /* ---------------------------------------------------------- domain decomposition
  * Partition of the mesh's cells over nranks ranks (the paper's primary level
  * of parallelism, Sec. 3.7: subdomains of the FE mesh on separate tasks; since

@@ -53,6 +53,14 @@ class PartitionInfo(C.Structure):
                 ("nneighbors", C.c_int), ("grid", C.c_int * 3)]
 
 
+class ScfParams(C.Structure):
+    _fields_ = [("nnuclei", C.c_int), ("xyz", C.POINTER(C.c_double)), ("Z", C.POINTER(C.c_double)),
+                ("sigma", C.POINTER(C.c_double)), ("n_states", C.c_int), ("kT", C.c_double),
+                ("degree", C.c_int), ("passes", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("beta", C.c_double), ("depth", C.c_int), ("seed", C.c_uint64),
+                ("poisson_tol", C.c_double), ("lanczos_steps", C.c_int)]
+
+
 class Request(C.Structure):
     _fields_ = [("mesh", MeshDesc), ("n", C.c_int), ("nwells", C.c_int),
                 ("xyz", C.POINTER(C.c_double)), ("depth", C.POINTER(C.c_double)),
@@ -131,6 +139,10 @@ _SIGS = {
     "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_set_potential_qp_device": (C.c_int, [_vp, _vp]),
+    "chfsi_poisson": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]),
+    "chfsi_scf": (C.c_int, [_vp, C.POINTER(ScfParams), _vp, _i64, _dp, _dp, _dp, _dp, _dp,
+                            C.POINTER(C.c_int)]),
     "chfsi_set_fp64_operator": (C.c_int, [_vp, C.c_int]),
     "chfsi_set_cell_gather": (C.c_int, [_vp, C.c_int]),
     "chfsi_fp64_operator": (C.c_int, [_vp]),
@@ -222,6 +234,8 @@ class Context:
             raise ChfsiError(st, "chfsi_create failed")
         self._h = h
         self.ndofs = lib.chfsi_num_dofs(h)
+        self._ncells = int(ncell[0]) * int(ncell[1]) * int(ncell[2])
+        self._q = int(quad_points) if quad_points else int(p) + 2
 
     def _check(self, st):
         if st != 0:
@@ -320,6 +334,43 @@ class Context:
         px, ldx, n = _dev(X, FP64)
         py, ldy, _ = _dev(Y, FP64)
         self._check(self._lib.chfsi_apply_noalloc(self._h, px, ldx, py, ldy, n))
+
+    def set_potential_qp_device(self, v):
+        """V_eff at the Gauss points from a CUDA float64 tensor (ncells * q^3)."""
+        import torch
+        if not isinstance(v, torch.Tensor) or not v.is_cuda or v.dtype != torch.float64 \
+                or not v.is_contiguous():
+            raise TypeError("v: contiguous CUDA float64 tensor")
+        self._check(self._lib.chfsi_set_potential_qp_device(self._h, _vp(v.data_ptr())))
+
+    def poisson(self, f, phi, tol=1e-12, max_iter=20000):
+        """phi (CUDA float64, M) of -(1/4 pi) lap phi = f (CUDA float64 at the Gauss
+        points); returns (CG iterations, relative residual)."""
+        it, rel = C.c_int(0), np.zeros(1)
+        self._check(self._lib.chfsi_poisson(self._h, _vp(f.data_ptr()), _vp(phi.data_ptr()),
+                                            float(tol), int(max_iter), C.byref(it), _ptr(rel)))
+        return it.value, float(rel[0])
+
+    def scf(self, X, centres, Z, sigma, kT=0.01, degree=20, passes=2, tol=1e-9, max_iter=60,
+            beta=0.5, depth=6, seed=1, poisson_tol=1e-13, lanczos_steps=20):
+        """Algorithm scf on a periodic Gaussian-charge system (chfsi_scf); X is a
+        CUDA float64 (M x n_states) work block.  Returns a dict with rho (Gauss
+        points), evals, occ, mu, residuals."""
+        px, ldx, n = _dev(X, FP64)
+        xyz = _host(centres).reshape(-1)
+        z, sg = _host(Z), _host(sigma)
+        prm = ScfParams(int(z.size), _ptr(xyz), _ptr(z), _ptr(sg), int(n), float(kT), int(degree),
+                        int(passes), float(tol), int(max_iter), float(beta), int(depth), int(seed),
+                        float(poisson_tol), int(lanczos_steps))
+        q = self._q
+        rho = np.empty(self._ncells * q ** 3)
+        ev, occ, mu = np.empty(n), np.empty(n), np.zeros(1)
+        hist = np.zeros(max_iter)
+        it = C.c_int(0)
+        self._check(self._lib.chfsi_scf(self._h, C.byref(prm), px, ldx, _ptr(rho), _ptr(ev), _ptr(occ),
+                                        _ptr(mu), _ptr(hist), C.byref(it)))
+        return {"rho": rho, "evals": ev, "occ": occ, "mu": float(mu[0]),
+                "residuals": hist[:it.value].copy(), "iters": it.value}
 
     def set_cell_gather(self, mode):
         """BF16x3 cell kernel gather: "async" (bulk copies) or "registers"."""

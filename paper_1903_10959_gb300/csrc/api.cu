@@ -205,6 +205,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
                                (const double*)ctx->Zb.ptr, ncol, (double*)ctx->NLb.ptr, B, ctx->stream));
     }
     const bool mf = use_matrix_free(ctx);
+    if (!mf && !ctx->d_Ht) return fail(ctx, CHFSI_ERR_STATE, "no cell matrices for the binary64 operator");
     for (int c = 0; c < ncolour; ++c) {
       KTimer kt(ctx, 0);
       if (mf) {
@@ -246,6 +247,9 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     return CHFSI_OK;
   }
   // mixed precisions: binary32 storage, tcgen05 TF32 (or BF16x3) cell products
+  if (!ctx->d_Ht)
+    return fail(ctx, CHFSI_ERR_STATE, "no cell matrices: the potential was set on the device "
+                                      "(binary64 only until chfsi_build)");
   const bool bf16 = prec == CHFSI_MIXED_BF16X3;
   if (bf16 && !ctx->tc.bf) {
     cudaError_t pe = tc_pack_bf16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
@@ -741,7 +745,8 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
   release(ctx, ctx->d_msq, m.mass.size() * 8);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
-                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol})
+                    &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
+                    &ctx->scfr, &ctx->scfw})
     dfree(ctx, b->ptr, b->bytes);
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)
@@ -1012,6 +1017,7 @@ chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, d
   if (st != CHFSI_OK) return st;
   if (ncol > 0 && (!Y || ldy < ncol)) return fail(ctx, CHFSI_ERR_ARG, "bad Y / ldy");
   if (ncol == 0) return CHFSI_OK;
+  if (!ctx->d_Ht) return fail(ctx, CHFSI_ERR_STATE, "no cell matrices: the potential was set on the device");
   const HostMesh& m = ctx->mesh;
   const int nsite = ctx->hproj.nsite;
   const size_t w_bytes = (size_t)m.ndofs * ncol * sizeof(double);

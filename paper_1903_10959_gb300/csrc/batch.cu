@@ -542,7 +542,7 @@ chfsi_status bfail(chfsi_batch* b, chfsi_status st, const std::string& m) {
 chfsi_status batch_check(chfsi_batch* b, float* const* X, const int64_t* ldx, const int* ncol) {
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     const chfsi_ctx* c = b->ctx[i];
-    if (!c->built || c->hproj.nsite > 0 || c->latched != CHFSI_OK)
+    if (!c->built || !c->d_Ht || c->hproj.nsite > 0 || c->latched != CHFSI_OK)
       return bfail(b, CHFSI_ERR_STATE, "system " + std::to_string(i) +
                                            " is not built, has projectors or has a latched error");
     if (!X || !X[i] || !ldx || !ncol || ncol[i] < 1 || ldx[i] < ncol[i])
@@ -609,7 +609,7 @@ chfsi_status chfsi_batch_create(int n, chfsi_ctx* const* ctxs, void* stream, chf
   *out = nullptr;
   const int p = ctxs[0] ? ctxs[0]->mesh.p : -1;
   for (int i = 0; i < n; ++i)
-    if (!ctxs[i] || !ctxs[i]->built || ctxs[i]->mesh.p != p || ctxs[i]->hproj.nsite > 0)
+    if (!ctxs[i] || !ctxs[i]->built || !ctxs[i]->d_Ht || ctxs[i]->mesh.p != p || ctxs[i]->hproj.nsite > 0)
       return CHFSI_ERR_ARG;
   chfsi_batch* b = new chfsi_batch();
   b->ctx.assign(ctxs, ctxs + n);

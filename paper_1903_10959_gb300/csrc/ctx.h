@@ -51,6 +51,9 @@ struct chfsi_ctx {
   // grown scratch
   chfsi::DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
   chfsi::DevBuf pol;               // binary64 staging block of the polish
+  chfsi::DevBuf scfb, scfq, scfr, scfw;   // Poisson / SCF work arrays (scf.cu)
+  bool scf_setup = false;          // scfb holds the load of 1 and the weights
+  double scf_msum = 0.0;           // sum_j int N_j (the box volume)
   chfsi::DevBuf Db;                // density tables: M^{-1/2}, basis at Gauss points, weights
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
