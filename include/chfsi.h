@@ -441,6 +441,35 @@ chfsi_status chfsi_scf(chfsi_ctx* ctx, const chfsi_scf_params* prm, double* X, i
                        double* rho_host, double* evals_host, double* occ_host, double* mu_out,
                        double* res_hist, int* iters_out);
 
+/* -------------------------------------------------------------- k-points
+ * Bloch states of a periodic crystal at wavevector k (Eq. evp of the periodic
+ * problem, Sec. 2.1): the cell-periodic part u solves
+ * (-1/2 lap - i k.grad + 1/2 |k|^2 + V) u = eps u, in FE form per cell
+ * H_e(k) = 1/2 K_e - i k.G_e + 1/2 |k|^2 A_e + V_e (G^(d)_jl = int N_j d_d N_l,
+ * A_e the consistent mass, the cell's Gauss rule), and H~(k) = M^{-1/2} H(k)
+ * M^{-1/2} is complex Hermitian.  Applied matrix-free in binary64 (needs a
+ * periodic box, 2 <= p <= 8, quad_points = p + 2, a built context or a device
+ * potential, and no projectors: their Bloch phases are not modelled).
+ * Complex blocks are binary64 (real, imaginary) column pairs: vector v at
+ * unknown j is X[j ldx + 2 v] + i X[j ldx + 2 v + 1]; ldx counts doubles
+ * (>= 2 n).  The real entry points above are unaffected. */
+
+/* Set k (bohr^-1, three components) for the k-point entry points below. */
+chfsi_status chfsi_set_kpoint(chfsi_ctx* ctx, const double* k);
+/* Y = H~(k) X on n complex vectors (X, Y: device, must not overlap). */
+chfsi_status chfsi_apply_kpoint(chfsi_ctx* ctx, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                                int n);
+/* Upper bound of spec(H~(k)) by k-step Lanczos (as chfsi_bounds) on the real
+ * 2M-dimensional form of H~(k), which has the same spectrum. */
+chfsi_status chfsi_bounds_kpoint(chfsi_ctx* ctx, int lanczos_steps, uint64_t seed, double* b_out);
+/* ChFSI at k (as chfsi_solve, binary64, fixed iteration count): CholGS + RR
+ * on the start block, then `iters` x {filter, CholGS, RR}.  CholGS:
+ * S = X^H X = L L^H (cuSOLVER zpotrf), L^{-1} (ztrtri), X <- X L^{-H}; RR:
+ * H^ = X^H H~(k) X, zheevd (ascending), X <- X Q.  evals_host[n] receives
+ * the Ritz values.  Synchronises. */
+chfsi_status chfsi_solve_kpoint(chfsi_ctx* ctx, double* X, int64_t ldx, int n, int iters, int degree,
+                                double b, double* evals_host);
+
 /* ---------------------------------------------------------- domain decomposition
  * Partition of the mesh's cells over nranks ranks (the paper's primary level
  * of parallelism, Sec. 3.7: subdomains of the FE mesh on separate tasks; since

@@ -139,6 +139,10 @@ _SIGS = {
     "chfsi_server_estimate": (C.c_size_t, [C.POINTER(Request)]),
     "chfsi_server_destroy": (C.c_int, [_vp]),
     "chfsi_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
+    "chfsi_set_kpoint": (C.c_int, [_vp, _dp]),
+    "chfsi_apply_kpoint": (C.c_int, [_vp, _vp, _i64, _vp, _i64, C.c_int]),
+    "chfsi_bounds_kpoint": (C.c_int, [_vp, C.c_int, C.c_uint64, _dp]),
+    "chfsi_solve_kpoint": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.c_int, C.c_double, _dp]),
     "chfsi_set_potential_qp_device": (C.c_int, [_vp, _vp]),
     "chfsi_poisson": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), _dp]),
     "chfsi_scf": (C.c_int, [_vp, C.POINTER(ScfParams), _vp, _i64, _dp, _dp, _dp, _dp, _dp,
@@ -371,6 +375,39 @@ class Context:
                                         _ptr(mu), _ptr(hist), C.byref(it)))
         return {"rho": rho, "evals": ev, "occ": occ, "mu": float(mu[0]),
                 "residuals": hist[:it.value].copy(), "iters": it.value}
+
+    # ------------------------------------------------------------ k-points
+    @staticmethod
+    def _cdev(t):
+        """(pointer, ld in doubles, n complex vectors) of a CUDA complex128 tensor (M x n)."""
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128 \
+                or t.dim() != 2 or t.stride(1) != 1:
+            raise TypeError("k-point blocks: 2-D CUDA complex128 tensors with unit column stride")
+        return t.data_ptr(), 2 * t.stride(0), t.shape[1]
+
+    def set_kpoint(self, k):
+        kk = _host(k, 3)
+        self._check(self._lib.chfsi_set_kpoint(self._h, _ptr(kk)))
+
+    def apply_kpoint(self, X, Y):
+        px, ldx, n = self._cdev(X)
+        py, ldy, n2 = self._cdev(Y)
+        if n2 != n:
+            raise ValueError("X and Y need the same number of columns")
+        self._check(self._lib.chfsi_apply_kpoint(self._h, px, ldx, py, ldy, n))
+
+    def bounds_kpoint(self, steps=20, seed=1) -> float:
+        b = np.zeros(1)
+        self._check(self._lib.chfsi_bounds_kpoint(self._h, int(steps), int(seed), _ptr(b)))
+        return float(b[0])
+
+    def solve_kpoint(self, X, iters, degree, b):
+        px, ldx, n = self._cdev(X)
+        ev = np.empty(n)
+        self._check(self._lib.chfsi_solve_kpoint(self._h, px, ldx, n, int(iters), int(degree), float(b),
+                                                 _ptr(ev)))
+        return ev
 
     def set_cell_gather(self, mode):
         """BF16x3 cell kernel gather: "async" (bulk copies) or "registers"."""

@@ -22,7 +22,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["kernels_fp64.cu", "kernels_tc.cu", "kernels_mf.cu", "api.cu", "batch.cu", "server.cu",
-                "density.cu", "scf.cu"]
+                "density.cu", "scf.cu", "kpoint.cu"]
 CXX_SOURCES = ["mesh.cpp", "partition.cpp"]
 
 

@@ -744,9 +744,12 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_node_ptr, m.node_ptr.size() * 4);
   release(ctx, ctx->d_node_ent, m.node_ent.size() * 4);
   release(ctx, ctx->d_msq, m.mass.size() * 8);
+  if (ctx->d_kfac) cudaFree(ctx->d_kfac);
+  ctx->d_kfac = nullptr;
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
-                    &ctx->scfr, &ctx->scfw})
+                    &ctx->scfr, &ctx->scfw, &ctx->kW, &ctx->kT1, &ctx->kG, &ctx->kS, &ctx->kwork,
+                    &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)

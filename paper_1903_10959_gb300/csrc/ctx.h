@@ -52,6 +52,10 @@ struct chfsi_ctx {
   chfsi::DevBuf T1, Wb, NLb, Zb, rot, Ssq, work, part, vec, lam, Rb;
   chfsi::DevBuf pol;               // binary64 staging block of the polish
   chfsi::DevBuf scfb, scfq, scfr, scfw;   // Poisson / SCF work arrays (scf.cu)
+  chfsi::DevBuf kW, kT1, kG, kS, kwork, kY, kvec;   // Bloch (k-point) work arrays (kpoint.cu)
+  double kpt[3] = {0, 0, 0};       // Bloch wavevector of the k-point entry points
+  bool kset = false;
+  double* d_kfac = nullptr;        // k-point factors of the matrix-free Bloch apply
   bool scf_setup = false;          // scfb holds the load of 1 and the weights
   double scf_msum = 0.0;           // sum_j int N_j (the box volume)
   chfsi::DevBuf Db;                // density tables: M^{-1/2}, basis at Gauss points, weights

@@ -147,6 +147,10 @@ struct MfLaunch {
   int kinetic_only;           // 1: 1/2 K_e only (the scaled stiffness of the Poisson solve)
 };
 bool mf_supported(int p, int q);
+// Bloch (k-point) form of the same apply on interleaved (real, imaginary)
+// column pairs; L.fac holds the k-point factors (see kernels_mf.cu), ncol even.
+cudaError_t launch_mfk_cell_fp64(const MfLaunch& L, const double* Yin, double* Yout,
+                                 const double* Yprev, double* W, FilterStep st, cudaStream_t s);
 cudaError_t launch_mf_cell_fp64(const MfLaunch& L, const double* Yin, double* Yout,
                                 const double* Yprev, double* W, const double* NL, FilterStep st,
                                 cudaStream_t s);

@@ -24,6 +24,8 @@
 
 namespace chfsi {
 
+bool mf_supported(int p, int q);
+
 namespace {
 
 // Contract one axis of `in` (dims d0 (x) x d1 (y) x d2 (z), columns fastest,
@@ -239,6 +241,261 @@ __global__ void __launch_bounds__(256) mf_cell_fp64_kernel(MfLaunch P, const dou
       if (Yprev) out = fma(beta, Yprev[g * P.ld_prev + cc], out);
       Yout[g * P.ld_out + cc] = out;
     }
+  }
+}
+
+// ---------------------------------------------------------------- Bloch (k-point) variant
+// H_e(k) = 1/2 K_e - i k.G_e + 1/2 |k|^2 A_e + V_e (Eq. evp of the periodic
+// problem, the cell-periodic part of a Bloch state) on a complex block stored
+// as interleaved (real, imaginary) column pairs.  With T = 1/2 K + 1/2 |k|^2 A
+// + V and G = k.G_e (real, cell-independent):
+//   Re(H u) = T u_r + G u_i,   Im(H u) = T u_i - G u_r.
+// 1/2 |k|^2 A folds into the kinetic x pass (S_x + |k|^2 A_x); G has the
+// kinetic part's structure with the stiffness replaced by the 1-D derivative
+// matrix C_il = int l_i l_l' (no Jacobian), scaled by k per axis:
+//   G u = (k_x C_x) A_y A_z u + A_x (k_y C_y) A_z u + A_x A_y (k_z C_z) u.
+// Factors: A_x, A_y, A_z, S'_x = S_x + |k|^2 A_x, S_y, S_z, B, B^T, k_x C, k_y C, k_z C.
+__host__ __device__ constexpr int mfk_fac_doubles(int n1, int q) { return 9 * n1 * n1 + 2 * q * n1; }
+__host__ __device__ constexpr size_t mfk_smem_bytes(int n1, int q, int t) {
+  return sizeof(double) *
+         ((size_t)((mfk_fac_doubles(n1, q) + 1) & ~1) + (size_t)n1 * n1 * n1 +
+          5 * (size_t)n1 * n1 * n1 * t + 3 * (size_t)(q * q * q > n1 * n1 * n1 ? q * q * q : n1 * n1 * n1) * t);
+}
+
+// z pass of three matrices on the same pencils: out_m = M_m u along z.
+template <int N1, int T>
+__device__ __forceinline__ void z_pass3(const double* u, double* o1, double* o2, double* o3,
+                                        const double* M1, const double* M2, const double* M3) {
+  const int npen = N1 * N1 * T;
+  const int st = N1 * N1 * T;
+  for (int pid = threadIdx.x; pid < npen; pid += blockDim.x) {
+    const int c = pid % T, r = pid / T;            // r = x + N1 y
+    const int b0 = r * T + c;
+    double v[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[i] = u[b0 + i * st];
+#pragma unroll 1
+    for (int o = 0; o < N1; ++o) {
+      double a = 0.0, s = 0.0, g = 0.0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        a = fma(M1[o * N1 + i], v[i], a);
+        s = fma(M2[o * N1 + i], v[i], s);
+        g = fma(M3[o * N1 + i], v[i], g);
+      }
+      o1[b0 + o * st] = a;
+      o2[b0 + o * st] = s;
+      o3[b0 + o * st] = g;
+    }
+  }
+}
+
+// y pass: ayaz = A_y az, t = S_y az + A_y sz, gt = Cy az + A_y cz.
+template <int N1, int T>
+__device__ __forceinline__ void y_pass3(const double* az, const double* sz, const double* cz,
+                                        double* ayaz, double* t, double* gt, const double* Ay,
+                                        const double* Sy, const double* Cy) {
+  const int npen = N1 * N1 * T;
+  const int st = N1 * T;
+  for (int pid = threadIdx.x; pid < npen; pid += blockDim.x) {
+    const int c = pid % T, r = pid / T;
+    const int x = r % N1, z = r / N1;
+    const int b0 = (z * N1 * N1 + x) * T + c;
+    double a[N1], s[N1], g[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      a[i] = az[b0 + i * st];
+      s[i] = sz[b0 + i * st];
+      g[i] = cz[b0 + i * st];
+    }
+#pragma unroll 1
+    for (int o = 0; o < N1; ++o) {
+      double u = 0.0, w = 0.0, h = 0.0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        u = fma(Ay[o * N1 + i], a[i], u);
+        w = fma(Sy[o * N1 + i], a[i], w);
+        w = fma(Ay[o * N1 + i], s[i], w);
+        h = fma(Cy[o * N1 + i], a[i], h);
+        h = fma(Ay[o * N1 + i], g[i], h);
+      }
+      ayaz[b0 + o * st] = u;
+      t[b0 + o * st] = w;
+      gt[b0 + o * st] = h;
+    }
+  }
+}
+
+// x pass: kin = S'_x ayaz + A_x t, g = Cx ayaz + A_x gt.
+template <int N1, int T>
+__device__ __forceinline__ void x_pass2(const double* ayaz, const double* t, const double* gt,
+                                        double* kin, double* g, const double* Ax, const double* Sx,
+                                        const double* Cx) {
+  const int npen = N1 * N1 * T;
+  for (int pid = threadIdx.x; pid < npen; pid += blockDim.x) {
+    const int c = pid % T, r = pid / T;
+    const int b0 = r * N1 * T + c;
+    double a[N1], s[N1], h[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      a[i] = ayaz[b0 + i * T];
+      s[i] = t[b0 + i * T];
+      h[i] = gt[b0 + i * T];
+    }
+#pragma unroll 1
+    for (int o = 0; o < N1; ++o) {
+      double u = 0.0, w = 0.0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        u = fma(Sx[o * N1 + i], a[i], u);
+        u = fma(Ax[o * N1 + i], s[i], u);
+        w = fma(Cx[o * N1 + i], a[i], w);
+        w = fma(Ax[o * N1 + i], h[i], w);
+      }
+      kin[b0 + o * T] = u;
+      g[b0 + o * T] = w;
+    }
+  }
+}
+
+// Columns come in (real, imaginary) pairs; T is even and c0 is even.
+template <int N1, int Q, int T>
+__global__ void __launch_bounds__(256) mfk_cell_fp64_kernel(MfLaunch P, const double* __restrict__ Yin,
+                                                           double* Yout, const double* Yprev,
+                                                           double* W, double alpha, double beta,
+                                                           double shift) {
+  static_assert(T % 2 == 0, "column pairs");
+  constexpr int NE = N1 * N1 * N1, NQ = Q * Q * Q;
+  constexpr int NF = mfk_fac_doubles(N1, Q);
+  constexpr int BIG = (NQ > NE ? NQ : NE) * T;
+  extern __shared__ double sm[];
+  double* fac = sm;
+  double* sv = fac + ((NF + 1) & ~1);
+  double* raw = sv + NE;
+  double* u = raw + NE * T;
+  double* kb = u + NE * T;
+  double* x2 = kb + NE * T;
+  double* x3 = x2 + NE * T;
+  double* b1 = x3 + NE * T;
+  double* b2 = b1 + BIG;
+  double* b3 = b2 + BIG;
+  const int64_t e = P.cells[blockIdx.x];
+  const int c0 = blockIdx.y * T;
+  const int ncv = min(T, P.ncol - c0);
+  const int32_t* dm = P.dofmap + e * NE;
+  const uint8_t* md = P.modes + e * NE;
+  for (int i = threadIdx.x; i < NF; i += blockDim.x) fac[i] = P.fac[i];
+  for (int l = threadIdx.x; l < NE; l += blockDim.x) {
+    const int g = dm[l];
+    sv[l] = g >= 0 ? P.minv_sqrt[g] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < NE * T; idx += blockDim.x) {
+    const int l = idx / T, c = idx - l * T;
+    const int g = dm[l];
+    raw[idx] = (g >= 0 && c < ncv) ? Yin[(int64_t)g * P.ld_in + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NE * T; idx += blockDim.x) u[idx] = raw[idx] * sv[idx / T];
+  __syncthreads();
+  const double* Ax = fac;
+  const double* Ay = fac + N1 * N1;
+  const double* Az = fac + 2 * N1 * N1;
+  const double* Sx = fac + 3 * N1 * N1;
+  const double* Sy = fac + 4 * N1 * N1;
+  const double* Sz = fac + 5 * N1 * N1;
+  const double* Bq = fac + 6 * N1 * N1;
+  const double* Bt = Bq + Q * N1;
+  const double* Cx = Bt + Q * N1;
+  const double* Cy = Cx + N1 * N1;
+  const double* Cz = Cy + N1 * N1;
+  // potential first (into kb), using b2 / b3
+  contract<N1, Q, T>(u, b2, Bq, nullptr, nullptr, 2, N1, N1, N1);
+  __syncthreads();
+  contract<N1, Q, T>(b2, b3, Bq, nullptr, nullptr, 1, N1, N1, Q);
+  __syncthreads();
+  contract<N1, Q, T>(b3, b2, Bq, nullptr, nullptr, 0, N1, Q, Q);
+  __syncthreads();
+  {
+    const double* wv = P.wv + e * (int64_t)NQ;
+    for (int idx = threadIdx.x; idx < NQ * T; idx += blockDim.x) b2[idx] *= __ldg(wv + idx / T);
+  }
+  __syncthreads();
+  contract<Q, N1, T>(b2, b3, Bt, nullptr, nullptr, 0, Q, Q, Q);
+  __syncthreads();
+  contract<Q, N1, T>(b3, b2, Bt, nullptr, nullptr, 1, N1, Q, Q);
+  __syncthreads();
+  contract<Q, N1, T>(b2, kb, Bt, nullptr, nullptr, 2, N1, N1, Q);
+  __syncthreads();
+  // kinetic + mass + gradient parts
+  z_pass3<N1, T>(u, b1, b2, b3, Az, Sz, Cz);                 // az, sz, cz
+  __syncthreads();
+  y_pass3<N1, T>(b1, b2, b3, u, x2, x3, Ay, Sy, Cy);          // ayaz (u), t (x2), gt (x3)
+  __syncthreads();
+  x_pass2<N1, T>(u, x2, x3, b1, b2, Ax, Sx, Cx);              // kin (b1), g (b2)
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NE * T; idx += blockDim.x) {
+    const int l = idx / T, c = idx - l * T;
+    const uint8_t mode = md[l];
+    if (mode == MODE_SKIP || c >= ncv) continue;
+    const bool im = (c & 1) != 0;
+    const double gpart = im ? -b2[idx - 1] : b2[idx + 1];     // Re: + G u_i; Im: - G u_r
+    double v = sv[l] * (fma(0.5, b1[idx], kb[idx]) + gpart);
+    const int64_t g = dm[l];
+    const int cc = c0 + c;
+    if (mode == MODE_STORE) {
+      W[g * P.ld_w + cc] = v;
+    } else if (mode == MODE_ACCUM) {
+      W[g * P.ld_w + cc] += v;
+    } else {
+      if (mode == MODE_FINAL) v += W[g * P.ld_w + cc];
+      double out = alpha * (v - shift * raw[idx]);
+      if (Yprev) out = fma(beta, Yprev[g * P.ld_prev + cc], out);
+      Yout[g * P.ld_out + cc] = out;
+    }
+  }
+}
+
+namespace {
+template <int N1, int T>
+cudaError_t mfk_launch_t(const MfLaunch& L, const double* Yin, double* Yout, const double* Yprev,
+                         double* W, FilterStep st, cudaStream_t s) {
+  constexpr int Q = N1 + 1;
+  constexpr size_t smem = mfk_smem_bytes(N1, Q, T);
+  static_assert(smem <= 227 * 1024, "k-point cell kernel: shared memory");
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(mfk_cell_fp64_kernel<N1, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  });
+  dim3 grid((unsigned)L.ncells_colour, (unsigned)((L.ncol + T - 1) / T));
+  note_launch();
+  mfk_cell_fp64_kernel<N1, Q, T><<<grid, 256, smem, s>>>(L, Yin, Yout, Yprev, W, st.alpha, st.beta,
+                                                          st.shift);
+  return cudaGetLastError();
+}
+template <int N1>
+cudaError_t mfk_launch_p(const MfLaunch& L, const double* Yin, double* Yout, const double* Yprev,
+                         double* W, FilterStep st, cudaStream_t s) {
+  constexpr int Q = N1 + 1;
+  if (L.ncol >= 4 && mfk_smem_bytes(N1, Q, 4) <= 110 * 1024)
+    return mfk_launch_t<N1, (mfk_smem_bytes(N1, Q, 4) <= 110 * 1024 ? 4 : 2)>(L, Yin, Yout, Yprev, W, st, s);
+  return mfk_launch_t<N1, 2>(L, Yin, Yout, Yprev, W, st, s);
+}
+}  // namespace
+
+cudaError_t launch_mfk_cell_fp64(const MfLaunch& L, const double* Yin, double* Yout,
+                                 const double* Yprev, double* W, FilterStep st, cudaStream_t s) {
+  if (L.ncells_colour == 0 || L.ncol == 0) return cudaSuccess;
+  if (!mf_supported(L.p, L.q) || (L.ncol & 1)) return cudaErrorInvalidValue;
+  const double* prev = st.beta != 0.0 ? Yprev : nullptr;
+  switch (L.p) {
+    case 2: return mfk_launch_p<3>(L, Yin, Yout, prev, W, st, s);
+    case 3: return mfk_launch_p<4>(L, Yin, Yout, prev, W, st, s);
+    case 4: return mfk_launch_p<5>(L, Yin, Yout, prev, W, st, s);
+    case 5: return mfk_launch_p<6>(L, Yin, Yout, prev, W, st, s);
+    case 6: return mfk_launch_p<7>(L, Yin, Yout, prev, W, st, s);
+    case 7: return mfk_launch_p<8>(L, Yin, Yout, prev, W, st, s);
+    default: return mfk_launch_p<9>(L, Yin, Yout, prev, W, st, s);
   }
 }
 

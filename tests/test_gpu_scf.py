@@ -6,7 +6,8 @@ solve of the same FE system (1e-10), the device potential path against the
 host one (the same operator to rounding), and the converged SCF fixed point:
 Ritz values to 1e-8 Ha and the density at the Gauss points to 1e-7 relative
 (both loops stop at a density residual of 1e-10; their random start blocks
-and Lanczos starts differ, the fixed point does not)."""
+and Lanczos starts differ, the fixed point does not).  The Ritz values
+compared are the converged ones below the subspace's buffer states."""
 import numpy as np
 import pytest
 import torch
@@ -67,7 +68,9 @@ def test_scf_fixed_point_matches_oracle():
         got = ctx.scf(X, args["centres"], args["Z"], args["sigma"], kT=0.01, degree=20, passes=2,
                       tol=1e-10, max_iter=60)
     assert got["residuals"][-1] < 1e-10 and got["iters"] < 60
-    assert np.abs(got["evals"] - ref["evals"]).max() < 1e-8
+    # the occupied state and the next one; the top of the 4-state subspace is
+    # the buffer (A9), which two ChFSI passes per step do not converge
+    assert np.abs(got["evals"][:2] - ref["evals"][:2]).max() < 1e-8
     assert abs(got["mu"] - ref["mu"]) < 1e-8
     rho_ref = ref["rho"].reshape(-1)
     assert np.abs(got["rho"] - rho_ref).max() < 1e-7 * np.abs(rho_ref).max()
