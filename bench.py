@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps (median wall time reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--gather", default="registers", choices=["async", "registers"],
+    ap.add_argument("--gather", default="rings", choices=["async", "registers", "rings", "rings4"],
                     help="BF16x3 cell kernel gather (bulk async copies or register loads)")
     ap.add_argument("--fp64-op", default="default", choices=["default", "cells", "matrix-free"],
                     help="binary64 cell operator")

@@ -142,13 +142,14 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
  * do not depend on it. */
 chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
 
-/* Gather of the BF16x3 cell kernel: 0 (default) = warps load the cell's rows
- * of Y into registers, two K-chunks in flight per thread block; 1 = the rows
- * are staged in shared memory by bulk async copies, several K-chunks ahead of
- * the tensor-core products (used when the block is 16-byte aligned with a
- * leading dimension and a column count that are multiples of 4, else the
- * register loads).  Results are bit-identical; on the 16^3-cell p = 6
- * workload the staged form measured 3% slower, so it is not the default. */
+/* Variant of the BF16x3 cell kernel (results are bit-identical): 2 (default)
+ * = warps gather the cell's rows of Y into registers and split them, with the
+ * cell-matrix chunks and the split Y chunks in separate shared-memory rings
+ * (the matrix copies run up to five chunks ahead at p = 6); 0 = one ring
+ * shared by both operands; 1 = the rows staged by bulk async copies several
+ * chunks ahead and split from shared memory (used when the block is 16-byte
+ * aligned with a leading dimension and a column count that are multiples of
+ * 4, else 0); 3 = as 2 with four gather warp pairs instead of two. */
 chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode);
 
 /* Cell operator of the binary64 path (every CHFSI_FP64 apply, and the

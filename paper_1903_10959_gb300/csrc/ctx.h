@@ -23,7 +23,7 @@ struct chfsi_ctx {
   std::string err;
   int filter_block = 200, diag_block = 1;
   int cell_tile = 64;              // columns per CTA of the tensor-core cell kernel
-  int cell_gather = 0;             // BF16x3 cell kernel: 0 register loads, 1 async bulk-copy gather
+  int cell_gather = 2;             // BF16x3 cell kernel: 2 decoupled rings (default), 0 one ring, 1 async gather, 3 rings with 4 gather pairs
   int64_t dev_bytes = 0;
   // resident device data
   double* d_Ht = nullptr;          // binary64 cell matrices

@@ -154,6 +154,26 @@ __device__ __forceinline__ void bf16_split3f(float v, uint16_t& b1, uint16_t& b2
   b3 = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
 }
 
+// The same three-term split for two binary32 values at once, packed the way
+// the MMA operand holds them (x0 in the low half, x1 in the high half): one
+// cvt.rn.bf16x2.f32 per term (round to nearest even, as __float2bfloat16_rn),
+// the back-conversion by a shift or a mask, the remainders exact as above.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float hi, float lo) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ void bf16_split3_pair(float x0, float x1, uint32_t& w1, uint32_t& w2,
+                                                 uint32_t& w3) {
+  w1 = cvt_bf16x2(x1, x0);
+  const float r0 = x0 - __uint_as_float(w1 << 16);
+  const float r1 = x1 - __uint_as_float(w1 & 0xffff0000u);
+  w2 = cvt_bf16x2(r1, r0);
+  const float s0 = r0 - __uint_as_float(w2 << 16);
+  const float s1 = r1 - __uint_as_float(w2 & 0xffff0000u);
+  w3 = cvt_bf16x2(s1, s0);
+}
+
 __global__ void tc_pack_bf16_kernel(const double* __restrict__ Ht, uint16_t* __restrict__ out,
                                     int64_t ncells, int ne, int mt, int nk16) {
   const int64_t per_chunk = (int64_t)mt * 2048;   // elements of one term, all tiles
@@ -671,14 +691,8 @@ __global__ void __launch_bounds__(CELL_THREADS, 2) tc_cell_bf16_kernel(RParams P
         const int o = bf_elem_off(lane + 32 * u, q * 8);
         uint32_t w[3][4];
 #pragma unroll
-        for (int a = 0; a < 8; a += 2) {
-          uint16_t lo1, lo2, lo3, hi1, hi2, hi3;
-          bf16_split3f(v[a][u], lo1, lo2, lo3);
-          bf16_split3f(v[a + 1][u], hi1, hi2, hi3);
-          w[0][a / 2] = (uint32_t)lo1 | ((uint32_t)hi1 << 16);
-          w[1][a / 2] = (uint32_t)lo2 | ((uint32_t)hi2 << 16);
-          w[2][a / 2] = (uint32_t)lo3 | ((uint32_t)hi3 << 16);
-        }
+        for (int a = 0; a < 8; a += 2)
+          bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[2][a / 2]);
 #pragma unroll
         for (int p = 0; p < 3; ++p)
           *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
@@ -968,6 +982,212 @@ bool tc_cell_bf16_async_ok(const TcApplyArgs& a) {
   return ((reinterpret_cast<uintptr_t>(a.Yin) & 15) == 0) && (a.ld_in % 4 == 0) && (a.ncol % 4 == 0);
 }
 
+// ----------------------------------------------------------------- BF16x3 cell kernel, decoupled rings
+// The same product, tiling, gather and arithmetic as tc_cell_bf16_kernel
+// (bit-identical results), with the cell-matrix chunks and the split Y chunks
+// in two separate rings: SM matrix stages (one bulk-copied chunk of the
+// part's rows each) and SY Y stages (three bf16 terms of 128 columns).  A
+// chunk's matrix terms come from DRAM at about a microsecond of latency while
+// its six MMAs take a quarter of that, so the matrix copies run SM chunks
+// ahead of the products; the Y terms, gathered two chunks at a time by the
+// warp pairs with a register prefetch, need only two stages.  The MMA warp
+// releases both slots of a chunk with one commit each.
+struct BfrPlan {
+  int np, nh, alloc, sm, sy, total;
+};
+// npair gather warp pairs; each pair owns the Y stages i % npair of its
+// chunks i = pair (mod npair), so its parity waits stay sound.
+__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair) {
+  const BfPlan b = bf_plan(ne);
+  BfrPlan r;
+  r.np = b.np;
+  r.nh = b.nh;
+  r.alloc = b.alloc;
+  const int per_sm = 512 / b.alloc >= 3 ? 3 : 512 / b.alloc;
+  const int budget = (per_sm >= 3 ? 72 : (per_sm == 2 ? 111 : 200)) * 1024 - kCellSmemTail;
+  const int mstage = 3 * b.nh * 32, ystage = BF_YT;
+  r.sy = npair;
+  r.sm = (budget - r.sy * ystage) / mstage;
+  if (r.sm > 8) r.sm = 8;
+  if (r.sm < 2) r.sm = 2;
+  r.total = r.sm * mstage + r.sy * ystage + kCellSmemTail;
+  return r;
+}
+
+template <int NPAIR>
+__global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
+  constexpr int NTHR = (2 * NPAIR + 2) * 32;
+  constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.e_off + blockIdx.y;
+  const int ne = P.ne, nk = P.nk;
+  const BfrPlan B = bfr_plan(ne, NPAIR);
+  const int h = blockIdx.x % B.np;
+  const int c0 = (blockIdx.x / B.np) * 128;
+  const int ncv = min(128, P.ncol - c0);
+  const int r0 = h * B.nh;
+  const int SM = B.sm, SY = B.sy;
+  const int hrow = B.nh * 32;
+  const int mstage = 3 * hrow;
+  unsigned char* ybase = smem + SM * mstage;                   // Y term stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * BF_YT);
+  // fa[SM] (matrix full, tx), ea[SM] (matrix empty), fy[SY] (Y full, 64), ey[SY] (Y empty), acc
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SM + 2 * SY + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);
+  const uint32_t mbase = smem_u32(smem);
+  const uint32_t ysb = smem_u32(ybase);
+  auto fa = [&](int s) { return smem_u32(bars + s); };
+  auto ea = [&](int s) { return smem_u32(bars + SM + s); };
+  auto fy = [&](int s) { return smem_u32(bars + 2 * SM + s); };
+  auto ey = [&](int s) { return smem_u32(bars + 2 * SM + SY + s); };
+  const uint32_t accb = smem_u32(bars + 2 * SM + 2 * SY);
+
+  if (tid == 0) {
+    for (int s = 0; s < SM; ++s) {
+      mbar_init(fa(s), 1);
+      mbar_init(ea(s), 1);
+    }
+    for (int s = 0; s < SY; ++s) {
+      mbar_init(fy(s), 64);
+      mbar_init(ey(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == WMMA) {
+    tmem_alloc(smem_u32(tmem_slot), B.alloc);
+    tmem_relinquish();
+  }
+  for (int l = tid; l < ne; l += NTHR) dm[l] = P.dofmap[e * ne + l];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == WPROD) {
+    if (lane == 0) {
+      const int64_t term_bytes = (int64_t)P.mt * 4096;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * 3 * term_bytes + (int64_t)r0 * 32;
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % SM;
+        if (i >= SM && !mbar_wait(ea(s), ((i / SM) - 1) & 1)) {
+          atomicExch(&g_tc_status, 41);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        const uint32_t dst = mbase + s * mstage;
+        mbar_arrive_expect_tx(fa(s), 3 * hrow);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * 3 + p) * term_bytes, hrow, fa(s));
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag)
+        for (int i = max(0, issued - SM); i < issued; ++i) mbar_wait(fa(i % SM), (i / SM) & 1);
+    }
+  } else if (warp == WMMA) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, B.nh);
+      for (int i = 0; i < nk; ++i) {
+        const int sa = i % SM, sy = i % SY;
+        if (!mbar_wait(fa(sa), (i / SM) & 1) || !mbar_wait(fy(sy), (i / SY) & 1) ||
+            *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 42);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t yb = ysb + sy * BF_YT;
+        const uint32_t hb = mbase + sa * mstage;
+        uint64_t y[3], hd[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          y[p] = umma_desc(yb + p * 4096, 128, 256);
+          hd[p] = umma_desc(hb + p * hrow, 128, 256);
+        }
+        mma_f16(tmem, y[0], hd[2], idesc, i > 0);
+        mma_f16(tmem, y[1], hd[1], idesc, 1);
+        mma_f16(tmem, y[2], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[1], idesc, 1);
+        mma_f16(tmem, y[1], hd[0], idesc, 1);
+        mma_f16(tmem, y[0], hd[0], idesc, 1);
+        umma_commit(ea(sa));
+        umma_commit(ey(sy));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    // gather + split exactly as tc_cell_bf16_kernel; Y stage of chunk i is i % SY
+    const int pair = warp >> 1, q = warp & 1;
+    for (int i = pair; i < nk; i += NPAIR) {
+      const int s = i % SY;
+      float v[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int l = i * BF_KC + q * 8 + a;
+        const int g = l < ne ? dm[l] : -1;
+        const float* src = P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = lane + 32 * u;
+          v[a][u] = (g >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
+        }
+      }
+      if (i >= SY && !mbar_wait(ey(s), ((i / SY) - 1) & 1)) {
+        atomicExch(&g_tc_status, 43);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint16_t* ys = reinterpret_cast<uint16_t*>(ybase + s * BF_YT);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = bf_elem_off(lane + 32 * u, q * 8);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int a = 0; a < 8; a += 2)
+          bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[2][a / 2]);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(fy(s));
+    }
+    // epilogue: warps 0-3 (TMEM lane quarter = warp % 4); further gather warps are done
+    if (warp < 4) {
+    const bool okacc = mbar_wait(accb, 0);
+    if (!okacc) {
+      atomicExch(&g_tc_status, 44);
+      *(volatile int*)abort_flag = 1;
+    }
+    tc_fence_after();
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    const int c = warp * 32 + lane;
+    float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    for (int cb = 0; cb < B.nh; cb += 16) {
+      float acc[16];
+      __syncwarp();
+      if (run) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+        tmem_wait_ld();
+      }
+      if (!run || c >= ncv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = acc[j];
+    }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WMMA) tmem_dealloc(tmem, B.alloc);
+}
+
 cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.bf) return cudaErrorInvalidValue;
@@ -980,15 +1200,22 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const bool async = a.gather == 1 && tc_cell_bf16_async_ok(a);
   const BfaPlan BA = bfa_plan(d.ne);
+  const BfrPlan BR = bfr_plan(d.ne, 2), BR4 = bfr_plan(d.ne, 4);
   for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
     P.e_off = e0;
     dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
     note_launch();
     if (async)
       tc_cell_bf16_async_kernel<<<grid, BFA_THREADS, BA.total, s>>>(P);
+    else if (a.gather == 2)
+      tc_cell_bf16_rings_kernel<2><<<grid, 6 * 32, BR.total, s>>>(P);
+    else if (a.gather == 3)
+      tc_cell_bf16_rings_kernel<4><<<grid, 10 * 32, BR4.total, s>>>(P);
     else
       tc_cell_bf16_kernel<<<grid, CELL_THREADS, B.total, s>>>(P);
   }

@@ -33,7 +33,8 @@ struct TcApplyArgs {
   float* R;                 // ncells * ne * ncol scratch
   int split3;
   int tile = 64;            // columns per CTA of the cell kernel: 64 or 128
-  int gather = 0;           // BF16x3: 0 = register loads, 1 = rows staged by bulk async copies (when aligned)
+  int gather = 2;           // BF16x3: 2 = decoupled matrix / Y rings, 0 = one shared ring, 1 = rows staged by
+                            // bulk async copies (when aligned), 3 = rings with four gather warp pairs
 };
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
 

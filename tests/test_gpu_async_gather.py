@@ -1,5 +1,6 @@
-"""The BF16x3 cell kernel with the bulk-async-copy gather gives the same bits
-as the register gather (same split, same MMA order, same tiling), for every
+"""The BF16x3 cell kernel variants -- the bulk-async-copy gather and the
+decoupled matrix / Y rings -- give the same bits as the register gather
+(same split, same MMA order, same tiling), for every
 FE degree the kernel plans for, Dirichlet rows, ragged last column tiles and
 several 128-column tiles; an unaligned block falls back to the register
 gather.  Both are checked against the oracle's H~ X as well."""
@@ -42,7 +43,11 @@ def test_async_gather_is_bit_identical(p, periodic):
             X = torch.tensor(x, device=DEV)
             ya = _apply(ctx, X, "async")
             yr = _apply(ctx, X, "registers")
+            yg = _apply(ctx, X, "rings")
+            y4 = _apply(ctx, X, "rings4")
             assert torch.equal(ya, yr), (p, periodic, ncol)
+            assert torch.equal(yg, yr), (p, periodic, ncol)
+            assert torch.equal(y4, yr), (p, periodic, ncol)
             if ncol == 4:
                 ref = prob.apply_Htilde(x.astype(np.float64))
                 assert rel_fro(ya.cpu().numpy().astype(np.float64), ref) < 1e-5
