@@ -51,13 +51,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps (median wall time reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--gather", default="rings", choices=["async", "registers", "rings", "rings4"],
+    ap.add_argument("--gather", default="rings", choices=["async", "registers", "rings", "rings4", "whole"],
                     help="BF16x3 cell kernel gather (bulk async copies or register loads)")
     ap.add_argument("--fp64-op", default="default", choices=["default", "cells", "matrix-free"],
                     help="binary64 cell operator")
     ap.add_argument("--no-side-arms", action="store_true",
                     help="skip the binary64 / polished arm and the 20^3-cell p=7 arm")
     ap.add_argument("--small", action="store_true", help="small case for profiling runs")
+    ap.add_argument("--n-want", type=int, default=0,
+                    help="small case: wanted states (default 200; the block adds a 10%% buffer)")
     ap.add_argument("--block", type=int, default=0,
                     help="wavefunction block of the filter (0: chosen by the autotuner)")
     ap.add_argument("--tile", type=int, default=64, choices=[64, 128],
@@ -77,12 +79,13 @@ def parse():
     return ap.parse_args()
 
 
-def workload(small=False, kind="chfsi"):
+def workload(small=False, kind="chfsi", n_want=0):
     from paper_1903_10959_gb300 import workloads as W
     if kind == "c3":
         return W.cubic_sites_nonlocal(block=1100)
     if small:
-        return W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=200, degree=40, iters=4, block=200)
+        return W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=n_want or 200, degree=40, iters=4,
+                              block=200)
     return W.fcc_periodic()
 
 
@@ -294,6 +297,10 @@ MMA_PASSES = {"bf16x3": 6, "mixed": 3, "tf32": 1}
 CELL_MATRIX_BYTES = {"bf16x3": 6, "mixed": 8, "tf32": 4, "fp64": 8}
 CELL_KERNEL = {"bf16x3": "tc_cell_bf16_kernel", "mixed": "tc_cell_r_kernel",
                "tf32": "tc_cell_r_kernel", "fp64": "cell_fp64_kernel"}
+# The BF16x3 cell kernel each gather mode launches.
+BF16_KERNEL = {"registers": "tc_cell_bf16_kernel", "async": "tc_cell_bf16_async_kernel",
+               "rings": "tc_cell_bf16_rings_kernel", "rings4": "tc_cell_bf16_rings_kernel",
+               "whole": "tc_cell_bf16_whole_kernel"}
 
 
 def load_peaks():
@@ -326,7 +333,7 @@ def mf_flops_per_cell(p):
 
 
 def rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks, cell_ms, cell_n, asm_ms, asm_n,
-              fp64_op="cells"):
+              fp64_op="cells", gather="rings"):
     """Cell-kernel, assembly and filter-step rooflines from the per-launch event times.
 
     Cell kernel: algorithmic work = N_c 2 n_e^2 flops per vector and
@@ -346,7 +353,7 @@ def rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks, cell_ms, c
     alg_flops = col_steps * ncells * 2 * ne * ne
     peak, note = dtype_peak(prec, peaks)
     achieved = alg_flops / (cell_ms / 1e3) / 1e12
-    kern = CELL_KERNEL[prec]
+    kern = BF16_KERNEL.get(gather, CELL_KERNEL[prec]) if prec == "bf16x3" else CELL_KERNEL[prec]
     roof = {"bound": "alu" if prec == "fp64" else "tensor", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profiled_traffic(kern, s, n) if prec != "fp64" else None,
@@ -451,7 +458,7 @@ def fp64_polish_arm(ctx, s, X, b, D_mixed, stream, mixed_s_per_iter):
     }
 
 
-def c3_arm(stream, steps=1):
+def c3_arm(stream, steps=1, gather="rings"):
     """The largest single-GPU workload (20^3 cells, p = 7, 1,000 projector
     sites, N = 3,000 + 300, block 1,100, degree 50): one warm-up and `steps`
     timed mixed (BF16x3) ChFSI iterations, with the cell-kernel roofline."""
@@ -465,6 +472,7 @@ def c3_arm(stream, steps=1):
     ctx.set_projectors(s.nl_centres, s.nl_h, s.nl_sigma, s.nl_rcut)
     ctx.build()
     ctx.set_blocking(s.block, 1)
+    ctx.set_cell_gather(gather)
     n, M = s.n_sub, ctx.ndofs
     b = ctx.bounds(20, s.seed)
     X = torch.empty((M, n), dtype=torch.float32, device="cuda")
@@ -497,7 +505,7 @@ def c3_arm(stream, steps=1):
     nblocks = -(-n // s.block)
     steps_blocks = steps * (s.degree + 1)
     roof, asm_roof, _ = rooflines("bf16x3", s, n, M, load_peaks(), steps_blocks * n, steps_blocks,
-                                  nblocks, kt[0], kt[2], kt[1], kt[3])
+                                  nblocks, kt[0], kt[2], kt[1], kt[3], gather=gather)
     ctx.destroy()
     del X
     torch.cuda.empty_cache()
@@ -525,7 +533,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     import dataclasses
-    s = workload(args.small, args.workload)
+    s = workload(args.small, args.workload, args.n_want)
     if args.block:
         s = dataclasses.replace(s, block=args.block)
     prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec]
@@ -602,7 +610,8 @@ def run_ours(args):
     peaks = load_peaks()
     cell_ms, asm_ms, cell_n, asm_n, nl_ms, nl_n = [float(v) for v in kt]
     roof, asm_roof, step_roof = rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks,
-                                          cell_ms, cell_n, asm_ms, asm_n, ctx.fp64_operator)
+                                          cell_ms, cell_n, asm_ms, asm_n, ctx.fp64_operator,
+                                          gather=args.gather)
     alg_flops = col_steps * ncells * 2 * ne * ne
     phase_timed = phase.copy()
     # end to end through host buffers, inside the library (chfsi_step_host):
@@ -691,7 +700,7 @@ def run_ours(args):
         ctx.destroy()
         del X
         torch.cuda.empty_cache()
-        side["c3"] = c3_arm(stream)
+        side["c3"] = c3_arm(stream, gather=args.gather)
     if rank != 0:
         return
     cpu = None
@@ -789,25 +798,26 @@ def run_serving(args):
     import torch
     from paper_1903_10959_gb300 import workloads as W
     torch.cuda.init()
+    sp = args.prec if args.prec != "fp64" else "bf16x3"     # the server's mixed precision
     reqs = W.serving_requests(seed=5, count=args.requests, dof_range=(2.0e4, args.dof_max),
                               degree=SERVE_DEGREE)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    warm, _ = serve_stream(reqs[:1], "mixed", 1)                     # builds, first-use costs
-    res_cap, span_cap = serve_stream(reqs, "mixed", args.slots)
+    warm, _ = serve_stream(reqs[:1], sp, 1)                     # builds, first-use costs
+    res_cap, span_cap = serve_stream(reqs, sp, args.slots)
     cap = serve_summary(res_cap, span_cap)
     rate_cap = len(reqs) / span_cap                                    # requests / s
     sweep = {}
     for f in [float(x) for x in args.rates.split(",") if x]:
         arr = W.poisson_arrivals(5, len(reqs), f * rate_cap)
-        r, span = serve_stream(reqs, "mixed", args.slots, arrivals=arr)
+        r, span = serve_stream(reqs, sp, args.slots, arrivals=arr)
         sweep["%.2f" % f] = serve_summary(r, span)
     # plain FP64, one request at a time, against the mixed server on the same
     # subset (the smallest requests: binary64 cell products run ~50x slower)
     order = sorted(range(len(reqs)), key=lambda i: reqs[i][0].ndofs * reqs[i][0].n_sub)
     sub = [reqs[i] for i in order[:args.fp64_requests]]
     r64, span64 = serve_stream(sub, "fp64", 1)
-    rmx, spanmx = serve_stream(sub, "mixed", args.slots)
+    rmx, spanmx = serve_stream(sub, sp, args.slots)
     fp64 = {"subset": [s.name for s, _ in sub], "fp64_sequential": serve_summary(r64, span64),
             "mixed_server": serve_summary(rmx, spanmx)}
     errs = [float(np.abs(a["evals"][:, :s.n_want] - b["evals"][:, :s.n_want]).max())
@@ -819,9 +829,10 @@ def run_serving(args):
     s08 = sweep.get("0.80", cap)
     line = {
         "metric": "serving solves/s and p50/p99 latency (mixed, continuous batching)",
+        "precision": sp,
         "value": cap["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
         "warmup": 1, "ms_per_step": 1e3 / cap["solves_per_s"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32x3 (f64 CholGS/RR/residual)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+%s (f64 residual)" % {"mixed": "tf32x3"}.get(sp, sp),
         "data": "synthetic",
         "config": {"workload": "serving: %d periodic Gaussian-well requests, unknowns log-uniform "
                                "2e4-%.0e, p in {5,6,7}, N log-uniform 32-1000, 5 warm re-solves "
@@ -880,12 +891,14 @@ def run_batch(args):
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    t_batch = timed(lambda: bt.filter(X, m, a, bnd, a0, prec="mixed"), args.steps)
+    t_batch_tf = timed(lambda: bt.filter(X, m, a, bnd, a0, prec="mixed"), args.steps)
+    t_batch = timed(lambda: bt.filter(X, m, a, bnd, a0, prec="bf16x3"), args.steps)
 
-    def seq():
+    def seq(prec):
         for c, x, ai, bi, a0i in zip(ctxs, X, a, bnd, a0):
-            c.filter(x, m, float(ai), float(bi), float(a0i), prec="mixed")
-    t_seq = timed(seq, args.steps)
+            c.filter(x, m, float(ai), float(bi), float(a0i), prec=prec)
+    t_seq = timed(lambda: seq("bf16x3"), args.steps)
+    t_seq_tf = timed(lambda: seq("mixed"), args.steps)
     X64 = []
     for c, s, x in zip(ctxs, systems, X):            # fresh start blocks (the filtered ones are
         x64 = torch.empty(x.shape, dtype=torch.float64, device="cuda")   # nearly rank-deficient)
@@ -894,14 +907,19 @@ def run_batch(args):
     evs = bt.solve(X64, 1, m, bnd * 1.02)           # warm-up of the per-system solver state
     t_solve = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02), 1)
     t_solve_mixed = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02, orth_prec="mixed"), 1)
+    t_solve_bf = timed(lambda: bt.solve(X64, 1, m, bnd * 1.02, filter_prec="bf16x3",
+                                        orth_prec="bf16x3"), 1)
     clk = clocks.stop()
-    tf32_peak, tf32_note = dtype_peak("mixed", load_peaks())
+    peaks = load_peaks()
+    tf32_peak, tf32_note = dtype_peak("mixed", peaks)
+    bf16_peak, bf16_note = dtype_peak("bf16x3", peaks)
     achieved = flops / t_batch / 1e12
+    achieved_tf = flops / t_batch_tf / 1e12
     line = {
         "metric": "batched Chebyshev filter aggregate TFLOP/s (64 Dirichlet systems, p=5)",
-        "value": flops / t_batch / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "value": achieved, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
         "config": {"workload": "64 Dirichlet Gaussian-well systems, 4-12 cells per side, p=5, "
                                "h=1.5, N log-uniform 16-400, degree %d" % m,
                    "unknowns_total": int(sum(c.ndofs for c in ctxs)),
@@ -910,13 +928,21 @@ def run_batch(args):
                                                                  for c, t in zip(cands, cand_ms)}},
         "filter_s_batched": t_batch, "filter_s_sequential": t_seq,
         "speedup_vs_sequential": t_seq / t_batch,
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tf32_peak, "traffic": None,
-                     "kernel": "tc_cell_r_kernel<64, true> (multi-system)",
-                     "peak_note": tf32_note + "; algorithmic flops N_c 2 n_e^2 per vector",
-                     "executed_mma": {"passes_per_flop": 3, "frac_of_peak": 3 * achieved / tf32_peak}},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": achieved / bf16_peak, "traffic": None,
+                     "kernel": "tc_cell_bf16_rings_kernel<2, true> (multi-system) + tc_assemble_batched_kernel",
+                     "peak_note": bf16_note + "; algorithmic flops N_c 2 n_e^2 per vector over the whole "
+                                  "filter (cell + assembly launches)",
+                     "executed_mma": {"passes_per_flop": 6, "frac_of_peak": 6 * achieved / bf16_peak}},
+        "tf32x3": {"filter_s_batched": t_batch_tf, "filter_s_sequential": t_seq_tf,
+                   "speedup_vs_sequential": t_seq_tf / t_batch_tf,
+                   "roofline": {"bound": "tensor", "achieved": achieved_tf, "peak": tf32_peak,
+                                "unit": "TFLOP/s", "frac": achieved_tf / tf32_peak,
+                                "kernel": "autotuned TF32 batched cell kernel",
+                                "peak_note": tf32_note}},
         "batched_chfsi_iteration_s": t_solve,
         "batched_chfsi_iteration_s_tf32x3_orth": t_solve_mixed,
+        "batched_chfsi_iteration_s_bf16x3": t_solve_bf,
         "clocks": clk,
     }
     del evs

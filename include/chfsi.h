@@ -528,7 +528,11 @@ const char*  chfsi_batch_last_error(const chfsi_batch* b);
 
 /* Filter X[s] (device, binary32, M_s x ncol[s], leading dimension ldx[s]) of
  * every system in place with degree `degree` and bounds a[s] < b[s],
- * a0[s] < a[s] (scaled Eq. chebFilter), precision MIXED_TF32X3 or MIXED_TF32.
+ * a0[s] < a[s] (scaled Eq. chebFilter), precision MIXED_BF16X3, MIXED_TF32X3 or
+ * MIXED_TF32.  MIXED_BF16X3 runs one launch of the BF16x3 cell kernel per
+ * degree step over the (system, cell, 128-column tile, row part) items (the
+ * tile choice below applies to the TF32 kernels only); the first BF16x3 call
+ * packs each member's three-term copy (3 x 2 bytes per cell-matrix element).
  * Synchronises the batch stream. */
 chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* ldx,
                                 const int* ncol, int degree, const double* a,
@@ -536,7 +540,8 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
 
 /* Autotuner of the batched cell kernel: times every candidate (column tile
  * width x pipeline depth, see chfsi_batch_candidates) on two degree steps of
- * this batch and keeps the fastest for later filter calls.  X is used as
+ * this batch and keeps the fastest for later filter calls (TF32 precisions
+ * only: CHFSI_ERR_ARG for MIXED_BF16X3, which has one kernel).  X is used as
  * scratch and overwritten.  choice (may be NULL) receives the winning index,
  * ms_out (may be NULL, one entry per candidate) the measured times. */
 chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t* ldx,
@@ -557,8 +562,9 @@ chfsi_status chfsi_batch_set_candidate(chfsi_batch* b, int k);
  * block), bnd[s] the upper bound of spec(H~_s); per iteration the batched
  * binary32 filter (filter_prec) followed, per system and concurrently, by
  * CholGS and Rayleigh-Ritz in orth_prec: CHFSI_FP64 (on the binary64 block)
- * or CHFSI_MIXED_TF32X3 (3xTF32 off-diagonal, binary64 diagonal, on the
- * binary32 working copy; the last Rayleigh-Ritz applies H~ with binary64
+ * or CHFSI_MIXED_TF32X3 / CHFSI_MIXED_BF16X3 (split-precision off-diagonal,
+ * binary64 diagonal, on the binary32 working copy; the last Rayleigh-Ritz
+ * applies H~ with binary64
  * products, as chfsi_solve does); X[s] receives the final block.
  * evals[s][n[s]] (host) receive the Ritz values. */
 chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* ldx, const int* n,

@@ -912,9 +912,9 @@ chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile) {
 
 chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode) {
   CHECK_CTX();
-  if (mode < 0 || mode > 3)
-    return fail(ctx, CHFSI_ERR_ARG, "gather: 0 register loads, 1 bulk async copies, 2 / 3 decoupled rings "
-                                    "with 2 / 4 gather warp pairs");
+  if (mode < 0 || mode > 4)
+    return fail(ctx, CHFSI_ERR_ARG, "cell kernel variant: 0 one ring, 1 bulk async copies, 2 / 3 decoupled "
+                                    "rings with 2 / 4 gather warp pairs, 4 whole cell per thread block");
   ctx->cell_gather = mode;
   return CHFSI_OK;
 }

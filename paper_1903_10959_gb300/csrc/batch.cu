@@ -439,9 +439,17 @@ cudaError_t launch_batched_cell(chfsi_batch* b, int split3, int S, int parity, c
   return cudaGetLastError();
 }
 
+// Cell-kernel modes of the batched filter (split3 argument of the helpers below).
+constexpr int kBatchTf32 = 0, kBatchTf32x3 = 1, kBatchBf16x3 = 2;
+
+int batch_mode(chfsi_precision prec) {
+  return prec == CHFSI_MIXED_BF16X3 ? kBatchBf16x3 : (prec == CHFSI_MIXED_TF32X3 ? kBatchTf32x3 : kBatchTf32);
+}
+
 // Describe every system for the current filter call (pointers, items, quads).
+// BF16x3: the packed three-term copy, items per (cell, 128-column tile, row part).
 cudaError_t batch_describe(chfsi_batch* b, float* const* X, const int64_t* ldx, const int* ncol,
-                           int bn) {
+                           int bn, int mode) {
   const int n = (int)b->ctx.size();
   b->h_sys.assign(n, BSys{});
   int64_t item = 0, q = 0;
@@ -453,7 +461,7 @@ cudaError_t batch_describe(chfsi_batch* b, float* const* X, const int64_t* ldx, 
     if ((e = ensure_dbuf(b->T1[i], (size_t)m.ndofs * ld4 * 4 + 16)) != cudaSuccess) return e;
     if ((e = ensure_dbuf(b->R[i], (size_t)m.ncells * m.ne * ld4 * 4 + 16)) != cudaSuccess) return e;
     BSys& sy = b->h_sys[i];
-    sy.A = c->tc.hi;
+    sy.A = mode == kBatchBf16x3 ? reinterpret_cast<const float*>(c->tc.bf) : c->tc.hi;
     sy.dofmap = c->d_dofmap;
     sy.Y[0] = X[i];
     sy.ldY[0] = ldx[i];
@@ -466,7 +474,7 @@ cudaError_t batch_describe(chfsi_batch* b, float* const* X, const int64_t* ldx, 
     sy.ncells = m.ncells;
     sy.M = m.ndofs;
     sy.ncol = ncol[i];
-    sy.tiles = (ncol[i] + bn - 1) / bn;
+    sy.tiles = mode == kBatchBf16x3 ? (ncol[i] + 127) / 128 * tc_bf16_parts(b->ne) : (ncol[i] + bn - 1) / bn;
     sy.item0 = item;
     sy.q0 = q;
     item += m.ncells * sy.tiles;
@@ -487,7 +495,9 @@ cudaError_t batch_enqueue(chfsi_batch* b, float* const* X, const int* ncol, int 
   if (e != cudaSuccess) return e;
   for (int k = 1; k <= degree; ++k) {
     const int parity = (k - 1) & 1;
-    if (S < 0)
+    if (split3 == kBatchBf16x3)
+      e = tc_cell_bf16_multi_launch(b->d_sys, n, b->nitems, b->ne, b->mt, parity, b->stream);
+    else if (S < 0)
       e = tc_cell_multi_launch(b->d_sys, n, b->nitems, b->ne, b->mt, b->nk, split3, parity, b->stream);
     else
       e = bn == 64 ? launch_batched_cell<64>(b, split3, S, parity, b->stream)
@@ -552,13 +562,18 @@ chfsi_status batch_check(chfsi_batch* b, float* const* X, const int64_t* ldx, co
 }
 
 chfsi_status batch_prepare(chfsi_batch* b, float* const* X, const int64_t* ldx, const int* ncol,
-                           int degree, int bn) {
+                           int degree, int bn, int mode) {
   const int n = (int)b->ctx.size();
   for (int i = 0; i < n; ++i) {
     chfsi_ctx* c = b->ctx[i];
     if (!c->tc.hi) {
       cudaError_t pe = tc_pack_from_device(c->tc, c->d_Ht, c->stream, &c->dev_bytes);
       if (pe != cudaSuccess) return bfail(b, CHFSI_ERR_OOM, "tensor-core cell data");
+      cudaStreamSynchronize(c->stream);
+    }
+    if (mode == kBatchBf16x3 && !c->tc.bf) {
+      cudaError_t pe = tc_pack_bf16_from_device(c->tc, c->d_Ht, c->stream, &c->dev_bytes);
+      if (pe != cudaSuccess) return bfail(b, CHFSI_ERR_OOM, "BF16x3 cell data");
       cudaStreamSynchronize(c->stream);
     }
   }
@@ -571,7 +586,7 @@ chfsi_status batch_prepare(chfsi_batch* b, float* const* X, const int64_t* ldx, 
       return bfail(b, CHFSI_ERR_OOM, "coefficient buffers");
     batch_free_graph(b);
   }
-  cudaError_t e = batch_describe(b, X, ldx, ncol, bn);
+  cudaError_t e = batch_describe(b, X, ldx, ncol, bn, mode);
   if (e != cudaSuccess) return bfail(b, CHFSI_ERR_OOM, cudaGetErrorString(e));
   return CHFSI_OK;
 }
@@ -665,7 +680,7 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
                                 int degree, const double* a, const double* bb, const double* a0,
                                 chfsi_precision prec) {
   if (!b) return CHFSI_ERR_ARG;
-  if (prec != CHFSI_MIXED_TF32X3 && prec != CHFSI_MIXED_TF32)
+  if (prec != CHFSI_MIXED_TF32X3 && prec != CHFSI_MIXED_TF32 && prec != CHFSI_MIXED_BF16X3)
     return bfail(b, CHFSI_ERR_ARG, "batched filter runs in a mixed precision");
   if (degree < 1 || !a || !bb || !a0) return bfail(b, CHFSI_ERR_ARG, "bad degree / bounds");
   chfsi_status st = batch_check(b, X, ldx, ncol);
@@ -673,9 +688,9 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
   const int n = (int)b->ctx.size();
   for (int i = 0; i < n; ++i)
     if (!(a0[i] < a[i]) || !(a[i] < bb[i])) return bfail(b, CHFSI_ERR_ARG, "need a0 < a < b");
-  const int split3 = prec == CHFSI_MIXED_TF32X3;
-  const int bn = b->bn;
-  const int S = b->S != 0 ? b->S : default_stages(b, bn, split3);
+  const int split3 = batch_mode(prec);   // kBatchBf16x3: one multi-system BF16x3 launch per step
+  const int bn = split3 == kBatchBf16x3 ? 128 : b->bn;
+  const int S = split3 == kBatchBf16x3 ? -1 : (b->S != 0 ? b->S : default_stages(b, bn, split3));
   if (b->own_stream) cudaDeviceSynchronize();   // order after the caller's work on any stream
   // the graph is valid while pointers, widths, strides, degree and tile choice stay the
   // same and no member context has been rebuilt (a rebuild frees the cell data and
@@ -688,7 +703,7 @@ chfsi_status chfsi_batch_filter(chfsi_batch* b, float* const* X, const int64_t* 
   cudaStreamSynchronize(b->stream);            // h_coef may still feed the previous replay
   if (!same) {
     batch_free_graph(b);
-    if ((st = batch_prepare(b, X, ldx, ncol, degree, bn)) != CHFSI_OK) return st;
+    if ((st = batch_prepare(b, X, ldx, ncol, degree, bn, split3)) != CHFSI_OK) return st;
     cudaStreamSynchronize(b->stream);
   }
   fill_coef(b, degree, a, bb, a0);
@@ -728,10 +743,10 @@ chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t
                                   double* ms_out) {
   if (!b) return CHFSI_ERR_ARG;
   if (prec != CHFSI_MIXED_TF32X3 && prec != CHFSI_MIXED_TF32)
-    return bfail(b, CHFSI_ERR_ARG, "autotuning is for the mixed precisions");
+    return bfail(b, CHFSI_ERR_ARG, "autotuning is for the TF32 precisions (BF16x3 has one kernel)");
   chfsi_status st = batch_check(b, X, ldx, ncol);
   if (st != CHFSI_OK) return st;
-  const int split3 = prec == CHFSI_MIXED_TF32X3;
+  const int split3 = batch_mode(prec);
   const int n = (int)b->ctx.size();
   if (b->own_stream) cudaDeviceSynchronize();
   // candidates: the non-persistent multi-system kernel (64-column tiles), then
@@ -750,7 +765,7 @@ chfsi_status chfsi_batch_autotune(chfsi_batch* b, float* const* X, const int64_t
   int bi = 0;
   for (size_t c = 0; c < cand.size(); ++c) {
     const int bn = cand[c].first, S = cand[c].second;
-    if ((st = batch_prepare(b, X, ldx, ncol, 2, bn)) != CHFSI_OK) break;
+    if ((st = batch_prepare(b, X, ldx, ncol, 2, bn, split3)) != CHFSI_OK) break;
     fill_coef(b, 2, mid.data(), hi.data(), lo.data());
     double t = 1e300;
     for (int rep = 0; rep < 3; ++rep) {
@@ -822,9 +837,9 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
                                int iters, int degree, const double* bnd, chfsi_precision filter_prec,
                                chfsi_precision orth_prec, double* const* evals) {
   if (!b || !X || !ldx || !n || !bnd || !evals || iters < 0 || degree < 1) return CHFSI_ERR_ARG;
-  if (orth_prec != CHFSI_FP64 && orth_prec != CHFSI_MIXED_TF32X3)
-    return bfail(b, CHFSI_ERR_ARG, "batched CholGS / RR run in binary64 or 3xTF32");
-  const bool mixed_orth = orth_prec == CHFSI_MIXED_TF32X3;
+  if (orth_prec != CHFSI_FP64 && orth_prec != CHFSI_MIXED_TF32X3 && orth_prec != CHFSI_MIXED_BF16X3)
+    return bfail(b, CHFSI_ERR_ARG, "batched CholGS / RR run in binary64, 3xTF32 or BF16x3");
+  const bool mixed_orth = orth_prec != CHFSI_FP64;
   const int ns = (int)b->ctx.size();
   cudaDeviceSynchronize();   // the start blocks may come from any stream
   // binary32 working copies for the filter
@@ -843,7 +858,7 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
   }
   std::vector<std::vector<double>> D(ns);
   std::vector<chfsi_status> sts(ns, CHFSI_OK);
-  // 3xTF32 orthogonalisation works on the binary32 copies in place; the last
+  // mixed orthogonalisation (3xTF32 or BF16x3) works on the binary32 copies in place; the last
   // Rayleigh-Ritz applies H~ with binary64 products (second-order eigenvalues)
   auto per_system_mixed = [&](int i, bool first, bool last) {
     chfsi_ctx* c = b->ctx[i];
@@ -853,9 +868,9 @@ chfsi_status chfsi_batch_solve(chfsi_batch* b, double* const* X, const int64_t* 
       return;
     }
     D[i].resize(n[i]);
-    chfsi_status s1 = chfsi_cholgs(c, xp[i], ld32[i], n[i], CHFSI_MIXED_TF32X3);
+    chfsi_status s1 = chfsi_cholgs(c, xp[i], ld32[i], n[i], orth_prec);
     if (s1 == CHFSI_OK)
-      s1 = rayleigh_ritz_internal(c, xp[i], ld32[i], n[i], CHFSI_MIXED_TF32X3, D[i].data(), last);
+      s1 = rayleigh_ritz_internal(c, xp[i], ld32[i], n[i], orth_prec, D[i].data(), last);
     if (s1 == CHFSI_OK && last &&
         launch_copy_cols(xp[i], ld32[i], X[i], ldx[i], M, n[i], 0, 1, c->stream) != cudaSuccess)
       s1 = CHFSI_ERR_CUDA;

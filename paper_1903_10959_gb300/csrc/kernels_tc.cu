@@ -1014,17 +1014,41 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair) {
   return r;
 }
 
-template <int NPAIR>
+// MULTI: grid x runs over the (system, cell, column tile, row part) items of
+// a batch (TcBatchSys: A = the system's packed BF16x3 copy, tiles = column
+// tiles x parts, items of system s from item0), all systems of one degree.
+template <int NPAIR, bool MULTI>
 __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
   constexpr int NTHR = (2 * NPAIR + 2) * 32;
   constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t e = P.e_off + blockIdx.y;
+  int64_t e = P.e_off + blockIdx.y;
   const int ne = P.ne, nk = P.nk;
   const BfrPlan B = bfr_plan(ne, NPAIR);
-  const int h = blockIdx.x % B.np;
-  const int c0 = (blockIdx.x / B.np) * 128;
+  int h = blockIdx.x % B.np;
+  int c0 = (blockIdx.x / B.np) * 128;
+  if (MULTI) {   // item -> (system, cell, tile, part): binary search over the systems' first items
+    const int64_t item = blockIdx.x;
+    int lo = 0, hi = P.nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.sys[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    const TcBatchSys& sy = P.sys[lo];
+    const int64_t li = item - sy.item0;
+    e = li / sy.tiles;
+    const int t = (int)(li % sy.tiles);
+    h = t % B.np;
+    c0 = (t / B.np) * 128;
+    P.A = sy.A;
+    P.dofmap = sy.dofmap;
+    P.Yin = sy.Y[P.parity];
+    P.ld_in = sy.ldY[P.parity];
+    P.R = sy.R;
+    P.ncol = sy.ncol;
+    P.ldr = sy.ldr;
+  }
   const int ncv = min(128, P.ncol - c0);
   const int r0 = h * B.nh;
   const int SM = B.sm, SY = B.sy;
@@ -1188,6 +1212,213 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   if (warp == WMMA) tmem_dealloc(tmem, B.alloc);
 }
 
+// ----------------------------------------------------------------- BF16x3 cell kernel, whole cell per CTA
+// For cells split into two row parts (p = 6, 7): one CTA per (cell, 128-column
+// tile) computes both parts into two TMEM accumulators (columns [0, nh) and
+// [256, 256 + nh): all 512 columns, one CTA per SM), so every gathered value
+// of Y is split once per cell instead of once per part.  Per K-chunk the
+// producer copies the three terms of both parts' rows (contiguous in the
+// packed layout) and the MMA warp issues the six products for each part.
+// Four gather warp pairs own one Y stage each (chunks i = pair mod 4); the
+// epilogue drains part 0 with warps 0-3 and part 1 with warps 4-7 (TMEM lane
+// quarter = warp % 4).  Same per-part arithmetic as tc_cell_bf16_kernel:
+// bit-identical results.
+constexpr int BFW_NPAIR = 4, BFW_THREADS = (2 * BFW_NPAIR + 2) * 32;
+struct BfwPlan {
+  int nh, sm, sy, total;
+};
+__host__ __device__ inline BfwPlan bfw_plan(int ne) {
+  const BfPlan b = bf_plan(ne);
+  BfwPlan w;
+  w.nh = b.nh;
+  w.sy = BFW_NPAIR;
+  const int budget = 200 * 1024 - kCellSmemTail;
+  const int mstage = 3 * 2 * b.nh * 32;
+  w.sm = (budget - w.sy * BF_YT) / mstage;
+  if (w.sm > 6) w.sm = 6;
+  if (w.sm < 2) w.sm = 2;
+  w.total = w.sm * mstage + w.sy * BF_YT + kCellSmemTail;
+  return w;
+}
+__host__ __device__ inline bool bfw_supported(int ne) {
+  const BfPlan b = bf_plan(ne);
+  return b.np == 2 && b.nh <= 256;
+}
+
+__global__ void __launch_bounds__(BFW_THREADS, 1) tc_cell_bf16_whole_kernel(RParams P) {
+  constexpr int WPROD = 2 * BFW_NPAIR, WMMA = 2 * BFW_NPAIR + 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.e_off + blockIdx.y;
+  const int ne = P.ne, nk = P.nk;
+  const BfwPlan B = bfw_plan(ne);
+  const int c0 = blockIdx.x * 128;
+  const int ncv = min(128, P.ncol - c0);
+  const int SM = B.sm, SY = B.sy;
+  const int hrow = B.nh * 32;                 // one term of one part's rows, one chunk
+  const int trow = 2 * hrow;                  // one term of both parts' rows
+  const int mstage = 3 * trow;
+  unsigned char* ybase = smem + SM * mstage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * BF_YT);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SM + 2 * SY + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);
+  const uint32_t mbase = smem_u32(smem);
+  const uint32_t ysb = smem_u32(ybase);
+  auto fa = [&](int s) { return smem_u32(bars + s); };
+  auto ea = [&](int s) { return smem_u32(bars + SM + s); };
+  auto fy = [&](int s) { return smem_u32(bars + 2 * SM + s); };
+  auto ey = [&](int s) { return smem_u32(bars + 2 * SM + SY + s); };
+  const uint32_t accb = smem_u32(bars + 2 * SM + 2 * SY);
+
+  if (tid == 0) {
+    for (int s = 0; s < SM; ++s) {
+      mbar_init(fa(s), 1);
+      mbar_init(ea(s), 1);
+    }
+    for (int s = 0; s < SY; ++s) {
+      mbar_init(fy(s), 64);
+      mbar_init(ey(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == WMMA) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  for (int l = tid; l < ne; l += BFW_THREADS) dm[l] = P.dofmap[e * ne + l];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == WPROD) {
+    if (lane == 0) {
+      const int64_t term_bytes = (int64_t)P.mt * 4096;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * 3 * term_bytes;
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % SM;
+        if (i >= SM && !mbar_wait(ea(s), ((i / SM) - 1) & 1)) {
+          atomicExch(&g_tc_status, 51);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        const uint32_t dst = mbase + s * mstage;
+        mbar_arrive_expect_tx(fa(s), 3 * trow);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          bulk_g2s(dst + p * trow, Ae + ((int64_t)i * 3 + p) * term_bytes, trow, fa(s));
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag)
+        for (int i = max(0, issued - SM); i < issued; ++i) mbar_wait(fa(i % SM), (i / SM) & 1);
+    }
+  } else if (warp == WMMA) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, B.nh);
+      for (int i = 0; i < nk; ++i) {
+        const int sa = i % SM, sy = i % SY;
+        if (!mbar_wait(fa(sa), (i / SM) & 1) || !mbar_wait(fy(sy), (i / SY) & 1) ||
+            *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 52);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t yb = ysb + sy * BF_YT;
+        const uint32_t hb = mbase + sa * mstage;
+        uint64_t y[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) y[p] = umma_desc(yb + p * 4096, 128, 256);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint64_t hd[3];
+#pragma unroll
+          for (int p = 0; p < 3; ++p) hd[p] = umma_desc(hb + p * trow + h * hrow, 128, 256);
+          const uint32_t acc = tmem + h * 256;
+          mma_f16(acc, y[0], hd[2], idesc, i > 0);
+          mma_f16(acc, y[1], hd[1], idesc, 1);
+          mma_f16(acc, y[2], hd[0], idesc, 1);
+          mma_f16(acc, y[0], hd[1], idesc, 1);
+          mma_f16(acc, y[1], hd[0], idesc, 1);
+          mma_f16(acc, y[0], hd[0], idesc, 1);
+        }
+        umma_commit(ea(sa));
+        umma_commit(ey(sy));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    // warps 0-7: gather + split (pair = warp >> 1 owns Y stage pair)
+    const int pair = warp >> 1, q = warp & 1;
+    for (int i = pair; i < nk; i += BFW_NPAIR) {
+      const int s = i % SY;
+      float v[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int l = i * BF_KC + q * 8 + a;
+        const int g = l < ne ? dm[l] : -1;
+        const float* src = P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = lane + 32 * u;
+          v[a][u] = (g >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
+        }
+      }
+      if (i >= SY && !mbar_wait(ey(s), ((i / SY) - 1) & 1)) {
+        atomicExch(&g_tc_status, 53);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint16_t* ys = reinterpret_cast<uint16_t*>(ybase + s * BF_YT);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = bf_elem_off(lane + 32 * u, q * 8);
+        uint32_t w[3][4];
+#pragma unroll
+        for (int a = 0; a < 8; a += 2)
+          bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[2][a / 2]);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(fy(s));
+    }
+    // epilogue: part h = warp / 4, TMEM lane quarter = warp % 4 (column c0 + 32 (warp % 4) + lane)
+    const bool okacc = mbar_wait(accb, 0);
+    if (!okacc) {
+      atomicExch(&g_tc_status, 54);
+      *(volatile int*)abort_flag = 1;
+    }
+    tc_fence_after();
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    const int h = warp >> 2, wq = warp & 3;
+    const int r0 = h * B.nh;
+    const int c = wq * 32 + lane;
+    float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    for (int cb = 0; cb < B.nh; cb += 16) {
+      float acc[16];
+      __syncwarp();
+      if (run) {
+        tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + h * 256 + cb, acc);
+        tmem_wait_ld();
+      }
+      if (!run || c >= ncv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = acc[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WMMA) tmem_dealloc(tmem, 512);
+}
+
 cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s) {
   if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
   if (!d.bf) return cudaErrorInvalidValue;
@@ -1200,12 +1431,15 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_whole_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const bool async = a.gather == 1 && tc_cell_bf16_async_ok(a);
   const BfaPlan BA = bfa_plan(d.ne);
   const BfrPlan BR = bfr_plan(d.ne, 2), BR4 = bfr_plan(d.ne, 4);
+  const BfwPlan BW = bfw_plan(d.ne);
   for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
     P.e_off = e0;
     dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
@@ -1213,12 +1447,37 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
     if (async)
       tc_cell_bf16_async_kernel<<<grid, BFA_THREADS, BA.total, s>>>(P);
     else if (a.gather == 2)
-      tc_cell_bf16_rings_kernel<2><<<grid, 6 * 32, BR.total, s>>>(P);
+      tc_cell_bf16_rings_kernel<2, false><<<grid, 6 * 32, BR.total, s>>>(P);
     else if (a.gather == 3)
-      tc_cell_bf16_rings_kernel<4><<<grid, 10 * 32, BR4.total, s>>>(P);
+      tc_cell_bf16_rings_kernel<4, false><<<grid, 10 * 32, BR4.total, s>>>(P);
+    else if (a.gather == 4 && bfw_supported(d.ne))
+      tc_cell_bf16_whole_kernel<<<dim3((unsigned)((a.ncol + 127) / 128), grid.y), BFW_THREADS, BW.total, s>>>(P);
+    else if (a.gather == 4)
+      tc_cell_bf16_rings_kernel<2, false><<<grid, 6 * 32, BR.total, s>>>(P);
     else
       tc_cell_bf16_kernel<<<grid, CELL_THREADS, B.total, s>>>(P);
   }
+  return cudaGetLastError();
+}
+
+int tc_bf16_parts(int ne) { return bf_plan(ne).np; }
+
+cudaError_t tc_cell_bf16_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
+                                      int parity, cudaStream_t s) {
+  if (nitems == 0 || nsys == 0) return cudaSuccess;
+  if (nitems > 0x7fffffff) return cudaErrorInvalidValue;
+  const int nk16 = (ne + BF_KC - 1) / BF_KC;
+  const BfPlan B0 = bf_plan(ne);
+  if (B0.np * B0.nh > mt * 128) return cudaErrorInvalidValue;
+  RParams P{nullptr, nullptr, nullptr, nullptr, 0, 0, ne, mt, nk16, 1, d_sys, nsys, parity, 0, 0};
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+  });
+  const BfrPlan BR = bfr_plan(ne, 2);
+  note_launch();
+  tc_cell_bf16_rings_kernel<2, true><<<(unsigned)nitems, 6 * 32, BR.total, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,7 @@ size_t estimate_bytes(const chfsi_request& r) {
   const size_t mt = (ne + 127) / 128, nk = (ne + 7) / 8;
   size_t b = ncells * ne * ne * 8;                                  // binary64 cell matrices
   if (mixed) b += ncells * nk * 2 * mt * 1024 * 4;                  // packed hi / lo TF32 copies
+  if (r.prec == CHFSI_MIXED_BF16X3) b += ncells * ((ne + 15) / 16) * 3 * mt * 4096;   // BF16x3 terms
   b += ncells * ne * 9 + ncells * 4 + M * 16 + 4096;                // dof map, modes, rows, mass
   b += M * n * es;                                                  // X
   b += std::max(M * n * es, M * B * 16);                            // rotation / binary64 pair

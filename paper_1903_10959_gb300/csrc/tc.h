@@ -58,6 +58,12 @@ struct TcBatchSys {
 // Y[parity] of each system is the input.  All systems share n_e / mt / nk.
 cudaError_t tc_cell_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
                                  int nk, int split3, int parity, cudaStream_t s);
+// The BF16x3 cell kernel over the (cell, 128-column tile, row part) items of
+// every system (A = each system's packed BF16x3 copy, tiles = column tiles x
+// tc_bf16_parts(ne)); Y[parity] is the input.
+cudaError_t tc_cell_bf16_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
+                                      int parity, cudaStream_t s);
+int tc_bf16_parts(int ne);
 // Set the cell kernels' shared-memory attributes (before any stream capture).
 void tc_cell_prepare();
 // Owner-computes assembly fused with the Chebyshev update:

@@ -45,6 +45,8 @@ def test_async_gather_is_bit_identical(p, periodic):
             yr = _apply(ctx, X, "registers")
             yg = _apply(ctx, X, "rings")
             y4 = _apply(ctx, X, "rings4")
+            yw = _apply(ctx, X, "whole")
+            assert torch.equal(yw, yr), (p, periodic, ncol)
             assert torch.equal(ya, yr), (p, periodic, ncol)
             assert torch.equal(yg, yr), (p, periodic, ncol)
             assert torch.equal(y4, yr), (p, periodic, ncol)
