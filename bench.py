@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gather", default="rings", choices=["async", "registers", "rings", "rings4", "whole"],
                     help="BF16x3 cell kernel gather (bulk async copies or register loads)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="filter lanes: column groups filtered concurrently on their own streams "
+                         "(0 = the library's default)")
+    ap.add_argument("--tall-kernel", default="auto", choices=["auto", "narrow", "wide"],
+                    help="tile kernel of the mixed rotations X U: 128 x 128 or 256-row tiles")
     ap.add_argument("--fp64-op", default="default", choices=["default", "cells", "matrix-free"],
                     help="binary64 cell operator")
     ap.add_argument("--no-side-arms", action="store_true",
@@ -547,6 +552,9 @@ def run_ours(args):
     ctx.set_blocking(s.block, 1)
     ctx.set_cell_tile(args.tile)
     ctx.set_cell_gather(args.gather)
+    ctx.set_gemm_kernels(tall={"auto": -1, "narrow": 0, "wide": 1}[args.tall_kernel])
+    if args.lanes:
+        ctx.set_filter_lanes(args.lanes)
     ctx.set_fp64_operator(args.fp64_op)
     n, M = s.n_sub, ctx.ndofs
     b = ctx.bounds(20, s.seed)

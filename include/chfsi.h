@@ -142,6 +142,24 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
  * do not depend on it. */
 chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile);
 
+/* Filter lanes (mixed precisions; default 1): the columns of a filter call
+ * are cut into up to `lanes` groups of whole 128-column tiles, each filtered
+ * on its own stream with its own scratch, so the memory-bound assembly of one
+ * lane overlaps the tensor-core cell products of another (the columns of the
+ * Chebyshev filter, Eq. chebFilter, are independent).  Results are identical
+ * to one lane.  Scratch per lane is sized by its columns, so the total equals
+ * one lane's.  lanes in 1..4, else CHFSI_ERR_ARG. */
+chfsi_status chfsi_set_filter_lanes(chfsi_ctx* ctx, int lanes);
+
+/* Tile kernels of the mixed-precision block products of CholGS and
+ * Rayleigh-Ritz (the overlap S = X^T X, the projection X^T H X and the
+ * rotations X U, Sec. 3.3.2-3.3.3): tall = the rotation kernel, gram = the
+ * overlap kernel; -1 (default) chooses by size, 0 = 128 x 128 output tiles,
+ * 1 = 256-row tiles (two TMEM accumulators per CTA, each operand chunk
+ * shared by twice the products).  Results are the same to rounding order
+ * of the binary32 accumulators; CHFSI_ERR_ARG for other values. */
+chfsi_status chfsi_set_gemm_kernels(chfsi_ctx* ctx, int tall, int gram);
+
 /* Variant of the BF16x3 cell kernel (results are bit-identical): 2 (default)
  * = warps gather the cell's rows of Y into registers and split them, with the
  * cell-matrix chunks and the split Y chunks in separate shared-memory rings

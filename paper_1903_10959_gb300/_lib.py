@@ -98,6 +98,8 @@ _SIGS = {
     "chfsi_build": (C.c_int, [_vp]),
     "chfsi_set_blocking": (C.c_int, [_vp, C.c_int, C.c_int]),
     "chfsi_set_cell_tile": (C.c_int, [_vp, C.c_int]),
+    "chfsi_set_gemm_kernels": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "chfsi_set_filter_lanes": (C.c_int, [_vp, C.c_int]),
     "chfsi_autotune": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), _dp]),
     "chfsi_fill_uniform": (C.c_int, [_vp, _vp, _i64, _i64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]),
@@ -303,6 +305,14 @@ class Context:
 
     def set_cell_tile(self, tile=64):
         self._check(self._lib.chfsi_set_cell_tile(self._h, int(tile)))
+
+    def set_filter_lanes(self, lanes=1):
+        """Column groups filtered concurrently on their own streams (mixed precisions)."""
+        self._check(self._lib.chfsi_set_filter_lanes(self._h, int(lanes)))
+
+    def set_gemm_kernels(self, tall=-1, gram=-1):
+        """Tile kernels of the mixed block products: -1 by size, 0 = 128 x 128, 1 = 256-row."""
+        self._check(self._lib.chfsi_set_gemm_kernels(self._h, int(tall), int(gram)))
 
     def autotune(self, X, prec="mixed"):
         """(block, tile, {(block, tile): ms}) chosen by chfsi_autotune."""

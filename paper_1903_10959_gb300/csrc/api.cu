@@ -354,8 +354,10 @@ void toc(chfsi_ctx* ctx, int slot) {
   ctx->times[slot] += ms;
 }
 
-chfsi_status filter_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
-                         double b, double a0, chfsi_precision prec) {
+// The filter of the columns [0, ncol) of X in blocks of the filter block size
+// (every step on ctx->stream, scratch in ctx->T1 / Rb / Zb).
+chfsi_status filter_range(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
+                          double b, double a0, chfsi_precision prec) {
   const HostMesh& m = ctx->mesh;
   const int B = std::max(1, std::min(ctx->filter_block, ncol));
   const size_t es = esize(prec);
@@ -395,6 +397,64 @@ chfsi_status filter_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int deg
   return CHFSI_OK;
 }
 
+// Lane l of a multi-lane filter: its stream and scratch take the place of the
+// context's for the duration of the scope.
+struct LaneScope {
+  chfsi_ctx* ctx;
+  int l;
+  cudaStream_t saved;
+  LaneScope(chfsi_ctx* c, int lane) : ctx(c), l(lane), saved(c->stream) {
+    if (l == 0) return;
+    ctx->stream = ctx->lane_stream[l];
+    std::swap(ctx->T1, ctx->laneT1[l]);
+    std::swap(ctx->Rb, ctx->laneR[l]);
+    std::swap(ctx->Zb, ctx->laneZ[l]);
+  }
+  ~LaneScope() {
+    if (l == 0) return;
+    std::swap(ctx->T1, ctx->laneT1[l]);
+    std::swap(ctx->Rb, ctx->laneR[l]);
+    std::swap(ctx->Zb, ctx->laneZ[l]);
+    ctx->stream = saved;
+  }
+};
+
+// Chebyshev filter (Eq. chebFilter).  The columns are independent, so with
+// L > 1 filter lanes (mixed precisions) they are cut into L groups of whole
+// 128-column tiles, each filtered on its own stream with its own scratch: the
+// memory-bound assembly of one lane then runs beside the tensor-core cell
+// products of another.  Every column gets the same arithmetic as with one lane.
+chfsi_status filter_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int degree, double a,
+                         double b, double a0, chfsi_precision prec) {
+  const int tiles = (ncol + 127) / 128;
+  const int L = is_mixed(prec) ? std::min(ctx->filter_lanes, tiles) : 1;
+  if (L <= 1) return filter_range(ctx, X, ldx, ncol, degree, a, b, a0, prec);
+  for (int l = 0; l < L; ++l) {
+    if (l > 0 && !ctx->lane_stream[l])
+      CK(cudaStreamCreateWithFlags(&ctx->lane_stream[l], cudaStreamNonBlocking));
+    if (!ctx->lane_ev[l]) CK(cudaEventCreateWithFlags(&ctx->lane_ev[l], cudaEventDisableTiming));
+  }
+  // the lanes start after the work queued so far on the context's stream
+  CK(cudaEventRecord(ctx->lane_ev[0], ctx->stream));
+  for (int l = 1; l < L; ++l) CK(cudaStreamWaitEvent(ctx->lane_stream[l], ctx->lane_ev[0], 0));
+  const size_t es = esize(prec);
+  chfsi_status st = CHFSI_OK;
+  int t0 = 0;
+  for (int l = 0; l < L && st == CHFSI_OK; ++l) {
+    const int nt = tiles / L + (l < tiles % L ? 1 : 0);
+    const int c0 = t0 * 128, c1 = std::min(ncol, (t0 + nt) * 128);
+    t0 += nt;
+    LaneScope scope(ctx, l);
+    st = filter_range(ctx, (char*)X + (size_t)c0 * es, ldx, c1 - c0, degree, a, b, a0, prec);
+  }
+  // the context's stream continues after every lane
+  for (int l = 1; l < L; ++l) {
+    CK(cudaEventRecord(ctx->lane_ev[l], ctx->lane_stream[l]));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[l], 0));
+  }
+  return st;
+}
+
 // S(n x n, column-major, lower part) = A^T B for the precision's storage type.
 chfsi_status gram_impl(chfsi_ctx* ctx, chfsi_precision prec, const void* A, int64_t lda,
                        const void* Bm, int64_t ldb, int n1, int n2, double* C, int64_t ldc,
@@ -430,7 +490,7 @@ chfsi_status rotate_impl(chfsi_ctx* ctx, chfsi_precision prec, void* X, int64_t 
     if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n))) != CHFSI_OK) return st;
     CK(tc_tallgemm_mixed((const float*)X, ldx, U, n, m.ndofs, n, n, (float*)ctx->rot.ptr, n, upper,
                          trans, ctx->diag_block, split3_of(prec), ctx->work.ptr,
-                         ctx->stream));
+                         ctx->stream, ctx->tall_kernel));
   }
   CK(cudaMemcpy2DAsync(X, ldx * es, ctx->rot.ptr, n * es, n * es, m.ndofs, cudaMemcpyDeviceToDevice,
                        ctx->stream));
@@ -751,6 +811,11 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
                     &ctx->scfr, &ctx->scfw, &ctx->kW, &ctx->kT1, &ctx->kG, &ctx->kS, &ctx->kwork,
                     &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);
+  for (int l = 0; l < chfsi_ctx::kMaxLanes; ++l) {
+    for (DevBuf* b : {&ctx->laneT1[l], &ctx->laneR[l], &ctx->laneZ[l]}) dfree(ctx, b->ptr, b->bytes);
+    if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
+    if (ctx->lane_ev[l]) cudaEventDestroy(ctx->lane_ev[l]);
+  }
   if (ctx->sol) cusolverDnDestroy(ctx->sol);
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
@@ -900,6 +965,21 @@ chfsi_status chfsi_set_blocking(chfsi_ctx* ctx, int filter_block, int diag_block
   if (filter_block < 1 || diag_block < 1) return fail(ctx, CHFSI_ERR_ARG, "block sizes must be >= 1");
   ctx->filter_block = filter_block;
   ctx->diag_block = diag_block;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_filter_lanes(chfsi_ctx* ctx, int lanes) {
+  CHECK_CTX();
+  if (lanes < 1 || lanes > chfsi_ctx::kMaxLanes) return fail(ctx, CHFSI_ERR_ARG, "lanes must be 1..4");
+  ctx->filter_lanes = lanes;
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_set_gemm_kernels(chfsi_ctx* ctx, int tall, int gram) {
+  CHECK_CTX();
+  if (tall < -1 || tall > 1 || gram < -1 || gram > 1) return fail(ctx, CHFSI_ERR_ARG, "kernel must be -1, 0 or 1");
+  ctx->tall_kernel = tall;
+  ctx->gram_kernel = gram;
   return CHFSI_OK;
 }
 
@@ -1168,7 +1248,7 @@ chfsi_status chfsi_rayleigh_ritz_split(chfsi_ctx* ctx, const void* X, int64_t ld
   } else {
     if ((st = grow(ctx, ctx->work, tc_tallgemm_work_bytes(n, n_fr))) != CHFSI_OK) return st;
     CK(tc_tallgemm_mixed((const float*)X, ldx, Hh, n, m.ndofs, n, n_fr, (float*)Xfr, ldfr, 0, 0, 0,
-                         split3_of(prec), ctx->work.ptr, ctx->stream));
+                         split3_of(prec), ctx->work.ptr, ctx->stream, ctx->tall_kernel));
   }
   toc(ctx, 2);
   return check_device_status(ctx, prec);

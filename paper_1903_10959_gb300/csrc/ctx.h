@@ -22,6 +22,7 @@ struct chfsi_ctx {
   chfsi_status latched = CHFSI_OK;
   std::string err;
   int filter_block = 200, diag_block = 1;
+  int tall_kernel = -1, gram_kernel = -1;   // GEMM tile kernels: -1 by size, 0 128 x 128, 1 256-wide
   int cell_tile = 64;              // columns per CTA of the tensor-core cell kernel
   int cell_gather = 2;             // BF16x3 cell kernel: 2 decoupled rings (default), 0 one ring, 1 async gather, 3 rings with 4 gather pairs
   int64_t dev_bytes = 0;
@@ -59,6 +60,13 @@ struct chfsi_ctx {
   bool scf_setup = false;          // scfb holds the load of 1 and the weights
   double scf_msum = 0.0;           // sum_j int N_j (the box volume)
   chfsi::DevBuf Db;                // density tables: M^{-1/2}, basis at Gauss points, weights
+  // filter lanes (mixed precisions): column groups filtered concurrently on
+  // their own streams, so one lane's assembly overlaps another's cell products
+  static constexpr int kMaxLanes = 4;
+  int filter_lanes = 1;
+  cudaStream_t lane_stream[kMaxLanes] = {};   // lane 0 runs on `stream`
+  cudaEvent_t lane_ev[kMaxLanes] = {};
+  chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes];
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double times[4] = {0, 0, 0, 0};

@@ -1791,31 +1791,60 @@ __global__ void tc_gram_reduce_kernel(const double* __restrict__ partial, int ns
   C[i + (int64_t)j * ldc] = s;
 }
 
-// Binary64 diagonal blocks: C[i, j] = sum_r A[r, i] B[r, j] for i / bd == j / bd
-// (i, j < min(n1, n2); BD divides 32).  Block: 8 row lanes x 32 columns; a
-// thread owns column i and accumulates its BD block partners, whose B values
-// come from neighbouring lanes by warp shuffles.  Rows are taken four at a
-// time (four loads in flight per thread, four partial sums combined in a
-// fixed order).  Products of binary32 values are exact in binary64; partial
-// sums over row chunks are reduced in fixed order.
+// Diagonal blocks of A^T B in extended precision: C[i, j] = sum_r A[r, i] B[r, j]
+// for i / bd == j / bd (i, j < min(n1, n2); BD divides 32).  Block: 8 row
+// lanes x 32 columns; a thread owns column i and accumulates its BD block
+// partners, whose B values come from neighbouring lanes by warp shuffles.
+// Every product is split exactly into p + e (p = a b rounded, e = fma(a, b, -p))
+// and summed as a float pair (Knuth's two-sum on the leading part, the
+// rounding errors and e gathered in the trailing part); every 16 products per
+// entry the pair is added into a binary64 partial sum.  This keeps the sums at
+// binary64-class accuracy (relative error ~1e-13 of sum |a b| at these
+// lengths) with two binary64 additions per 16 products: GB300's binary64 pipe
+// issues 2 operations per clock and SM against 128 binary32 ones, and the
+// plain binary64 form (two conversions and an FMA per product) was bound by
+// it.  Rows are taken four at a time (four loads in flight per thread);
+// partial sums over row chunks are reduced in fixed order.
+// (explicitly rounded operations: the two-sum must not be contracted into FMAs)
+__device__ __forceinline__ void ff_add_prod(float a, float b, float& sh, float& sl) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float t = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
 template <int BD>
-__global__ void __launch_bounds__(256) diag_gram_fp64_kernel(const float* __restrict__ A, int64_t lda,
-                                                             const float* __restrict__ B, int64_t ldb,
-                                                             int64_t M, int nd, int64_t rows_per_chunk,
-                                                             double* __restrict__ part) {
+__global__ void __launch_bounds__(256) diag_gram_ff_kernel(const float* __restrict__ A, int64_t lda,
+                                                           const float* __restrict__ B, int64_t ldb,
+                                                           int64_t M, int nd, int64_t rows_per_chunk,
+                                                           double* __restrict__ part) {
   const int lane = threadIdx.x & 31, rl = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
   const int64_t r1 = min(M, r0 + rows_per_chunk);
   const int jb = lane / BD * BD;            // first lane of this column's block
   const bool in = i < nd;
-  constexpr int NA = BD >= 8 ? 1 : 4;       // partial-sum sets (register budget)
-  double acc[4][BD];
+  double acc[BD];
+  float sh[BD], sl[BD];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int q = 0; q < BD; ++q) {
+    acc[q] = 0.0;
+    sh[q] = 0.f;
+    sl[q] = 0.f;
+  }
+  auto flush = [&]() {
 #pragma unroll
-    for (int q = 0; q < BD; ++q) acc[u][q] = 0.0;
+    for (int q = 0; q < BD; ++q) {
+      acc[q] += (double)sh[q] + (double)sl[q];
+      sh[q] = 0.f;
+      sl[q] = 0.f;
+    }
+  };
   int64_t r = r0 + rl;
+  int steps = 0;
   for (; r + 24 < r1; r += 32) {
     float a[4], b[4];
 #pragma unroll
@@ -1828,8 +1857,12 @@ __global__ void __launch_bounds__(256) diag_gram_fp64_kernel(const float* __rest
 #pragma unroll
       for (int q = 0; q < BD; ++q) {
         const float bq = BD == 1 ? b[u] : __shfl_sync(0xffffffffu, b[u], jb + q);
-        acc[u % NA][q] = fma((double)a[u], (double)bq, acc[u % NA][q]);
+        ff_add_prod(a[u], bq, sh[q], sl[q]);
       }
+    if (++steps == 4) {
+      flush();
+      steps = 0;
+    }
   }
   for (; r < r1; r += 8) {
     const float a = in ? A[r * lda + i] : 0.f;
@@ -1837,13 +1870,14 @@ __global__ void __launch_bounds__(256) diag_gram_fp64_kernel(const float* __rest
 #pragma unroll
     for (int q = 0; q < BD; ++q) {
       const float bq = BD == 1 ? b : __shfl_sync(0xffffffffu, b, jb + q);
-      acc[0][q] = fma((double)a, (double)bq, acc[0][q]);
+      ff_add_prod(a, bq, sh[q], sl[q]);
     }
   }
+  flush();
   __shared__ double red[8][32];
 #pragma unroll
   for (int q = 0; q < BD; ++q) {
-    red[rl][lane] = (acc[0][q] + acc[1][q]) + (acc[2][q] + acc[3][q]);
+    red[rl][lane] = acc[q];
     __syncthreads();
     if (rl == 0 && in) {
       double t = 0.0;
@@ -1866,9 +1900,27 @@ __global__ void diag_reduce_kernel(const double* __restrict__ part, int nchunk, 
   C[i + (int64_t)j * ldc] = s;
 }
 
+constexpr int GR_MAX_SPLIT = 16;
 size_t tc_gram_partial_bytes(int64_t M, int n1, int n2) {
   (void)M;
-  return (size_t)8 * 8 * n1 * n2 + (size_t)64 * 1024 * 1024;
+  return (size_t)8 * GR_MAX_SPLIT * n1 * n2 + (size_t)64 * 1024 * 1024;
+}
+
+// K splits of the Gram grid: the grid runs in waves of `slots` CTAs (two per
+// SM) and every CTA of a split takes the same time, so the launch lasts
+// ceil(tiles * ns / slots) CTA times of 1 / ns of the rows each; take the ns
+// that minimises that (the smaller on ties).
+int64_t tc_gram_splits(int64_t tiles, int64_t max_split, int64_t slots) {
+  int64_t best = 1;
+  double tbest = 1e300;
+  for (int64_t ns = 1; ns <= std::max<int64_t>(1, max_split); ++ns) {
+    const double t = (double)((tiles * ns + slots - 1) / slots) / (double)ns;
+    if (t < tbest * (1.0 - 1e-9)) {
+      tbest = t;
+      best = ns;
+    }
+  }
+  return best;
 }
 
 cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
@@ -1879,8 +1931,8 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
   const int64_t tiles = lower ? (int64_t)t1 * (t1 + 1) / 2 : (int64_t)t1 * t2;
   const size_t diag_bytes = (size_t)64 * 1024 * 1024;
   int64_t max_split = (int64_t)((partial_bytes - diag_bytes) / (sizeof(double) * (size_t)n1 * n2));
-  int64_t want = (2 * 152 + tiles - 1) / tiles;
-  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(std::min(want, max_split), (M + 1023) / 1024));
+  max_split = std::min<int64_t>(std::min<int64_t>(max_split, GR_MAX_SPLIT), (M + 1023) / 1024);
+  int64_t nsplit = tc_gram_splits(tiles, max_split, 2 * 152);
   int64_t rps = ((M + nsplit - 1) / nsplit + GR_KC - 1) / GR_KC * GR_KC;
   nsplit = (M + rps - 1) / rps;
   GramParams P{A, B, lda, ldb, M, n1, n2, lower, split3, rps, (double*)partial};
@@ -1895,7 +1947,7 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
   note_launch();
   tc_gram_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((double*)partial, (int)nsplit,
                                                                       n1, n2, C, ldc, lower);
-  // binary64 diagonal blocks overwrite the tensor-core values there
+  // extended-precision diagonal blocks overwrite the tensor-core values there
   if (diag_block > 0) {
     int bd = 1;
     while (bd * 2 <= std::min(diag_block, 32)) bd *= 2;
@@ -1911,12 +1963,12 @@ cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t l
     const dim3 dg(ntile, (unsigned)nchunk);
     note_launch();
     switch (bd) {
-      case 1: diag_gram_fp64_kernel<1><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
-      case 2: diag_gram_fp64_kernel<2><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
-      case 4: diag_gram_fp64_kernel<4><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
-      case 8: diag_gram_fp64_kernel<8><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
-      case 16: diag_gram_fp64_kernel<16><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
-      default: diag_gram_fp64_kernel<32><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 1: diag_gram_ff_kernel<1><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 2: diag_gram_ff_kernel<2><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 4: diag_gram_ff_kernel<4><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 8: diag_gram_ff_kernel<8><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      case 16: diag_gram_ff_kernel<16><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
+      default: diag_gram_ff_kernel<32><<<dg, 256, 0, s>>>(A, lda, B, ldb, M, nd, rpc, dpart); break;
     }
     const int64_t tot2 = (int64_t)nd * bd;
     note_launch();
@@ -1961,11 +2013,45 @@ __global__ void tc_splitu_kernel(const double* __restrict__ U, int64_t ldu, int 
   base[TG_T * TG_KC + k8_off(n, k)] = l;
 }
 
+// Diagonal-block entries of U as float pairs: Ud[col * bd + q] = (hi, lo) of
+// U[k0 + q, col] (k0 = col / bd * bd; zero outside U or, when upper, below
+// the diagonal), hi + lo = U's entry to about 2^-48 relative.
+__global__ void tc_diagu_kernel(const double* __restrict__ U, int64_t ldu, int n1, int n2, int upper,
+                                int trans, int bd, float2* __restrict__ Ud) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n2 * bd) return;
+  const int col = (int)(idx / bd), q = (int)(idx % bd);
+  const int kk = col / bd * bd + q;
+  double v = 0.0;
+  if (kk < n1 && (!upper || kk <= col)) v = trans ? U[col + (int64_t)kk * ldu] : U[kk + (int64_t)col * ldu];
+  const float h = (float)v;
+  Ud[idx] = make_float2(h, (float)(v - (double)h));
+}
+
+// acc + sum over the diagonal block of col of A[row, kk] U[kk, col] (the
+// paper's Psi L^{-1}_d term), in binary32 pairs: exact products of the
+// leading parts, two-sum accumulation, the trailing parts of U by FMA.
+__device__ __forceinline__ float tall_diag_add(float acc, const float* __restrict__ Arow,
+                                               const float2* __restrict__ Ud, int col, int bd, int n1,
+                                               int upper) {
+  const int k0 = (col / bd) * bd;
+  const int k1 = min(n1, k0 + bd);
+  float sh = acc, sl = 0.f;
+  for (int kk = k0; kk < k1; ++kk) {
+    if (upper && kk > col) break;
+    const float2 u = Ud[(int64_t)col * bd + (kk - k0)];
+    const float a = Arow[kk];
+    ff_add_prod(a, u.x, sh, sl);
+    sl = __fmaf_rn(a, u.y, sl);
+  }
+  return __fadd_rn(sh, sl);
+}
+
 struct TallParams {
   const float* A;
   int64_t lda, M;
   const float* Us;       // split U
-  const double* U;       // binary64 U for the diagonal blocks
+  const float2* Ud;      // U's diagonal-block entries as float pairs (hi, lo), n2 x bd
   int64_t ldu;
   int n1, n2, upper, trans, bd, split3;
   float* C;
@@ -2137,17 +2223,9 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
         if (row >= P.M) break;
         for (int c = lane; c < ncv; c += 32) {
           const int col = tj * TG_T + c;
-          double v = (double)E[r * EP + c];
-          if (P.bd > 0) {   // binary64 diagonal block of U
-            const int k0 = (col / P.bd) * P.bd;
-            const int k1 = min(P.n1, k0 + P.bd);
-            for (int kk = k0; kk < k1; ++kk) {
-              if (P.upper && kk > col) break;
-              const double u_ = P.trans ? P.U[col + (int64_t)kk * P.ldu] : P.U[kk + (int64_t)col * P.ldu];
-              v = fma((double)P.A[row * P.lda + kk], u_, v);
-            }
-          }
-          P.C[row * P.ldc + col] = (float)v;
+          float v = E[r * EP + c];
+          if (P.bd > 0) v = tall_diag_add(v, P.A + row * P.lda, P.Ud, col, P.bd, P.n1, P.upper);
+          P.C[row * P.ldc + col] = v;
         }
       }
     }
@@ -2157,22 +2235,306 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
   if (warp == 4) tmem_dealloc(tmem, 128);
 }
 
+// kernel < 0: the 256-row kernel takes the tall products with at least two
+// waves of its one-CTA-per-SM grid; 0 / 1 force the 128 x 128 / 256-row kernel.
+bool tc_tall_use_wide(int64_t M, int n2, int kernel) {
+  if (kernel >= 0) return kernel == 1;
+  const int64_t ctas = (M + 255) / 256 * ((n2 + 255) / 256);
+  return ctas >= 2 * 152;
+}
+
+// ----------------------------------------------------------------- tall GEMM, 256-row tiles
+// The same product as tc_tall_kernel with a 256-row x BW-column CTA tile (BW
+// <= 256, a multiple of 16, n2 split into equal column tiles): two TMEM
+// accumulators (rows 0-127 at column 0, rows 128-255 at column 256; all 512
+// columns, one CTA per SM) share every chunk of U, and every row block of A
+// is read by ceil(n2 / 256) column tiles instead of ceil(n2 / 128), which
+// halves the operand bytes each tensor-core flop pulls through L2.  Eight
+// producer warps: warp w fills row half w & 1 of the chunks i = w >> 1
+// (mod 4); the row-half-0 warp also issues the bulk copy of the chunk's
+// pre-split U (layout as tc_splitu_kernel with tile width BW).  The epilogue
+// (the same eight warps: TMEM lane quarter w % 4, accumulator w >> 2) reads
+// its rows straight from TMEM and writes 16 consecutive columns per thread.
+constexpr int TW_ROWS = 256, TW_PROD = 8, TW_THREADS = (TW_PROD + 1) * 32, TW_S = 6;
+static_assert(TW_S >= 4, "parity waits of the 4 producer groups need at least 4 stages");
+
+__host__ __device__ inline int tw_stage_bytes(int bw) { return TW_ROWS * TG_KC * 4 * 2 + bw * TG_KC * 4 * 2; }
+
+// Column tiling of n2 for the 256-row kernel: ntile tiles of bw columns.
+inline void tw_tiling(int n2, int& ntile, int& bw) {
+  ntile = (n2 + 255) / 256;
+  bw = ((n2 + ntile - 1) / ntile + 15) / 16 * 16;
+}
+
+// Bytes of the split U of either tall kernel (16-byte multiple).
+inline size_t tall_split_bytes(int n1, int n2) {
+  const int nkc = (n1 + TG_KC - 1) / TG_KC;
+  const int ntile = (n2 + TG_T - 1) / TG_T;
+  int ntw, bw;
+  tw_tiling(n2, ntw, bw);
+  const size_t narrow = (size_t)ntile * nkc * 2 * TG_T * TG_KC * 4;
+  const size_t wide = (size_t)ntw * nkc * 2 * bw * TG_KC * 4;
+  return (std::max(narrow, wide) + 15) / 16 * 16;
+}
+
+__global__ void tc_splitu_w_kernel(const double* __restrict__ U, int64_t ldu, int n1, int n2, int upper,
+                                   int trans, int bd, int bw, float* __restrict__ out) {
+  const int nkc = (n1 + TG_KC - 1) / TG_KC;
+  const int64_t per_tile = (int64_t)nkc * bw * TG_KC;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ntile = (n2 + bw - 1) / bw;
+  if (idx >= (int64_t)ntile * per_tile) return;
+  const int tile = (int)(idx / per_tile);
+  int rem = (int)(idx - (int64_t)tile * per_tile);
+  const int kc = rem / (bw * TG_KC);
+  rem -= kc * bw * TG_KC;
+  const int n = rem / TG_KC, k = rem % TG_KC;
+  const int col = tile * bw + n, kk = kc * TG_KC + k;
+  double v = 0.0;
+  if (col < n2 && kk < n1 && (!upper || kk <= col) && !(bd > 0 && kk / bd == col / bd))
+    v = trans ? U[col + (int64_t)kk * ldu] : U[kk + (int64_t)col * ldu];
+  const float h = tf32_rna((float)v);
+  const float l = tf32_rna((float)(v - (double)h));
+  float* base = out + ((int64_t)tile * nkc + kc) * 2 * bw * TG_KC;
+  base[k8_off(n, k)] = h;
+  base[bw * TG_KC + k8_off(n, k)] = l;
+}
+
+__global__ void __launch_bounds__(TW_THREADS, 1) tc_tall_wide_kernel(TallParams P, int bw) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tj = blockIdx.x;
+  const int64_t rb = (int64_t)blockIdx.y * TW_ROWS;
+  const int nkc_all = (P.n1 + TG_KC - 1) / TG_KC;
+  int kend = P.n1;
+  if (P.upper) kend = min(P.n1, (tj + 1) * bw);
+  const int nk = (kend + TG_KC - 1) / TG_KC;
+  const int SB = tw_stage_bytes(bw);
+  const uint32_t ubytes = (uint32_t)bw * TG_KC * 4 * 2;
+  const int S = TW_S;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * SB);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto emp = [&](int s) { return smem_u32(bars + S + s); };
+  const uint32_t accb = smem_u32(bars + 2 * S);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 64);
+      mbar_init(emp(s), 1);
+    }
+    mbar_init(accb, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == TW_PROD) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ncv = min(bw, P.n2 - tj * bw);
+  const int bne = (ncv + 15) / 16 * 16;
+
+  if (warp == TW_PROD) {
+    if (lane == 0 && nk > 0) {
+      const uint32_t idesc = idesc_tf32(128, bne);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % S;
+        if (!mbar_wait(full(s), (i / S) & 1) || *(volatile int*)abort_flag) {
+          atomicExch(&g_tc_status, 11);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * SB;
+        const uint32_t su = sa + TW_ROWS * TG_KC * 8;
+        const uint64_t uh = umma_desc(su, 128, 256);
+        const uint64_t ul = umma_desc(su + bw * TG_KC * 4, 128, 256);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t acc = tmem + h * 256;
+          const uint32_t ah_a = sa + h * 128 * TG_KC * 4;
+          const uint64_t ah = umma_desc(ah_a, 128, 256);
+          const uint64_t al = umma_desc(ah_a + TW_ROWS * TG_KC * 4, 128, 256);
+          if (P.split3) {
+            mma_tf32(acc, al, uh, idesc, i > 0);
+            mma_tf32(acc, ah, ul, idesc, 1);
+            mma_tf32(acc, ah, uh, idesc, 1);
+          } else {
+            mma_tf32(acc, ah, uh, idesc, i > 0);
+          }
+        }
+        umma_commit(emp(s));
+      }
+      umma_commit(accb);
+    }
+  } else {
+    const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+    const int hw = warp & 1, grp = warp >> 1;
+    int last_issued = -1;
+    // rows hw*128 + lane + 32 j, K quads kq of chunk i, into registers
+    auto load_chunk = [&](int i, float4 (&av)[4][2]) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t row = rb + hw * 128 + lane + 32 * j;
+#pragma unroll
+        for (int kq = 0; kq < 2; ++kq) {
+          const int k0 = i * TG_KC + kq * 4;
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < P.M) {
+            const float* src = P.A + row * P.lda + k0;
+            if (vec && k0 + 4 <= P.n1) {
+              t = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+              if (k0 + 0 < P.n1) t.x = __ldg(src + 0);
+              if (k0 + 1 < P.n1) t.y = __ldg(src + 1);
+              if (k0 + 2 < P.n1) t.z = __ldg(src + 2);
+              if (k0 + 3 < P.n1) t.w = __ldg(src + 3);
+            }
+          }
+          av[j][kq] = t;
+        }
+      }
+    };
+    // wait for stage i % S, split the registers into it, add the U chunk, arrive
+    auto fill_stage = [&](int i, const float4 (&av)[4][2]) -> bool {
+      const int s = i % S;
+      if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
+        atomicExch(&g_tc_status, 12);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) return false;
+      float* sa = reinterpret_cast<float*>(smem + s * SB);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = hw * 128 + lane + 32 * j;
+#pragma unroll
+        for (int kq = 0; kq < 2; ++kq) {
+          const float4 t = av[j][kq];
+          float4 h, l;
+          h.x = tf32_rna(t.x); l.x = t.x - h.x;
+          h.y = tf32_rna(t.y); l.y = t.y - h.y;
+          h.z = tf32_rna(t.z); l.z = t.z - h.z;
+          h.w = tf32_rna(t.w); l.w = t.w - h.w;
+          const int o = k8_off(r, kq * 4);
+          *reinterpret_cast<float4*>(sa + o) = h;
+          *reinterpret_cast<float4*>(sa + TW_ROWS * TG_KC + o) = l;
+        }
+      }
+      // the pre-split U chunk: one bulk copy on the same barrier, issued once
+      // the stage is free and never abandoned before this warp's arrivals
+      if (hw == 0 && lane == 0) {
+        mbar_expect_tx(full(s), ubytes);
+        bulk_g2s(smem_u32(sa + 2 * TW_ROWS * TG_KC),
+                 P.Us + ((int64_t)tj * nkc_all + i) * 2 * bw * TG_KC, ubytes, full(s));
+        last_issued = i;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(full(s));
+      return true;
+    };
+    // chunks grp, grp + 4, ...: the loads of the next chunk are in flight
+    // while the current one is split (two register sets)
+    float4 va[4][2], vb[4][2];
+    if (grp < nk) load_chunk(grp, va);
+    for (int i = grp; i < nk; i += 8) {
+      const bool more = i + 4 < nk;
+      if (more) load_chunk(i + 4, vb);
+      if (!fill_stage(i, va) || !more) break;
+      if (i + 8 < nk) load_chunk(i + 8, va);
+      if (!fill_stage(i + 4, vb)) break;
+    }
+    if (lane == 0 && last_issued >= 0 && *(volatile int*)abort_flag)
+      mbar_wait(full(last_issued % S), (last_issued / S) & 1);
+    bool okacc = true;
+    if (nk > 0) {
+      okacc = mbar_wait(accb, 0);
+      if (!okacc) atomicExch(&g_tc_status, 13);
+    }
+    tc_fence_after();
+    const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+    const int q = warp & 3, h = warp >> 2;
+    const int64_t row = rb + h * 128 + q * 32 + lane;
+    const bool cvec = ((P.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.C) & 15) == 0);
+    for (int cb = 0; cb < bne; cb += 16) {
+      float acc[16];
+      __syncwarp();
+      if (run && nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + h * 256 + cb, acc);
+        tmem_wait_ld();
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      }
+      if (!run || row >= P.M) continue;
+      const int c0 = tj * bw + cb;
+      float out[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int col = c0 + u;
+        out[u] = acc[u];
+        if (P.bd > 0 && col < P.n2)
+          out[u] = tall_diag_add(acc[u], P.A + row * P.lda, P.Ud, col, P.bd, P.n1, P.upper);
+      }
+      float* dst = P.C + row * P.ldc + c0;
+      if (cvec && c0 + 16 <= tj * bw + ncv) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4)
+          *reinterpret_cast<float4*>(dst + u) = make_float4(out[u], out[u + 1], out[u + 2], out[u + 3]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (cb + u < ncv) dst[u] = out[u];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == TW_PROD) tmem_dealloc(tmem, 512);
+}
+
 cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int64_t ldu, int64_t M,
                               int n1, int n2, float* C, int64_t ldc, int upper, int trans,
-                              int diag_block, int split3, void* work, cudaStream_t s) {
+                              int diag_block, int split3, void* work, cudaStream_t s, int kernel) {
   if (M == 0 || n2 == 0) return cudaSuccess;
   const int nkc = (n1 + TG_KC - 1) / TG_KC;
   const int ntile = (n2 + TG_T - 1) / TG_T;
   float* Us = (float*)work;
+  float2* Ud = reinterpret_cast<float2*>((char*)work + tall_split_bytes(n1, n2));
   int bd = 0;
   if (diag_block > 0) {
     bd = 1;
     while (bd * 2 <= std::min(diag_block, 32)) bd *= 2;
+    note_launch();
+    tc_diagu_kernel<<<(unsigned)(((int64_t)n2 * bd + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans,
+                                                                               bd, Ud);
+  }
+  if (tc_tall_use_wide(M, n2, kernel)) {   // 256-row tiles
+    int ntw, bw;
+    tw_tiling(n2, ntw, bw);
+    const int64_t totw = (int64_t)ntw * nkc * bw * TG_KC;
+    note_launch();
+    tc_splitu_w_kernel<<<(unsigned)((totw + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans, bd, bw,
+                                                                     Us);
+    TallParams P{A, lda, M, Us, Ud, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
+    const int smem = TW_S * tw_stage_bytes(256) + 1024;
+    static std::once_flag attrw;
+    std::call_once(attrw, [&] {
+      cudaFuncSetAttribute(tc_tall_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    dim3 grid(ntw, (unsigned)((M + TW_ROWS - 1) / TW_ROWS));
+    note_launch();
+    tc_tall_wide_kernel<<<grid, TW_THREADS, TW_S * tw_stage_bytes(bw) + 1024, s>>>(P, bw);
+    return cudaGetLastError();
   }
   const int64_t tot = (int64_t)ntile * nkc * TG_T * TG_KC;
   note_launch();
   tc_splitu_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, ldu, n1, n2, upper, trans, bd, Us);
-  TallParams P{A, lda, M, Us, U, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
+  TallParams P{A, lda, M, Us, Ud, ldu, n1, n2, upper, trans, bd, split3, C, ldc};
   const int smem = TG_S * (2 * TG_T * TG_KC * 4 * 2) + 1024;
   static std::once_flag attr;
   std::call_once(attr, [&] {
@@ -2185,9 +2547,7 @@ cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int6
 }
 
 size_t tc_tallgemm_work_bytes(int n1, int n2) {
-  const int nkc = (n1 + TG_KC - 1) / TG_KC;
-  const int ntile = (n2 + TG_T - 1) / TG_T;
-  return (size_t)ntile * nkc * 2 * TG_T * TG_KC * 4 + 256;
+  return tall_split_bytes(n1, n2) + (size_t)n2 * 32 * sizeof(float2) + 256;
 }
 
 // ----------------------------------------------------------------- nonlocal (binary32)

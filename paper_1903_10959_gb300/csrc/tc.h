@@ -109,9 +109,10 @@ size_t tc_gram_partial_bytes(int64_t M, int n1, int n2);
 cudaError_t tc_gram_mixed(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
                           int n1, int n2, double* C, int64_t ldc, int lower, int diag_block,
                           int split3, void* partial, size_t partial_bytes, cudaStream_t s);
+// kernel: -1 chooses by size, 0 the 128 x 128 tile kernel, 1 the 256-row tile kernel.
 cudaError_t tc_tallgemm_mixed(const float* A, int64_t lda, const double* U, int64_t ldu, int64_t M,
                               int n1, int n2, float* C, int64_t ldc, int upper, int trans,
-                              int diag_block, int split3, void* work, cudaStream_t s);
+                              int diag_block, int split3, void* work, cudaStream_t s, int kernel = -1);
 cudaError_t tc_nl_project(const int64_t* site_ptr, const int32_t* site_dof, const float* site_c,
                           int nsite, const float* Y, int64_t ldy, int ncol, float* Z,
                           cudaStream_t s);
