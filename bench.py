@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "mixed", "fp64", "tf32"],
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "f16x2", "mixed", "fp64", "tf32"],
                     help="bf16x3: BF16x3 cell products (the fastest mixed path); mixed: 3xTF32")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="end-to-end steps (median wall time reported)")
@@ -297,10 +297,11 @@ def run_reference(args):
 # x 2 flops x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # MMA passes the cell kernel issues per algorithmic multiply-add, by precision.
-MMA_PASSES = {"bf16x3": 6, "mixed": 3, "tf32": 1}
+MMA_PASSES = {"bf16x3": 6, "f16x2": 3, "mixed": 3, "tf32": 1}
 # Cell-matrix bytes per element each precision's cell kernel reads.
-CELL_MATRIX_BYTES = {"bf16x3": 6, "mixed": 8, "tf32": 4, "fp64": 8}
-CELL_KERNEL = {"bf16x3": "tc_cell_bf16_kernel", "mixed": "tc_cell_r_kernel",
+CELL_MATRIX_BYTES = {"bf16x3": 6, "f16x2": 4, "mixed": 8, "tf32": 4, "fp64": 8}
+CELL_KERNEL = {"bf16x3": "tc_cell_bf16_kernel", "f16x2": "tc_cell_bf16_rings_kernel<2, 0, 2>",
+               "mixed": "tc_cell_r_kernel",
                "tf32": "tc_cell_r_kernel", "fp64": "cell_fp64_kernel"}
 # The BF16x3 cell kernel each gather mode launches.
 BF16_KERNEL = {"registers": "tc_cell_bf16_kernel", "async": "tc_cell_bf16_async_kernel",
@@ -325,6 +326,9 @@ def dtype_peak(prec, peaks):
     bf = peaks.get("bf16_tflops_sustained", 1700.0)
     if prec == "bf16x3":
         return bf, "BF16 dense, measured sustained (MEASURED_PEAKS.json), %s" % peaks["source"]
+    if prec == "f16x2":
+        return bf, ("FP16 dense = measured BF16 sustained x 1 (the nominal FP16 and BF16 dense rates "
+                    "are equal), %s" % peaks["source"])
     if prec in ("mixed", "tf32"):
         return bf * 1.1 / 2.25, ("TF32 dense = measured BF16 sustained x 1.1/2.25 nominal ratio, %s"
                                  % peaks["source"])
@@ -463,7 +467,7 @@ def fp64_polish_arm(ctx, s, X, b, D_mixed, stream, mixed_s_per_iter):
     }
 
 
-def c3_arm(stream, steps=1, gather="rings"):
+def c3_arm(stream, steps=1, gather="rings", prec="bf16x3"):
     """The largest single-GPU workload (20^3 cells, p = 7, 1,000 projector
     sites, N = 3,000 + 300, block 1,100, degree 50): one warm-up and `steps`
     timed mixed (BF16x3) ChFSI iterations, with the cell-kernel roofline."""
@@ -481,19 +485,19 @@ def c3_arm(stream, steps=1, gather="rings"):
     n, M = s.n_sub, ctx.ndofs
     b = ctx.bounds(20, s.seed)
     X = torch.empty((M, n), dtype=torch.float32, device="cuda")
-    ctx.fill_uniform(X, s.seed, prec="bf16x3")
-    ctx.cholgs(X, prec="bf16x3")
-    state = {"D": ctx.rayleigh_ritz(X, prec="bf16x3")}
+    ctx.fill_uniform(X, s.seed, prec=prec)
+    ctx.cholgs(X, prec=prec)
+    state = {"D": ctx.rayleigh_ritz(X, prec=prec)}
     setup_s = time.perf_counter() - t0
     phase = np.zeros(3)
 
     def step():
         D = state["D"]
-        ctx.filter(X, s.degree, float(D[-1]), b, float(D[0]), prec="bf16x3")
+        ctx.filter(X, s.degree, float(D[-1]), b, float(D[0]), prec=prec)
         phase[0] += ctx.last_timings()[0]
-        ctx.cholgs(X, prec="bf16x3")
+        ctx.cholgs(X, prec=prec)
         phase[1] += ctx.last_timings()[1]
-        state["D"] = ctx.rayleigh_ritz(X, prec="bf16x3")
+        state["D"] = ctx.rayleigh_ritz(X, prec=prec)
         phase[2] += ctx.last_timings()[2]
 
     step()
@@ -509,7 +513,7 @@ def c3_arm(stream, steps=1, gather="rings"):
     ctx.set_kernel_timing(False)
     nblocks = -(-n // s.block)
     steps_blocks = steps * (s.degree + 1)
-    roof, asm_roof, _ = rooflines("bf16x3", s, n, M, load_peaks(), steps_blocks * n, steps_blocks,
+    roof, asm_roof, _ = rooflines(prec, s, n, M, load_peaks(), steps_blocks * n, steps_blocks,
                                   nblocks, kt[0], kt[2], kt[1], kt[3], gather=gather)
     ctx.destroy()
     del X
@@ -521,7 +525,7 @@ def c3_arm(stream, steps=1, gather="rings"):
             "phases_ms_per_step": {"filter": phase[0] / steps, "cholgs": phase[1] / steps,
                                    "rr": phase[2] / steps},
             "projector_kernels_ms_per_step": kt[4] / steps,
-            "roofline": roof, "roofline_assembly": asm_roof, "precision": "bf16x3"}
+            "roofline": roof, "roofline_assembly": asm_roof, "precision": prec}
 
 
 # ------------------------------------------------------------------ our arm
@@ -541,7 +545,7 @@ def run_ours(args):
     s = workload(args.small, args.workload, args.n_want)
     if args.block:
         s = dataclasses.replace(s, block=args.block)
-    prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec]
+    prec = {"mixed": "mixed", "fp64": "fp64", "tf32": "tf32", "bf16x3": "bf16x3", "f16x2": "f16x2"}[args.prec]
     dt = torch.float64 if prec == "fp64" else torch.float32
     stream = torch.cuda.current_stream()
     ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
@@ -708,7 +712,7 @@ def run_ours(args):
         ctx.destroy()
         del X
         torch.cuda.empty_cache()
-        side["c3"] = c3_arm(stream, gather=args.gather)
+        side["c3"] = c3_arm(stream, gather=args.gather, prec=prec if prec in ("bf16x3", "f16x2") else "bf16x3")
     if rank != 0:
         return
     cpu = None
@@ -724,7 +728,7 @@ def run_ours(args):
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3"}[prec],
+        "dtype": {"fp64": "f64", "mixed": "tf32x3", "tf32": "tf32", "bf16x3": "bf16x3", "f16x2": "f16x2"}[prec],
         "data": "synthetic",
         "config": workload_config(s, "inputs larger than L2: X %.1f GB, cell matrices %.1f GB"
                                   % (M * n * sx / 1e9, s.ncell ** 3 * ne * ne * 8 / 1e9)),

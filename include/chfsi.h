@@ -64,7 +64,14 @@ typedef enum {
   /* Binary32 storage; cell products with both operands split into three
    * bf16 terms (about 24 bits) and six kind::f16 MMAs (K = 16) accumulated
    * in FP32; Gram / rotations as CHFSI_MIXED_TF32X3. */
-  CHFSI_MIXED_BF16X3 = 3
+  CHFSI_MIXED_BF16X3 = 3,
+  /* Binary32 storage; cell products with both operands split into two fp16
+   * terms (about 22 bits, as 3xTF32) after exact power-of-two scaling (each
+   * cell matrix by its maximum, each column of the block by its maximum,
+   * undone in the epilogue), three kind::f16 MMAs (K = 16) accumulated in
+   * FP32: half the tensor work of BF16x3.  Gram / rotations as
+   * CHFSI_MIXED_TF32X3.  Single-context calls only (not the batch API). */
+  CHFSI_MIXED_F16X2 = 4
 } chfsi_precision;
 
 /* Uniform mesh of ncell[0] x ncell[1] x ncell[2] boxes on [0,len[0]] x ... .
@@ -238,7 +245,8 @@ chfsi_status chfsi_apply_noalloc(chfsi_ctx* ctx, const double* X, int64_t ldx, d
                                  int64_t ldy, int ncol);
 
 /* Test hook of the bounded device waits (no counterpart in the paper; off by
- * default).  on != 0: in later BF16x3 cell-kernel launches on this device, one
+ * default).  on != 0: in later BF16x3 cell-kernel launches on this device
+ * (gather modes 0 and 2, the default), one
  * gather warp of the first thread block withholds its arrival on the first
  * K-chunk's barrier, so the MMA warp's bounded wait (2 s) runs out; the
  * kernel unwinds (waits for its own copies in flight, frees its TMEM) and the

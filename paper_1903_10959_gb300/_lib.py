@@ -16,9 +16,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libchfsi.so")
 
-FP64, MIXED_TF32X3, MIXED_TF32, MIXED_BF16X3 = 0, 1, 2, 3
+FP64, MIXED_TF32X3, MIXED_TF32, MIXED_BF16X3, MIXED_F16X2 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "mixed": MIXED_TF32X3, "tf32x3": MIXED_TF32X3, "tf32": MIXED_TF32,
-              "bf16x3": MIXED_BF16X3}
+              "bf16x3": MIXED_BF16X3, "f16x2": MIXED_F16X2}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_SPD", 5: "ERR_EIG",
           6: "ERR_STATE", 7: "ERR_TIMEOUT"}

@@ -126,10 +126,11 @@ chfsi_status grow(chfsi_ctx* ctx, DevBuf& b, size_t bytes) {
 }
 
 bool is_mixed(chfsi_precision p) {
-  return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32 || p == CHFSI_MIXED_BF16X3;
+  return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_TF32 || p == CHFSI_MIXED_BF16X3 ||
+         p == CHFSI_MIXED_F16X2;
 }
-// Gram and tall GEMMs: 3xTF32 for both three-term precisions, 1xTF32 otherwise.
-int split3_of(chfsi_precision p) { return p == CHFSI_MIXED_TF32X3 || p == CHFSI_MIXED_BF16X3; }
+// Gram and tall GEMMs: 3xTF32 for the binary32-accurate precisions, 1xTF32 for TF32.
+int split3_of(chfsi_precision p) { return p != CHFSI_MIXED_TF32; }
 // Columns per block of the binary64 staging copies (residuals, binary64 RR apply).
 constexpr int kStage64 = 512;
 // Whether the binary64 path uses the matrix-free cell apply when the context
@@ -139,7 +140,7 @@ constexpr bool kMatrixFreeDefault = true;
 // blocks, projector and binary64 staging buffers); later calls regrow it.
 void release_scratch(chfsi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot}) {
+  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot, &ctx->cmaxb}) {
     dfree(ctx, b->ptr, b->bytes);
     b->ptr = nullptr;
     b->bytes = 0;
@@ -167,7 +168,7 @@ void free_device_data(chfsi_ctx* ctx) {
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
   release(ctx, ctx->d_wv, ctx->wv.size() * 8);
   release(ctx, ctx->d_fac, ctx->fac.size() * 8);
-  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes);   // packed copies (0 when never packed)
+  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes);   // packed copies (0 when never packed)
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
@@ -185,7 +186,8 @@ void free_device_data(chfsi_ctx* ctx) {
 // Yout = alpha (H~ Yin - shift Yin) + beta Yprev, colour by colour.
 chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, int64_t ld_in,
                         void* Yout, int64_t ld_out, const void* Yprev, int64_t ld_prev, int ncol,
-                        double alpha, double beta, double shift) {
+                        double alpha, double beta, double shift, const uint32_t* cmax_in = nullptr,
+                        uint32_t* cmax_out = nullptr) {
   const HostMesh& m = ctx->mesh;
   const int B = std::max(ncol, 1);
   const size_t es = esize(prec);
@@ -251,6 +253,15 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     return fail(ctx, CHFSI_ERR_STATE, "no cell matrices: the potential was set on the device "
                                       "(binary64 only until chfsi_build)");
   const bool bf16 = prec == CHFSI_MIXED_BF16X3;
+  const bool f16 = prec == CHFSI_MIXED_F16X2;
+  if (f16 && !ctx->tc.f16) {
+    cudaError_t pe = tc_pack_f16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("FP16x2 cell data: ") + cudaGetErrorString(pe));
+    }
+  }
   if (bf16 && !ctx->tc.bf) {
     cudaError_t pe = tc_pack_bf16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
     if (pe != cudaSuccess) {
@@ -259,7 +270,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
                   std::string("BF16x3 cell data: ") + cudaGetErrorString(pe));
     }
   }
-  if (!bf16 && !ctx->tc.hi) {
+  if (!bf16 && !f16 && !ctx->tc.hi) {
     cudaError_t pe = tc_pack_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
     if (pe != cudaSuccess) {
       cudaGetLastError();
@@ -285,9 +296,16 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
   ra.tile = ctx->cell_tile;
   ra.gather = ctx->cell_gather;
+  if (f16 && !cmax_in) {   // column maxima of the input block (the scales of its fp16 split)
+    if ((st = grow(ctx, ctx->cmaxb, (size_t)3 * ncol * sizeof(uint32_t))) != CHFSI_OK) return st;
+    uint32_t* cm = (uint32_t*)ctx->cmaxb.ptr + 2 * (size_t)ncol;
+    CK(tc_colmax_launch((const float*)Yin, ld_in, m.ndofs, ncol, cm, ctx->stream));
+    cmax_in = cm;
+  }
   {
     KTimer kt(ctx, 0);
-    if (bf16) CK(tc_cell_bf16_launch(ctx->tc, ra, ctx->stream));
+    if (f16) CK(tc_cell_f16_launch(ctx->tc, ra, cmax_in, ctx->stream));
+    else if (bf16) CK(tc_cell_bf16_launch(ctx->tc, ra, ctx->stream));
     else CK(tc_cell_r_launch(ctx->tc, ra, ctx->stream));
   }
   KTimer kt(ctx, 1);
@@ -312,7 +330,8 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ap.alpha = (float)alpha;
   ap.beta = (float)beta;
   ap.shift = (float)shift;
-  CK(tc_assemble_launch(ap, ctx->stream));
+  if (cmax_out) CK(tc_assemble_cmax_launch(ap, cmax_out, ctx->stream));
+  else CK(tc_assemble_launch(ap, ctx->stream));
   return CHFSI_OK;
 }
 
@@ -373,6 +392,14 @@ chfsi_status filter_range(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int de
     int64_t lds[2] = {ldx, (int64_t)nb};
     int cur = 0;  // buffer holding Y_k
     double sig = s1;
+    // FP16x2: each step's assembly leaves the column maxima of its output, the
+    // next step's input (two alternating arrays; the first step measures X)
+    uint32_t* cm[2] = {nullptr, nullptr};
+    if (prec == CHFSI_MIXED_F16X2) {
+      if ((st = grow(ctx, ctx->cmaxb, (size_t)3 * nb * sizeof(uint32_t))) != CHFSI_OK) return st;
+      cm[0] = (uint32_t*)ctx->cmaxb.ptr;
+      cm[1] = cm[0] + nb;
+    }
     for (int k = 1; k <= degree; ++k) {
       double alpha, beta;
       if (k == 1) {
@@ -386,7 +413,7 @@ chfsi_status filter_range(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int de
       }
       const int nxt = 1 - cur;  // holds Y_{k-2} (or is free at k = 1)
       st = apply_step(ctx, prec, bufs[cur], lds[cur], bufs[nxt], lds[nxt], bufs[nxt], lds[nxt], nb,
-                      alpha, beta, c);
+                      alpha, beta, c, k == 1 ? nullptr : cm[cur], k == degree ? nullptr : cm[nxt]);
       if (st != CHFSI_OK) return st;
       cur = nxt;
     }
@@ -409,12 +436,14 @@ struct LaneScope {
     std::swap(ctx->T1, ctx->laneT1[l]);
     std::swap(ctx->Rb, ctx->laneR[l]);
     std::swap(ctx->Zb, ctx->laneZ[l]);
+    std::swap(ctx->cmaxb, ctx->laneC[l]);
   }
   ~LaneScope() {
     if (l == 0) return;
     std::swap(ctx->T1, ctx->laneT1[l]);
     std::swap(ctx->Rb, ctx->laneR[l]);
     std::swap(ctx->Zb, ctx->laneZ[l]);
+    std::swap(ctx->cmaxb, ctx->laneC[l]);
     ctx->stream = saved;
   }
 };
@@ -808,11 +837,13 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   ctx->d_kfac = nullptr;
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
+                    &ctx->cmaxb,
                     &ctx->scfr, &ctx->scfw, &ctx->kW, &ctx->kT1, &ctx->kG, &ctx->kS, &ctx->kwork,
                     &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);
   for (int l = 0; l < chfsi_ctx::kMaxLanes; ++l) {
-    for (DevBuf* b : {&ctx->laneT1[l], &ctx->laneR[l], &ctx->laneZ[l]}) dfree(ctx, b->ptr, b->bytes);
+    for (DevBuf* b : {&ctx->laneT1[l], &ctx->laneR[l], &ctx->laneZ[l], &ctx->laneC[l]})
+      dfree(ctx, b->ptr, b->bytes);
     if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
     if (ctx->lane_ev[l]) cudaEventDestroy(ctx->lane_ev[l]);
   }

@@ -66,7 +66,8 @@ struct chfsi_ctx {
   int filter_lanes = 1;
   cudaStream_t lane_stream[kMaxLanes] = {};   // lane 0 runs on `stream`
   cudaEvent_t lane_ev[kMaxLanes] = {};
-  chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes];
+  chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes], laneC[kMaxLanes];
+  chfsi::DevBuf cmaxb;             // FP16x2: column maxima of the filter's blocks (3 x ncol words)
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double times[4] = {0, 0, 0, 0};

@@ -30,6 +30,7 @@
 #include <mutex>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.h"
 #include "tc.h"
@@ -41,8 +42,9 @@ using namespace ptx;
 
 __device__ int g_tc_status = 0;   // nonzero after a bounded wait gave up
 // Test hook of the bounded waits (0 = off, the default): when set, gather warp
-// 0 of the first CTA of the BF16x3 cell kernel withholds its arrival on the
-// first chunk's full barrier, so that the MMA warp's wait on it runs out.
+// 0 of the first CTA of the BF16x3 cell kernel (the shared-ring and the
+// decoupled-ring forms) withholds its arrival on the first chunk's full
+// barrier, so that the MMA warp's wait on it runs out.
 __device__ int g_tc_withhold = 0;
 
 constexpr int CELL_BN = 64;       // default columns per CTA (128 selectable)
@@ -116,6 +118,8 @@ cudaError_t tc_pack_from_device(TcCellData& d, const double* dHt, cudaStream_t s
 void tc_free(TcCellData& d) {
   if (d.hi) cudaFree(d.hi);
   if (d.bf) cudaFree(d.bf);
+  if (d.f16) cudaFree(d.f16);
+  if (d.f16_inv) cudaFree(d.f16_inv);
   d = TcCellData();
 }
 
@@ -174,6 +178,20 @@ __device__ __forceinline__ void bf16_split3_pair(float x0, float x1, uint32_t& w
   w3 = cvt_bf16x2(s1, s0);
 }
 
+// Two-term fp16 split of two binary32 values, packed as the MMA operand holds
+// them: one cvt.rn.f16x2.f32 per term, the remainders exact in binary32.
+__device__ __forceinline__ uint32_t cvt_f16x2(float hi, float lo) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ void f16_split2_pair(float x0, float x1, uint32_t& w1, uint32_t& w2) {
+  w1 = cvt_f16x2(x1, x0);
+  const float r0 = x0 - __half2float(__ushort_as_half((unsigned short)(w1 & 0xffffu)));
+  const float r1 = x1 - __half2float(__ushort_as_half((unsigned short)(w1 >> 16)));
+  w2 = cvt_f16x2(r1, r0);
+}
+
 __global__ void tc_pack_bf16_kernel(const double* __restrict__ Ht, uint16_t* __restrict__ out,
                                     int64_t ncells, int ne, int mt, int nk16) {
   const int64_t per_chunk = (int64_t)mt * 2048;   // elements of one term, all tiles
@@ -211,6 +229,86 @@ cudaError_t tc_pack_bf16_from_device(TcCellData& d, const double* dHt, cudaStrea
   const int64_t n = d.ncells * (int64_t)nk16 * d.mt * 2048;
   note_launch();
   tc_pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dHt, d.bf, d.ncells, d.ne, d.mt, nk16);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- FP16x2 packing
+// Two fp16 terms carry about 22 significant bits, within a factor four of
+// binary32, and fp16 MMAs run at the bf16 rate: three kind::f16 MMAs per
+// chunk (h1 y2 + h2 y1 + h1 y1; the dropped h2 y2 is 2^-22 relative) against
+// BF16x3's six.  fp16's range is narrow, so each operand is scaled by a power
+// of two first (exact): each cell matrix by 2^s_e with max |2^s_e H~_e| in
+// [2^13, 2^14), each column of the block likewise from its maximum, and the
+// epilogue multiplies the product back by 2^-s_e 2^-t_c.  Same layout as the
+// BF16x3 copy with two terms per chunk.
+
+// Power-of-two scale taking a maximum m into [2^13, 2^14) (1 for m = 0 or not finite).
+__device__ __forceinline__ float f16_scale_of(float m) {
+  if (!(m > 0.f) || !(m <= 3.0e38f)) return 1.f;
+  int E;
+  frexpf(m, &E);                       // m = f 2^E, f in [0.5, 1)
+  return ldexpf(1.f, 14 - E);
+}
+
+__global__ void __launch_bounds__(256) tc_cell_scale_kernel(const double* __restrict__ Ht, int ne,
+                                                            float* __restrict__ inv) {
+  const int64_t e = blockIdx.x;
+  const double* h = Ht + e * (int64_t)ne * ne;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < ne * ne; i += blockDim.x) m = fmax(m, fabs(h[i]));
+  __shared__ double red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) inv[e] = 1.f / f16_scale_of((float)red[0]);
+}
+
+__global__ void tc_pack_f16_kernel(const double* __restrict__ Ht, const float* __restrict__ inv,
+                                   uint16_t* __restrict__ out, int64_t ncells, int ne, int mt, int nk16) {
+  const int64_t per_chunk = (int64_t)mt * 2048;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ncells * nk16 * per_chunk) return;
+  const int64_t e = idx / (nk16 * per_chunk);
+  int64_t rem = idx - e * nk16 * per_chunk;
+  const int kc = (int)(rem / per_chunk);
+  rem -= (int64_t)kc * per_chunk;
+  const int t = (int)(rem / 2048);
+  const int w = (int)(rem - t * 2048);
+  const int r = w / BF_KC, k = w % BF_KC;
+  const int row = t * 128 + r, col = kc * BF_KC + k;
+  const double v = (row < ne && col < ne) ? Ht[(e * ne + row) * (int64_t)ne + col] : 0.0;
+  const double x = v * (double)(1.f / inv[e]);   // exact: a power of two
+  const __half h1 = __float2half_rn((float)x);
+  const __half h2 = __float2half_rn((float)(x - (double)__half2float(h1)));
+  uint16_t* base = out + (e * nk16 + kc) * 2 * per_chunk + (int64_t)t * 2048 + bf_elem_off(r, k);
+  base[0] = __half_as_ushort(h1);
+  base[per_chunk] = __half_as_ushort(h2);
+}
+
+cudaError_t tc_pack_f16_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                    int64_t* dev_bytes) {
+  const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  const size_t terms = (size_t)d.ncells * nk16 * 2 * d.mt * 2048 * sizeof(uint16_t);
+  cudaError_t e = cudaMalloc(&d.f16, terms);
+  if (e == cudaSuccess) e = cudaMalloc(&d.f16_inv, (size_t)d.ncells * sizeof(float));
+  if (e != cudaSuccess) {
+    if (d.f16) cudaFree(d.f16);
+    d.f16 = nullptr;
+    d.f16_inv = nullptr;
+    d.f16_bytes = 0;
+    return e;
+  }
+  d.f16_bytes = terms + (size_t)d.ncells * sizeof(float);
+  if (dev_bytes) *dev_bytes += (int64_t)d.f16_bytes;
+  note_launch();
+  tc_cell_scale_kernel<<<(unsigned)d.ncells, 256, 0, s>>>(dHt, d.ne, d.f16_inv);
+  const int64_t n = d.ncells * (int64_t)nk16 * d.mt * 2048;
+  note_launch();
+  tc_pack_f16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dHt, d.f16_inv, d.f16, d.ncells, d.ne,
+                                                                 d.mt, nk16);
   return cudaGetLastError();
 }
 
@@ -269,6 +367,8 @@ struct RParams {
   int nsys, parity;
   int64_t ldr;              // row stride of R (>= ncol)
   int64_t e_off;            // first cell of this launch (grids of at most 65535 cells)
+  const uint32_t* cmax;     // FP16x2: column maxima of |Yin| (binary32 bits), index c0 + c
+  const float* cinv;        // FP16x2: per-cell inverse scales
 };
 
 template <int BN, bool MULTI>
@@ -996,8 +1096,9 @@ struct BfrPlan {
   int np, nh, alloc, sm, sy, total;
 };
 // npair gather warp pairs; each pair owns the Y stages i % npair of its
-// chunks i = pair (mod npair), so its parity waits stay sound.
-__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair) {
+// chunks i = pair (mod npair), so its parity waits stay sound.  nt: terms per
+// operand (3 for BF16x3, 2 for FP16x2).
+__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3) {
   const BfPlan b = bf_plan(ne);
   BfrPlan r;
   r.np = b.np;
@@ -1005,7 +1106,7 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair) {
   r.alloc = b.alloc;
   const int per_sm = 512 / b.alloc >= 3 ? 3 : 512 / b.alloc;
   const int budget = (per_sm >= 3 ? 72 : (per_sm == 2 ? 111 : 200)) * 1024 - kCellSmemTail;
-  const int mstage = 3 * b.nh * 32, ystage = BF_YT;
+  const int mstage = nt * b.nh * 32, ystage = nt * 128 * BF_KC * 2;
   r.sy = npair;
   r.sm = (budget - r.sy * ystage) / mstage;
   if (r.sm > 8) r.sm = 8;
@@ -1017,15 +1118,19 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair) {
 // MULTI: grid x runs over the (system, cell, column tile, row part) items of
 // a batch (TcBatchSys: A = the system's packed BF16x3 copy, tiles = column
 // tiles x parts, items of system s from item0), all systems of one degree.
-template <int NPAIR, bool MULTI>
+// NT = 2: the FP16x2 form (P.A the fp16 terms, P.cinv the per-cell inverse
+// scales, P.cmax the column maxima of Yin): three MMAs per chunk.
+template <int NPAIR, bool MULTI, int NT = 3>
 __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
+  static_assert(NT == 3 || (NT == 2 && !MULTI), "BF16x3, or single-system FP16x2");
   constexpr int NTHR = (2 * NPAIR + 2) * 32;
   constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
+  constexpr int YT = NT * 128 * BF_KC * 2;   // Y stage bytes
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int64_t e = P.e_off + blockIdx.y;
   const int ne = P.ne, nk = P.nk;
-  const BfrPlan B = bfr_plan(ne, NPAIR);
+  const BfrPlan B = bfr_plan(ne, NPAIR, NT);
   int h = blockIdx.x % B.np;
   int c0 = (blockIdx.x / B.np) * 128;
   if (MULTI) {   // item -> (system, cell, tile, part): binary search over the systems' first items
@@ -1053,9 +1158,9 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   const int r0 = h * B.nh;
   const int SM = B.sm, SY = B.sy;
   const int hrow = B.nh * 32;
-  const int mstage = 3 * hrow;
+  const int mstage = NT * hrow;
   unsigned char* ybase = smem + SM * mstage;                   // Y term stages
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * BF_YT);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * YT);
   // fa[SM] (matrix full, tx), ea[SM] (matrix empty), fy[SY] (Y full, 64), ey[SY] (Y empty), acc
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SM + 2 * SY + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -1094,7 +1199,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   if (warp == WPROD) {
     if (lane == 0) {
       const int64_t term_bytes = (int64_t)P.mt * 4096;
-      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * 3 * term_bytes + (int64_t)r0 * 32;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % SM;
@@ -1105,10 +1210,10 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         }
         if (*(volatile int*)abort_flag) break;
         const uint32_t dst = mbase + s * mstage;
-        mbar_arrive_expect_tx(fa(s), 3 * hrow);
+        mbar_arrive_expect_tx(fa(s), NT * hrow);
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
-          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * 3 + p) * term_bytes, hrow, fa(s));
+        for (int p = 0; p < NT; ++p)
+          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * NT + p) * term_bytes, hrow, fa(s));
         ++issued;
       }
       if (*(volatile int*)abort_flag)
@@ -1116,7 +1221,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     }
   } else if (warp == WMMA) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, B.nh);
+      const uint32_t idesc = NT == 3 ? idesc_bf16(128, B.nh) : idesc_f16(128, B.nh);
       for (int i = 0; i < nk; ++i) {
         const int sa = i % SM, sy = i % SY;
         if (!mbar_wait(fa(sa), (i / SM) & 1) || !mbar_wait(fy(sy), (i / SY) & 1) ||
@@ -1126,20 +1231,26 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
           break;
         }
         tc_fence_after();
-        const uint32_t yb = ysb + sy * BF_YT;
+        const uint32_t yb = ysb + sy * YT;
         const uint32_t hb = mbase + sa * mstage;
-        uint64_t y[3], hd[3];
+        uint64_t y[NT], hd[NT];
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
+        for (int p = 0; p < NT; ++p) {
           y[p] = umma_desc(yb + p * 4096, 128, 256);
           hd[p] = umma_desc(hb + p * hrow, 128, 256);
         }
-        mma_f16(tmem, y[0], hd[2], idesc, i > 0);
-        mma_f16(tmem, y[1], hd[1], idesc, 1);
-        mma_f16(tmem, y[2], hd[0], idesc, 1);
-        mma_f16(tmem, y[0], hd[1], idesc, 1);
-        mma_f16(tmem, y[1], hd[0], idesc, 1);
-        mma_f16(tmem, y[0], hd[0], idesc, 1);
+        if (NT == 3) {
+          mma_f16(tmem, y[0], hd[NT - 1], idesc, i > 0);
+          mma_f16(tmem, y[1], hd[1], idesc, 1);
+          mma_f16(tmem, y[NT - 1], hd[0], idesc, 1);
+          mma_f16(tmem, y[0], hd[1], idesc, 1);
+          mma_f16(tmem, y[1], hd[0], idesc, 1);
+          mma_f16(tmem, y[0], hd[0], idesc, 1);
+        } else {
+          mma_f16(tmem, y[0], hd[1], idesc, i > 0);
+          mma_f16(tmem, y[1], hd[0], idesc, 1);
+          mma_f16(tmem, y[0], hd[0], idesc, 1);
+        }
         umma_commit(ea(sa));
         umma_commit(ey(sy));
       }
@@ -1148,6 +1259,16 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   } else {
     // gather + split exactly as tc_cell_bf16_kernel; Y stage of chunk i is i % SY
     const int pair = warp >> 1, q = warp & 1;
+    // test hook (off by default): warp 0 of the first CTA withholds its first arrival
+    const bool withhold = g_tc_withhold != 0 && blockIdx.x == 0 && blockIdx.y == 0 && P.e_off == 0;
+    float tsc[4] = {1.f, 1.f, 1.f, 1.f};   // FP16x2: power-of-two scales of the lane's columns
+    if (NT == 2) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        if (c < ncv) tsc[u] = f16_scale_of(__uint_as_float(P.cmax[c0 + c]));
+      }
+    }
     for (int i = pair; i < nk; i += NPAIR) {
       const int s = i % SY;
       float v[8][4];
@@ -1167,20 +1288,24 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         *(volatile int*)abort_flag = 1;
       }
       if (*(volatile int*)abort_flag) break;
-      uint16_t* ys = reinterpret_cast<uint16_t*>(ybase + s * BF_YT);
+      uint16_t* ys = reinterpret_cast<uint16_t*>(ybase + s * YT);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int o = bf_elem_off(lane + 32 * u, q * 8);
-        uint32_t w[3][4];
+        uint32_t w[NT][4];
 #pragma unroll
-        for (int a = 0; a < 8; a += 2)
-          bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[2][a / 2]);
+        for (int a = 0; a < 8; a += 2) {
+          if (NT == 3)
+            bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[NT - 1][a / 2]);
+          else
+            f16_split2_pair(v[a][u] * tsc[u], v[a + 1][u] * tsc[u], w[0][a / 2], w[1][a / 2]);
+        }
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+        for (int p = 0; p < NT; ++p)
           *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
       }
       fence_proxy_async_smem();
-      mbar_arrive(fy(s));
+      if (!(withhold && warp == 0 && i == 0)) mbar_arrive(fy(s));
     }
     // epilogue: warps 0-3 (TMEM lane quarter = warp % 4); further gather warps are done
     if (warp < 4) {
@@ -1193,6 +1318,8 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
     const int c = warp * 32 + lane;
     float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    // FP16x2: undo the cell's and the column's scales (exact powers of two)
+    const float back = NT == 2 && c < ncv ? P.cinv[e] / f16_scale_of(__uint_as_float(P.cmax[c0 + c])) : 1.f;
     for (int cb = 0; cb < B.nh; cb += 16) {
       float acc[16];
       __syncwarp();
@@ -1203,7 +1330,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
       if (!run || c >= ncv) continue;
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = acc[j];
+        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = NT == 2 ? acc[j] * back : acc[j];
     }
     }
   }
@@ -1460,6 +1587,30 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t tc_cell_f16_launch(const TcCellData& d, const TcApplyArgs& a, const uint32_t* cmax,
+                               cudaStream_t s) {
+  if (a.ncells == 0 || a.ncol == 0) return cudaSuccess;
+  if (!d.f16 || !d.f16_inv || !cmax) return cudaErrorInvalidValue;
+  const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  const BfPlan B = bf_plan(d.ne);
+  if (B.np * B.nh > d.mt * 128) return cudaErrorInvalidValue;
+  RParams P{reinterpret_cast<const float*>(d.f16), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
+            nk16, 1, nullptr, 0, 0, a.ncol, 0, cmax, d.f16_inv};
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+  });
+  const BfrPlan BR = bfr_plan(d.ne, 2, 2);
+  for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
+    P.e_off = e0;
+    dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+    note_launch();
+    tc_cell_bf16_rings_kernel<2, false, 2><<<grid, 6 * 32, BR.total, s>>>(P);
+  }
+  return cudaGetLastError();
+}
+
 int tc_bf16_parts(int ne) { return bf_plan(ne).np; }
 
 cudaError_t tc_cell_bf16_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t nitems, int ne, int mt,
@@ -1488,13 +1639,11 @@ cudaError_t tc_cell_bf16_multi_launch(const TcBatchSys* d_sys, int nsys, int64_t
 // list), then applies the three-term update.  Y_out may alias Y_prev (each
 // element is read before it is written by the same thread); it must not
 // alias Y_in.
+// The update of unknown j, columns c .. c + 3 (fewer at the block's edge);
+// absout (when not null) receives |Y_out| of the four columns (0 past the edge).
 template <bool NL>
-__global__ void __launch_bounds__(256) tc_assemble_kernel(AssembleParams P) {
-  const int nq = (P.ncol + 3) / 4;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= P.M * nq) return;
-  const int64_t j = idx / nq;
-  const int c = (int)(idx - j * nq) * 4;
+__device__ __forceinline__ void assemble_quad(const AssembleParams& P, int64_t j, int c,
+                                              float* absout = nullptr) {
   const int nc = min(4, P.ncol - c);
   const bool v4 = P.vec && nc == 4;
   float sum[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1559,6 +1708,105 @@ __global__ void __launch_bounds__(256) tc_assemble_kernel(AssembleParams P) {
   } else {
     for (int u = 0; u < nc; ++u) dst[u] = out[u];
   }
+  if (absout) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) absout[u] = u < nc ? fabsf(out[u]) : 0.f;
+  }
+}
+
+// Each thread: one unknown j, 4 consecutive columns.  Sums the cell rows
+// holding j in ascending cell order, adds the projector term (when Z is set:
+// sum over the sites touching j of the h-scaled coefficients times the
+// projected block Z, the expansion half of H~_nl, in the order of j's site
+// list), then applies the three-term update.  Y_out may alias Y_prev (each
+// element is read before it is written by the same thread); it must not
+// alias Y_in.
+template <bool NL>
+__global__ void __launch_bounds__(256) tc_assemble_kernel(AssembleParams P) {
+  const int nq = (P.ncol + 3) / 4;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= P.M * nq) return;
+  const int64_t j = idx / nq;
+  const int c = (int)(idx - j * nq) * 4;
+  assemble_quad<NL>(P, j, c);
+}
+
+// The same per-element update with the column maxima of |Y_out|: block (32,
+// 8) takes 128 columns (a quad per lane) of every 8-th row group; each thread
+// keeps its quad's maximum over its rows, the block reduces over its 8 row
+// lanes and adds one atomicMax per column (binary32 bits of a non-negative
+// value order as unsigned integers).
+template <bool NL>
+__global__ void __launch_bounds__(256) tc_assemble_cmax_kernel(AssembleParams P, uint32_t* __restrict__ cmax) {
+  const int nq = (P.ncol + 3) / 4;
+  const int qd = blockIdx.x * 32 + threadIdx.x;
+  float m[4] = {0.f, 0.f, 0.f, 0.f};
+  if (qd < nq) {
+    const int c = qd * 4;
+    for (int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y; j < P.M; j += (int64_t)gridDim.y * 8) {
+      float a[4];
+      assemble_quad<NL>(P, j, c, a);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = fmaxf(m[u], a[u]);
+    }
+  }
+  __shared__ float red[8][32][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) red[threadIdx.y][threadIdx.x][u] = m[u];
+  __syncthreads();
+  if (threadIdx.y == 0 && qd < nq) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float t = red[0][threadIdx.x][u];
+      for (int w = 1; w < 8; ++w) t = fmaxf(t, red[w][threadIdx.x][u]);
+      if (qd * 4 + u < P.ncol) atomicMax(cmax + qd * 4 + u, __float_as_uint(t));
+    }
+  }
+}
+
+// Column maxima of |Y| with the same mapping.
+__global__ void __launch_bounds__(256) tc_colmax_kernel(const float* __restrict__ Y, int64_t ld, int64_t M,
+                                                        int ncol, uint32_t* __restrict__ cmax) {
+  const int nq = (ncol + 3) / 4;
+  const int qd = blockIdx.x * 32 + threadIdx.x;
+  float m[4] = {0.f, 0.f, 0.f, 0.f};
+  if (qd < nq) {
+    const int c = qd * 4;
+    const int nc = min(4, ncol - c);
+    for (int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y; j < M; j += (int64_t)gridDim.y * 8)
+      for (int u = 0; u < nc; ++u) m[u] = fmaxf(m[u], fabsf(__ldg(Y + j * ld + c + u)));
+  }
+  __shared__ float red[8][32][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) red[threadIdx.y][threadIdx.x][u] = m[u];
+  __syncthreads();
+  if (threadIdx.y == 0 && qd < nq) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float t = red[0][threadIdx.x][u];
+      for (int w = 1; w < 8; ++w) t = fmaxf(t, red[w][threadIdx.x][u]);
+      if (qd * 4 + u < ncol) atomicMax(cmax + qd * 4 + u, __float_as_uint(t));
+    }
+  }
+}
+
+// Row groups of the column-maximum grids: about 8 blocks per SM over all columns.
+static unsigned cmax_row_blocks(int64_t M, int ncol) {
+  const int64_t xs = ((ncol + 3) / 4 + 31) / 32;
+  int64_t ys = std::max<int64_t>(1, (8 * 152 + xs - 1) / xs);
+  ys = std::min<int64_t>(ys, std::max<int64_t>(1, (M + 7) / 8));
+  return (unsigned)std::min<int64_t>(ys, 65535);
+}
+
+cudaError_t tc_colmax_launch(const float* Y, int64_t ld, int64_t M, int ncol, uint32_t* cmax,
+                             cudaStream_t s) {
+  if (ncol <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(cmax, 0, (size_t)ncol * sizeof(uint32_t), s);
+  if (e != cudaSuccess || M <= 0) return e;
+  dim3 grid((unsigned)(((ncol + 3) / 4 + 31) / 32), cmax_row_blocks(M, ncol));
+  note_launch();
+  tc_colmax_kernel<<<grid, dim3(32, 8), 0, s>>>(Y, ld, M, ncol, cmax);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_assemble_launch(const AssembleParams& P0, cudaStream_t s) {
@@ -1575,6 +1823,25 @@ cudaError_t tc_assemble_launch(const AssembleParams& P0, cudaStream_t s) {
     tc_assemble_kernel<true><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P);
   else
     tc_assemble_kernel<false><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_assemble_cmax_launch(const AssembleParams& P0, uint32_t* cmax, cudaStream_t s) {
+  if (P0.ncol <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(cmax, 0, (size_t)P0.ncol * sizeof(uint32_t), s);
+  if (e != cudaSuccess || P0.M <= 0) return e;
+  AssembleParams P = P0;
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  P.vec = (P.ncol & 3) == 0 && al16(P.R) && (!P.Z || al16(P.Z));
+  P.vin = (P.ld_in & 3) == 0 && al16(P.Yin);
+  P.vprev = P.Yprev && (P.ld_prev & 3) == 0 && al16(P.Yprev);
+  P.vout = (P.ld_out & 3) == 0 && al16(P.Yout);
+  dim3 grid((unsigned)(((P.ncol + 3) / 4 + 31) / 32), cmax_row_blocks(P.M, P.ncol));
+  note_launch();
+  if (P.Z)
+    tc_assemble_cmax_kernel<true><<<grid, dim3(32, 8), 0, s>>>(P, cmax);
+  else
+    tc_assemble_cmax_kernel<false><<<grid, dim3(32, 8), 0, s>>>(P, cmax);
   return cudaGetLastError();
 }
 
@@ -1724,20 +1991,21 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
   } else {
     // lane l owns the tile columns l, l + 32, l + 64, l + 96 (conflict-free split stores)
     const int ia = ti * GR_T + lane, jb = tj * GR_T + lane;
-    for (int i = warp; i < nk; i += 4) {
-      const int s = i % S;
+    auto load_chunk = [&](int i, float (&va)[2][4][4], float (&vb)[2][4][4]) {
       const int64_t row0 = r0 + (int64_t)i * GR_KC;
-      float va[2][4][4], vb[2][4][4];
 #pragma unroll
       for (int kq = 0; kq < 2; ++kq) {
         load4x4_strided(P.A, P.lda, row0 + kq * 4, r1, ia, P.n1, va[kq]);
         if (!same) load4x4_strided(P.B, P.ldb, row0 + kq * 4, r1, jb, P.n2, vb[kq]);
       }
+    };
+    auto fill_stage = [&](int i, const float (&va)[2][4][4], const float (&vb)[2][4][4]) -> bool {
+      const int s = i % S;
       if (i >= S && !mbar_wait(emp(s), ((i / S) - 1) & 1)) {
         atomicExch(&g_tc_status, 6);
         *(volatile int*)abort_flag = 1;
       }
-      if (*(volatile int*)abort_flag) break;
+      if (*(volatile int*)abort_flag) return false;
       float* sh = reinterpret_cast<float*>(smem + s * SB);
 #pragma unroll
       for (int kq = 0; kq < 2; ++kq) {
@@ -1746,6 +2014,15 @@ __global__ void __launch_bounds__(GR_THREADS, 1) tc_gram_kernel(GramParams P) {
       }
       fence_proxy_async_smem();
       mbar_arrive(full(s));
+      return true;
+    };
+    // chunks warp, warp + 4, ...: loads into registers before the stage is
+    // free, then the split.  (A second register set for the next chunk costs
+    // the second CTA per SM: 196 registers, measured 1.5x slower.)
+    for (int i = warp; i < nk; i += 4) {
+      float va[2][4][4], vb[2][4][4];
+      load_chunk(i, va, vb);
+      if (!fill_stage(i, va, vb)) break;
     }
     bool okacc = true;
     if (nk > 0) {
@@ -2047,6 +2324,14 @@ __device__ __forceinline__ float tall_diag_add(float acc, const float* __restric
   return __fadd_rn(sh, sl);
 }
 
+// bd = 1: the term is A[row, col] U[col, col] alone (zero for col >= n1).
+__device__ __forceinline__ float tall_diag1(float acc, float a, float2 u) {
+  float sh = acc, sl = 0.f;
+  ff_add_prod(a, u.x, sh, sl);
+  sl = __fmaf_rn(a, u.y, sl);
+  return __fadd_rn(sh, sl);
+}
+
 struct TallParams {
   const float* A;
   int64_t lda, M;
@@ -2221,6 +2506,24 @@ __global__ void __launch_bounds__(TG_THREADS, 1) tc_tall_kernel(TallParams P) {
       for (int r = warp; r < TG_T; r += 4) {
         const int64_t row = rb + r;
         if (row >= P.M) break;
+        if (P.bd == 1) {   // the row's four diagonal-term loads issued together
+          float a[4], v[4];
+          float2 u[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = lane + 32 * q, col = tj * TG_T + c;
+            const bool ok = c < ncv && col < P.n1;
+            a[q] = ok ? __ldg(P.A + row * P.lda + col) : 0.f;
+            u[q] = ok ? P.Ud[col] : make_float2(0.f, 0.f);
+            v[q] = c < ncv ? E[r * EP + c] : 0.f;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = lane + 32 * q;
+            if (c < ncv) P.C[row * P.ldc + tj * TG_T + c] = tall_diag1(v[q], a[q], u[q]);
+          }
+          continue;
+        }
         for (int c = lane; c < ncv; c += 32) {
           const int col = tj * TG_T + c;
           float v = E[r * EP + c];
@@ -2473,12 +2776,26 @@ __global__ void __launch_bounds__(TW_THREADS, 1) tc_tall_wide_kernel(TallParams 
       if (!run || row >= P.M) continue;
       const int c0 = tj * bw + cb;
       float out[16];
+      if (P.bd == 1) {   // the 16 diagonal-term loads issued together
+        float a[16];
+        float2 ud[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int col = c0 + u;
-        out[u] = acc[u];
-        if (P.bd > 0 && col < P.n2)
-          out[u] = tall_diag_add(acc[u], P.A + row * P.lda, P.Ud, col, P.bd, P.n1, P.upper);
+        for (int u = 0; u < 16; ++u) {
+          const int col = c0 + u;
+          const bool ok = col < P.n2 && col < P.n1;
+          a[u] = ok ? __ldg(P.A + row * P.lda + col) : 0.f;
+          ud[u] = ok ? P.Ud[col] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) out[u] = tall_diag1(acc[u], a[u], ud[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int col = c0 + u;
+          out[u] = acc[u];
+          if (P.bd > 0 && col < P.n2)
+            out[u] = tall_diag_add(acc[u], P.A + row * P.lda, P.Ud, col, P.bd, P.n1, P.upper);
+        }
       }
       float* dst = P.C + row * P.ldc + c0;
       if (cvec && c0 + 16 <= tj * bw + ncv) {

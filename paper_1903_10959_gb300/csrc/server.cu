@@ -88,6 +88,7 @@ size_t estimate_bytes(const chfsi_request& r) {
   size_t b = ncells * ne * ne * 8;                                  // binary64 cell matrices
   if (mixed) b += ncells * nk * 2 * mt * 1024 * 4;                  // packed hi / lo TF32 copies
   if (r.prec == CHFSI_MIXED_BF16X3) b += ncells * ((ne + 15) / 16) * 3 * mt * 4096;   // BF16x3 terms
+  if (r.prec == CHFSI_MIXED_F16X2) b += ncells * ((ne + 15) / 16) * 2 * mt * 4096 + ncells * 4 + n * 12;
   b += ncells * ne * 9 + ncells * 4 + M * 16 + 4096;                // dof map, modes, rows, mass
   b += M * n * es;                                                  // X
   b += std::max(M * n * es, M * B * 16);                            // rotation / binary64 pair

@@ -18,6 +18,11 @@ struct TcCellData {
   // BF16x3 copy (three bf16 terms per value), packed on first use
   uint16_t* bf = nullptr;
   size_t bf_bytes = 0;
+  // FP16x2 copy (two fp16 terms of 2^s_e H~_e per value) and the per-cell
+  // inverse scales 2^-s_e (float), packed on first use; f16_bytes covers both
+  uint16_t* f16 = nullptr;
+  float* f16_inv = nullptr;
+  size_t f16_bytes = 0;
 };
 
 // Owner-computes form of one H~ Y step (no colouring): every cell writes its
@@ -88,6 +93,18 @@ struct AssembleParams {
   int vec, vin, vprev, vout;  // set by the launcher
 };
 cudaError_t tc_assemble_launch(const AssembleParams& P, cudaStream_t s);
+// The same update with the column maxima of |Y_out| as a by-product: cmax
+// (ncol words, the bits of non-negative binary32 values) is zeroed and filled.
+cudaError_t tc_assemble_cmax_launch(const AssembleParams& P, uint32_t* cmax, cudaStream_t s);
+// Column maxima of |Y| (M x ncol, leading dimension ld) into cmax (zeroed first).
+cudaError_t tc_colmax_launch(const float* Y, int64_t ld, int64_t M, int ncol, uint32_t* cmax,
+                             cudaStream_t s);
+// FP16x2 cell kernel: as tc_cell_bf16_launch with two fp16 terms per operand,
+// the block's columns scaled by powers of two from cmax (column maxima of Yin).
+cudaError_t tc_cell_f16_launch(const TcCellData& d, const TcApplyArgs& a, const uint32_t* cmax,
+                               cudaStream_t s);
+cudaError_t tc_pack_f16_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
+                                    int64_t* dev_bytes);
 
 cudaError_t tc_build(TcCellData& d, const std::vector<double>& Ht, int64_t ncells, int ne,
                      cudaStream_t s, int64_t* dev_bytes);

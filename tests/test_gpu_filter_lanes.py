@@ -34,7 +34,7 @@ def case(request):
 
 
 @pytest.mark.parametrize("ncol", [129, 300, 700])
-@pytest.mark.parametrize("prec", ["bf16x3", "mixed"])
+@pytest.mark.parametrize("prec", ["bf16x3", "mixed", "f16x2"])
 def test_lanes_bit_identical(case, ncol, prec):
     s, ctx = case
     X0 = W.start_block(90 + ncol, ctx.ndofs, ncol).astype(np.float32)

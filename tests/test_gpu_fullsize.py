@@ -70,7 +70,7 @@ def _x0_columns(s, M, cols):
     return W.uniform_pm1(s.seed, W.STREAM_X0, cnt).astype(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "f16x2"])
 def test_apply_sampled_rows_match_oracle(full, oprob, prec):
     s, ctx, X = full
     M, n = ctx.ndofs, s.n_sub
@@ -89,7 +89,8 @@ def test_apply_sampled_rows_match_oracle(full, oprob, prec):
     assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
 
 
-def test_filter_sampled_rows_match_oracle(full, oprob):
+@pytest.mark.parametrize("prec", ["bf16x3", "f16x2"])
+def test_filter_sampled_rows_match_oracle(full, oprob, prec):
     """Degree-3 BF16x3 filter of the whole 1,100-column block (the bench's
     block and kernel) against the oracle filter of four of its columns, on
     unknowns of one cell: interior, face, edge and corner nodes."""
@@ -97,7 +98,7 @@ def test_filter_sampled_rows_match_oracle(full, oprob):
     M, n = ctx.ndofs, s.n_sub
     a, b, a0, m = 5.0, 2000.0, -3.0, 3
     Xf = X.clone()
-    ctx.filter(Xf, m, a, b, a0, prec="bf16x3")
+    ctx.filter(Xf, m, a, b, a0, prec=prec)
     n1 = s.ncell * s.p
 
     def gidx(x, y, z):

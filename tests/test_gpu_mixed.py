@@ -56,7 +56,8 @@ def _x32(seed, m, n):
 @pytest.mark.parametrize("ncol,prec,tol", [(1, "tf32x3", 1e-5), (13, "tf32x3", 1e-5),
                                            (64, "tf32x3", 1e-5), (150, "tf32x3", 1e-5),
                                            (70, "tf32", 2e-3), (1, "bf16x3", 1e-5),
-                                           (13, "bf16x3", 1e-5), (150, "bf16x3", 1e-5)])
+                                           (13, "bf16x3", 1e-5), (150, "bf16x3", 1e-5),
+                                           (1, "f16x2", 1e-5), (13, "f16x2", 1e-5), (150, "f16x2", 1e-5)])
 def test_mixed_apply(case, ncol, prec, tol):
     s, prob, ctx = case
     X0 = _x32(3, prob.ndofs, ncol)
@@ -181,6 +182,66 @@ def test_bf16x3_filter(case):
     assert rel_fro(X.cpu().numpy().astype(np.float64), ref) < 1e-4
 
 
+def test_f16x2_solve_meets_eigenvalue_tolerance(case):
+    """ChFSI with FP16x2 cell products (three fp16 MMAs on power-of-two scaled
+    operands): <= 1e-7 Ha per eigenvalue, as BF16x3 and 3xTF32."""
+    s, prob, ctx = case
+    iters = 12
+    X0 = W.start_block(s.seed, prob.ndofs, s.n_sub)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(s.seed, prob.ndofs), 20)
+    D_ref, _ = och.chfsi(prob.apply_Htilde, X0, s.degree, iters, b)
+    X = torch.tensor(X0.astype(np.float32), device=DEV)
+    ctx.set_blocking(200, 8)
+    D, done = ctx.solve(X, iters, s.degree, b, prec="f16x2")
+    assert np.abs(D[:s.n_want] - D_ref[:s.n_want]).max() < 1e-7
+
+
+def test_f16x2_filter(case):
+    s, prob, ctx = case
+    X0 = _x32(4, prob.ndofs, 45)
+    b = och.lanczos_upper_bound(prob.apply_Htilde, W.lanczos_start(4, prob.ndofs), 15)
+    a, a0 = 0.2 * b, -3.0
+    ref = och.chebyshev_filter(prob.apply_Htilde, X0.astype(np.float64), 20, a, b, a0)
+    X = torch.tensor(X0, device=DEV)
+    ctx.set_blocking(32, 8)
+    ctx.filter(X, 20, a, b, a0, prec="f16x2")
+    assert rel_fro(X.cpu().numpy().astype(np.float64), ref) < 1e-4
+
+
+def test_f16x2_column_scales(case):
+    """The fp16 split scales each column of the block by a power of two from
+    its maximum: columns spread over 2^-60 .. 2^60, and a zero column, keep
+    the same relative accuracy as unit columns (each column against the
+    oracle), and the filter's later steps take the scales from the previous
+    step's assembly (a degree-5 filter of the same block)."""
+    s, prob, ctx = case
+    ncol = 13
+    X0 = _x32(9, prob.ndofs, ncol).astype(np.float64)
+    exps = np.array([-60, -40, -20, -7, 0, 0, 3, 11, 20, 40, 60, 0, 0])
+    X0 = X0 * np.ldexp(1.0, exps)[None, :]
+    X0[:, 11] = 0.0
+    X0 = X0.astype(np.float32)
+    X = torch.tensor(X0, device=DEV)
+    Y = torch.empty_like(X)
+    ctx.apply(X, Y, prec="f16x2")
+    got = Y.cpu().numpy().astype(np.float64)
+    ref = prob.apply_Htilde(X0.astype(np.float64))
+    for c in range(ncol):
+        if c == 11:
+            assert np.all(got[:, c] == 0.0)
+            continue
+        assert np.linalg.norm(got[:, c] - ref[:, c]) < 1e-5 * np.linalg.norm(ref[:, c]), c
+    a, b, a0 = 4.0, 80.0, -3.0
+    Xf = torch.tensor(X0, device=DEV)
+    ctx.filter(Xf, 5, a, b, a0, prec="f16x2")
+    got = Xf.cpu().numpy().astype(np.float64)
+    ref = och.chebyshev_filter(prob.apply_Htilde, X0.astype(np.float64), 5, a, b, a0)
+    for c in range(ncol):
+        if c == 11:
+            continue
+        assert np.linalg.norm(got[:, c] - ref[:, c]) < 1e-4 * np.linalg.norm(ref[:, c]), c
+
+
 def test_mixed_tf32_runs(case):
     s, prob, ctx = case
     X0 = W.start_block(s.seed, prob.ndofs, s.n_sub)
@@ -191,8 +252,9 @@ def test_mixed_tf32_runs(case):
     assert np.abs(D[:s.n_want] - D_ref[:s.n_want]).max() < 1e-3
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "f16x2"])
 @pytest.mark.parametrize("p,ncell,ncol", [(2, 3, 70), (8, 2, 131)])
-def test_bf16x3_apply_part_sizes(p, ncell, ncol):
+def test_bf16x3_apply_part_sizes(p, ncell, ncol, prec):
     """BF16x3 cell products at the ends of the row-part sizing: p = 2 (one
     part of 32 rows, two K-chunks) and p = 8 (three parts of 256 rows, 46
     K-chunks), with a ragged last column tile."""
@@ -204,7 +266,7 @@ def test_bf16x3_apply_part_sizes(p, ncell, ncol):
         X = torch.tensor(X0, device=DEV)
         Y = torch.empty_like(X)
         ctx.set_blocking(200, 8)
-        ctx.apply(X, Y, prec="bf16x3")
+        ctx.apply(X, Y, prec=prec)
         ref = prob.apply_Htilde(X0.astype(np.float64))
         assert rel_fro(Y.cpu().numpy().astype(np.float64), ref) < 1e-5
     finally:

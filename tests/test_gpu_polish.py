@@ -45,7 +45,7 @@ def _gres(ctx, X64, ev, n):
     return float(np.max(g))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "f16x2"])
 def test_polished_solve_meets_residual_and_eigenvalue_targets(case, prec):
     s, ctx, exact, b = case
     M, n, k = ctx.ndofs, s.n_sub, s.n_want

@@ -118,7 +118,7 @@ def test_eigenvalues_match_dense_oracle(mix, small):
 POLISHED_GRES = 1e-6
 
 
-@pytest.mark.parametrize("prec", ["mixed", "bf16x3"])
+@pytest.mark.parametrize("prec", ["mixed", "bf16x3", "f16x2"])
 def test_polished_solves_meet_the_residual_target(small, prec):
     """With the binary64 polish (one binary64 iteration of the request's
     degree after the mixed iterations, chfsi_solve_polish) every solve of the

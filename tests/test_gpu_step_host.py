@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64", "f16x2"])
 def test_step_host_equals_device_step(prec):
     s = W.small_periodic(seed=81, ncell=3, p=4, L=7.5, n_wells=3, n_want=20, degree=10, iters=2)
     ctx = gpu_context(s)
