@@ -247,7 +247,7 @@ __device__ __forceinline__ float f16_scale_of(float m) {
   if (!(m > 0.f) || !(m <= 3.0e38f)) return 1.f;
   int E;
   frexpf(m, &E);                       // m = f 2^E, f in [0.5, 1)
-  return ldexpf(1.f, 14 - E);
+  return ldexpf(1.f, max(-126, min(126, 14 - E)));   // a normal binary32 power of two
 }
 
 __global__ void __launch_bounds__(256) tc_cell_scale_kernel(const double* __restrict__ Ht, int ne,
