@@ -87,6 +87,8 @@ def parse():
 def workload(small=False, kind="chfsi", n_want=0):
     from paper_1903_10959_gb300 import workloads as W
     if kind == "c3":
+        if small:   # the same site density and degree on a 10^3-cell box (profiling runs)
+            return W.cubic_sites_nonlocal(ncell=10, L=20.0, n_side=5, n_want=600, block=660)
         return W.cubic_sites_nonlocal(block=1100)
     if small:
         return W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=n_want or 200, degree=40, iters=4,
