@@ -168,7 +168,7 @@ void free_device_data(chfsi_ctx* ctx) {
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
   release(ctx, ctx->d_wv, ctx->wv.size() * 8);
   release(ctx, ctx->d_fac, ctx->fac.size() * 8);
-  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes);   // packed copies (0 when never packed)
+  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes + ctx->tc.nl_bytes);   // packed copies
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
@@ -296,6 +296,25 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
   ra.tile = ctx->cell_tile;
   ra.gather = ctx->cell_gather;
+  // BF16x3 ring kernels take the projector expansion as extra K-chunks of the
+  // cell products (the owned rows' share of C~ h Z lands in R); the assembly
+  // then has no projector term
+  const bool nl_in_cells = nl && bf16 && tc_cell_bf16_nl_ok(ra.gather);
+  if (nl_in_cells) {
+    if (!ctx->tc.nl) {
+      NlCells nc;
+      build_nl_cells(m, ctx->hproj, nc);
+      cudaError_t pe = tc_pack_nl(ctx->tc, nc.chunk_off.data(), m.ncells, nc.zrow.data(), nc.nz_pos.data(),
+                                  nc.nz_val.data(), (int64_t)nc.nz_val.size(), ctx->stream, &ctx->dev_bytes);
+      if (pe != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                    std::string("projector chunks: ") + cudaGetErrorString(pe));
+      }
+    }
+    ra.Z = (const float*)ctx->Zb.ptr;
+    ra.ldz = ncol;
+  }
   if (f16 && !cmax_in) {   // column maxima of the input block (the scales of its fp16 split)
     if ((st = grow(ctx, ctx->cmaxb, (size_t)3 * ncol * sizeof(uint32_t))) != CHFSI_OK) return st;
     uint32_t* cm = (uint32_t*)ctx->cmaxb.ptr + 2 * (size_t)ncol;
@@ -321,7 +340,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ap.ld_out = ld_out;
   ap.Yprev = beta != 0.0 ? (const float*)Yprev : nullptr;
   ap.ld_prev = ld_prev;
-  if (nl) {
+  if (nl && !nl_in_cells) {
     ap.dof_ptr = ctx->d_dof_ptr;
     ap.dof_site = ctx->d_dof_site;
     ap.dof_c = ctx->d_dof_c32;

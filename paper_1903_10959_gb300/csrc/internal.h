@@ -103,6 +103,23 @@ struct HostProjectors {
 };
 void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& out);
 
+// The projector expansion C~ h Z (Eq. nonlocalHamDiscrete) as extra K-chunks
+// of the cell products: cell e takes the rows of the unknowns it owns (the
+// first cell holding them, ascending cell order), and its K axis runs over
+// the 4 projectors of the sites touching those rows (4 ns_e values, padded to
+// chunks of 16).  chunk_off: ncells + 1 chunk offsets; zrow: per chunk 16 rows
+// of Z (4 site + t, -1 for padding); nz_pos / nz_val: the nonzero entries
+// B[k][l] = h-scaled coefficient of node l for projector k, at their element
+// position in a K-chunk-major block layout (chunk, 128-row tile, 16 x 128
+// core-matrix order, as the packed cell matrices), term 0.
+struct NlCells {
+  std::vector<int32_t> chunk_off;
+  std::vector<int32_t> zrow;
+  std::vector<int64_t> nz_pos;
+  std::vector<double> nz_val;
+};
+void build_nl_cells(const HostMesh& m, const HostProjectors& hp, NlCells& out);
+
 // --------------------------------------------------------------- device side
 struct DevBuf {
   void* ptr = nullptr;

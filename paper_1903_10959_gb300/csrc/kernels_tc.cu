@@ -120,6 +120,9 @@ void tc_free(TcCellData& d) {
   if (d.bf) cudaFree(d.bf);
   if (d.f16) cudaFree(d.f16);
   if (d.f16_inv) cudaFree(d.f16_inv);
+  if (d.nl) cudaFree(d.nl);
+  if (d.nl_off) cudaFree(d.nl_off);
+  if (d.nl_zrow) cudaFree(d.nl_zrow);
   d = TcCellData();
 }
 
@@ -230,6 +233,64 @@ cudaError_t tc_pack_bf16_from_device(TcCellData& d, const double* dHt, cudaStrea
   note_launch();
   tc_pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dHt, d.bf, d.ncells, d.ne, d.mt, nk16);
   return cudaGetLastError();
+}
+
+// Projector chunks: scatter the three bf16 terms of each nonzero coefficient
+// into the zeroed chunk array (positions from build_nl_cells, term 0; the
+// other terms one term block further on).
+__global__ void tc_pack_nl_kernel(const int64_t* __restrict__ pos, const double* __restrict__ val, int64_t nnz,
+                                  int64_t per_chunk, uint16_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nnz) return;
+  uint16_t b1, b2, b3;
+  bf16_split3(val[i], b1, b2, b3);
+  const int64_t p = pos[i];
+  out[p] = b1;
+  out[p + per_chunk] = b2;
+  out[p + 2 * per_chunk] = b3;
+}
+
+cudaError_t tc_pack_nl(TcCellData& d, const int32_t* chunk_off, int64_t ncells, const int32_t* zrow,
+                       const int64_t* nz_pos, const double* nz_val, int64_t nnz, cudaStream_t s,
+                       int64_t* dev_bytes) {
+  const int64_t nchunk = chunk_off[ncells];
+  const int64_t per_chunk = (int64_t)d.mt * 2048;
+  const size_t bytes = (size_t)nchunk * 3 * per_chunk * sizeof(uint16_t);
+  int64_t* dpos = nullptr;
+  double* dval = nullptr;
+  cudaError_t e = cudaMalloc(&d.nl, std::max<size_t>(bytes, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&d.nl_off, (size_t)(ncells + 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d.nl_zrow, std::max<size_t>((size_t)nchunk * 16 * sizeof(int32_t), 16));
+  if (e == cudaSuccess && nnz > 0) e = cudaMalloc(&dpos, (size_t)nnz * sizeof(int64_t));
+  if (e == cudaSuccess && nnz > 0) e = cudaMalloc(&dval, (size_t)nnz * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.nl, 0, bytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.nl_off, chunk_off, (size_t)(ncells + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nchunk > 0)
+    e = cudaMemcpyAsync(d.nl_zrow, zrow, (size_t)nchunk * 16 * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(dpos, nz_pos, (size_t)nnz * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(dval, nz_val, (size_t)nnz * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) {
+    note_launch();
+    tc_pack_nl_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(dpos, dval, nnz, per_chunk, d.nl);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (dpos) cudaFree(dpos);
+  if (dval) cudaFree(dval);
+  if (e != cudaSuccess) {
+    if (d.nl) cudaFree(d.nl);
+    if (d.nl_off) cudaFree(d.nl_off);
+    if (d.nl_zrow) cudaFree(d.nl_zrow);
+    d.nl = nullptr;
+    d.nl_off = nullptr;
+    d.nl_zrow = nullptr;
+    d.nl_bytes = 0;
+    return e;
+  }
+  d.nl_bytes = bytes + (size_t)(ncells + 1) * 4 + (size_t)nchunk * 64;
+  if (dev_bytes) *dev_bytes += (int64_t)d.nl_bytes;
+  return cudaSuccess;
 }
 
 // ----------------------------------------------------------------- FP16x2 packing
@@ -369,6 +430,12 @@ struct RParams {
   int64_t e_off;            // first cell of this launch (grids of at most 65535 cells)
   const uint32_t* cmax;     // FP16x2: column maxima of |Yin| (binary32 bits), index c0 + c
   const float* cinv;        // FP16x2: per-cell inverse scales
+  // projector chunks of the BF16x3 ring kernel (null: none)
+  const uint16_t* nlA;
+  const int32_t* nl_off;
+  const int32_t* nl_zrow;
+  const float* Z;
+  int64_t ldz;
 };
 
 template <int BN, bool MULTI>
@@ -1195,13 +1262,20 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // projector chunks (BF16x3, single system): K continues over the cell's
+  // 4 ns_e projectors with the rows of Z as the gathered operand
+  const int nl0 = P.nlA ? P.nl_off[e] : 0;
+  const int nkt = nk + (P.nlA ? P.nl_off[e + 1] - nl0 : 0);
 
   if (warp == WPROD) {
     if (lane == 0) {
       const int64_t term_bytes = (int64_t)P.mt * 4096;
       const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
+      const char* An = P.nlA ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
+                                   (int64_t)r0 * 32
+                             : Ae;   // chunk i >= nk of the projector block
       int issued = 0;
-      for (int i = 0; i < nk; ++i) {
+      for (int i = 0; i < nkt; ++i) {
         const int s = i % SM;
         if (i >= SM && !mbar_wait(ea(s), ((i / SM) - 1) & 1)) {
           atomicExch(&g_tc_status, 41);
@@ -1211,9 +1285,10 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         if (*(volatile int*)abort_flag) break;
         const uint32_t dst = mbase + s * mstage;
         mbar_arrive_expect_tx(fa(s), NT * hrow);
+        const char* src = i < nk ? Ae : An;
 #pragma unroll
         for (int p = 0; p < NT; ++p)
-          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * NT + p) * term_bytes, hrow, fa(s));
+          bulk_g2s(dst + p * hrow, src + ((int64_t)i * NT + p) * term_bytes, hrow, fa(s));
         ++issued;
       }
       if (*(volatile int*)abort_flag)
@@ -1222,7 +1297,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   } else if (warp == WMMA) {
     if (lane == 0) {
       const uint32_t idesc = NT == 3 ? idesc_bf16(128, B.nh) : idesc_f16(128, B.nh);
-      for (int i = 0; i < nk; ++i) {
+      for (int i = 0; i < nkt; ++i) {
         const int sa = i % SM, sy = i % SY;
         if (!mbar_wait(fa(sa), (i / SM) & 1) || !mbar_wait(fy(sy), (i / SY) & 1) ||
             *(volatile int*)abort_flag) {
@@ -1269,14 +1344,16 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         if (c < ncv) tsc[u] = f16_scale_of(__uint_as_float(P.cmax[c0 + c]));
       }
     }
-    for (int i = pair; i < nk; i += NPAIR) {
+    for (int i = pair; i < nkt; i += NPAIR) {
       const int s = i % SY;
       float v[8][4];
+      const bool zc = i >= nk;   // a projector chunk: rows of Z
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int l = i * BF_KC + q * 8 + a;
-        const int g = l < ne ? dm[l] : -1;
-        const float* src = P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
+        const int g = zc ? P.nl_zrow[(int64_t)(nl0 + i - nk) * BF_KC + q * 8 + a] : (l < ne ? dm[l] : -1);
+        const float* src = zc ? P.Z + (int64_t)(g < 0 ? 0 : g) * P.ldz + c0
+                              : P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int c = lane + 32 * u;
@@ -1554,6 +1631,14 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   if (B.np * B.nh > d.mt * 128) return cudaErrorInvalidValue;   // parts stay inside the packed rows
   RParams P{reinterpret_cast<const float*>(d.bf), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
             nk16, 1, nullptr, 0, 0, a.ncol, 0};
+  if (a.Z) {   // projector chunks: only the ring kernels take them
+    if (!d.nl || !tc_cell_bf16_nl_ok(a.gather)) return cudaErrorInvalidValue;
+    P.nlA = d.nl;
+    P.nl_off = d.nl_off;
+    P.nl_zrow = d.nl_zrow;
+    P.Z = a.Z;
+    P.ldz = a.ldz;
+  }
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -536,4 +536,51 @@ void build_projectors(const HostMesh& m, const Projectors& pr, HostProjectors& o
     }
 }
 
+void build_nl_cells(const HostMesh& m, const HostProjectors& hp, NlCells& out) {
+  out = NlCells();
+  const int ne = m.ne, mt = (ne + 127) / 128;
+  const int64_t per_chunk = (int64_t)mt * 2048;   // elements of one term of one K-chunk
+  out.chunk_off.assign(m.ncells + 1, 0);
+  if (hp.nsite == 0) return;
+  // owner cell of each unknown: the first (lowest) cell holding it
+  std::vector<int32_t> owner(m.ndofs);
+  for (int64_t j = 0; j < m.ndofs; ++j) owner[j] = m.node_ent[m.node_ptr[j]] / ne;
+  std::vector<std::vector<int32_t>> sites(m.ncells);
+  for (int64_t e = 0; e < m.ncells; ++e) {
+    std::vector<int32_t>& st = sites[e];
+    for (int l = 0; l < ne; ++l) {
+      const int32_t g = m.dofmap[e * ne + l];
+      if (g < 0 || owner[g] != e) continue;
+      for (int64_t k = hp.dof_ptr[g]; k < hp.dof_ptr[g + 1]; ++k) st.push_back(hp.dof_site[k]);
+    }
+    std::sort(st.begin(), st.end());
+    st.erase(std::unique(st.begin(), st.end()), st.end());
+    out.chunk_off[e + 1] = out.chunk_off[e] + (int32_t)((4 * st.size() + 15) / 16);
+  }
+  out.zrow.assign((size_t)out.chunk_off[m.ncells] * 16, -1);
+  for (int64_t e = 0; e < m.ncells; ++e)
+    for (size_t i = 0; i < sites[e].size(); ++i)
+      for (int t = 0; t < 4; ++t) out.zrow[(size_t)out.chunk_off[e] * 16 + 4 * i + t] = 4 * sites[e][i] + t;
+  for (int64_t e = 0; e < m.ncells; ++e) {
+    const std::vector<int32_t>& st = sites[e];
+    for (int l = 0; l < ne; ++l) {
+      const int32_t g = m.dofmap[e * ne + l];
+      if (g < 0 || owner[g] != e) continue;
+      const int tile = l / 128, r = l % 128;
+      for (int64_t k = hp.dof_ptr[g]; k < hp.dof_ptr[g + 1]; ++k) {
+        const int slot = (int)(std::lower_bound(st.begin(), st.end(), hp.dof_site[k]) - st.begin());
+        for (int t = 0; t < 4; ++t) {
+          const int kk = 4 * slot + t;
+          const int64_t chunk = out.chunk_off[e] + kk / 16;
+          const int kc = kk % 16;
+          // element offset as bf_elem_off(r, kc) of the 128 x 16 tile block
+          const int64_t off = (r >> 3) * 128 + (kc >> 3) * 64 + (r & 7) * 8 + (kc & 7);
+          out.nz_pos.push_back(chunk * 3 * per_chunk + (int64_t)tile * 2048 + off);
+          out.nz_val.push_back(hp.dof_c[4 * k + t]);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace chfsi

@@ -23,6 +23,12 @@ struct TcCellData {
   uint16_t* f16 = nullptr;
   float* f16_inv = nullptr;
   size_t f16_bytes = 0;
+  // projector expansion as extra BF16x3 K-chunks per cell (NlCells layout),
+  // packed on first use; nl_bytes covers the three arrays
+  uint16_t* nl = nullptr;
+  int32_t* nl_off = nullptr;       // ncells + 1 chunk offsets
+  int32_t* nl_zrow = nullptr;      // 16 rows of Z per chunk (-1: padding)
+  size_t nl_bytes = 0;
 };
 
 // Owner-computes form of one H~ Y step (no colouring): every cell writes its
@@ -40,7 +46,18 @@ struct TcApplyArgs {
   int tile = 64;            // columns per CTA of the cell kernel: 64 or 128
   int gather = 2;           // BF16x3: 2 = decoupled matrix / Y rings, 0 = one shared ring, 1 = rows staged by
                             // bulk async copies (when aligned), 3 = rings with four gather warp pairs
+  // BF16x3 ring kernels: when set, each cell's K loop continues over its
+  // projector chunks (TcCellData::nl) with the rows of Z as the gathered
+  // operand, so R holds H~_loc Y plus the owned rows' share of C~ h Z
+  const float* Z = nullptr;
+  int64_t ldz = 0;
 };
+// Whether tc_cell_bf16_launch can add the projector chunks for this gather mode.
+inline bool tc_cell_bf16_nl_ok(int gather) { return gather == 2 || gather == 3; }
+// Pack the projector chunks (from build_nl_cells: nnz entries at nz_pos) into d.nl.
+cudaError_t tc_pack_nl(TcCellData& d, const int32_t* chunk_off, int64_t ncells, const int32_t* zrow,
+                       const int64_t* nz_pos, const double* nz_val, int64_t nnz, cudaStream_t s,
+                       int64_t* dev_bytes);
 cudaError_t tc_cell_r_launch(const TcCellData& d, const TcApplyArgs& a, cudaStream_t s);
 
 // One system of a batched filter (device array, one entry per system).

@@ -70,3 +70,31 @@ def test_unaligned_block_falls_back():
         assert torch.equal(_apply(ctx, V, "async"), _apply(ctx, V, "registers"))
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("p", [3, 5, 7])
+def test_projector_chunks_in_the_ring_kernel(p):
+    """With projectors, the ring kernels add the expansion C~ h Z as extra
+    K-chunks of each cell's product (the owned rows' share) instead of in the
+    assembly: against the oracle's H~ X (1e-5, as every BF16x3 apply) and the
+    register-gather path, whose assembly adds the same term (1e-6)."""
+    s = W.small_periodic(seed=170 + p, ncell=3 if p <= 5 else 2, p=p, L=7.0, n_wells=4, n_want=10)
+    s.nl_centres = s.centres[:3].copy()
+    s.nl_h = 0.5 + np.arange(12).reshape(3, 4) / 8.0
+    s.nl_rcut = 2.5
+    ctx = gpu_context(s)
+    prob = oracle_problem(s)
+    try:
+        for ncol in (4, 132):
+            x = W.start_block(ncol + 1, ctx.ndofs, ncol).astype(np.float32)
+            X = torch.tensor(x, device=DEV)
+            yg = _apply(ctx, X, "rings")
+            y4 = _apply(ctx, X, "rings4")
+            yr = _apply(ctx, X, "registers")
+            assert torch.equal(yg, y4)
+            ref = prob.apply_Htilde(x.astype(np.float64))
+            assert rel_fro(yg.cpu().numpy().astype(np.float64), ref) < 1e-5
+            assert rel_fro(yg.cpu().numpy().astype(np.float64), yr.cpu().numpy().astype(np.float64)) < 1e-6
+    finally:
+        ctx.set_cell_gather("rings")
+        ctx.destroy()
