@@ -1187,9 +1187,12 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3) {
 // tiles x parts, items of system s from item0), all systems of one degree.
 // NT = 2: the FP16x2 form (P.A the fp16 terms, P.cinv the per-cell inverse
 // scales, P.cmax the column maxima of Yin): three MMAs per chunk.
-template <int NPAIR, bool MULTI, int NT = 3>
+// NLC: the projector chunks are compiled in (a separate instantiation, so the
+// kernel without projectors keeps its lean gather loop).
+template <int NPAIR, bool MULTI, int NT = 3, bool NLC = false>
 __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
   static_assert(NT == 3 || (NT == 2 && !MULTI), "BF16x3, or single-system FP16x2");
+  static_assert(!NLC || (NT == 3 && !MULTI), "projector chunks: single-system BF16x3");
   constexpr int NTHR = (2 * NPAIR + 2) * 32;
   constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
   constexpr int YT = NT * 128 * BF_KC * 2;   // Y stage bytes
@@ -1264,16 +1267,16 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   const uint32_t tmem = *tmem_slot;
   // projector chunks (BF16x3, single system): K continues over the cell's
   // 4 ns_e projectors with the rows of Z as the gathered operand
-  const int nl0 = P.nlA ? P.nl_off[e] : 0;
-  const int nkt = nk + (P.nlA ? P.nl_off[e + 1] - nl0 : 0);
+  const int nl0 = NLC ? P.nl_off[e] : 0;
+  const int nkt = NLC ? nk + P.nl_off[e + 1] - nl0 : nk;
 
   if (warp == WPROD) {
     if (lane == 0) {
       const int64_t term_bytes = (int64_t)P.mt * 4096;
       const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
-      const char* An = P.nlA ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
-                                   (int64_t)r0 * 32
-                             : Ae;   // chunk i >= nk of the projector block
+      const char* An = NLC ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
+                                 (int64_t)r0 * 32
+                           : Ae;   // chunk i >= nk of the projector block
       int issued = 0;
       for (int i = 0; i < nkt; ++i) {
         const int s = i % SM;
@@ -1285,7 +1288,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         if (*(volatile int*)abort_flag) break;
         const uint32_t dst = mbase + s * mstage;
         mbar_arrive_expect_tx(fa(s), NT * hrow);
-        const char* src = i < nk ? Ae : An;
+        const char* src = !NLC || i < nk ? Ae : An;
 #pragma unroll
         for (int p = 0; p < NT; ++p)
           bulk_g2s(dst + p * hrow, src + ((int64_t)i * NT + p) * term_bytes, hrow, fa(s));
@@ -1347,7 +1350,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     for (int i = pair; i < nkt; i += NPAIR) {
       const int s = i % SY;
       float v[8][4];
-      const bool zc = i >= nk;   // a projector chunk: rows of Z
+      const bool zc = NLC && i >= nk;   // a projector chunk: rows of Z
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int l = i * BF_KC + q * 8 + a;
@@ -1645,6 +1648,10 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
     cudaFuncSetAttribute(tc_cell_bf16_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<4, false, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_whole_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
@@ -1658,6 +1665,10 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
     note_launch();
     if (async)
       tc_cell_bf16_async_kernel<<<grid, BFA_THREADS, BA.total, s>>>(P);
+    else if (a.gather == 2 && P.nlA)
+      tc_cell_bf16_rings_kernel<2, false, 3, true><<<grid, 6 * 32, BR.total, s>>>(P);
+    else if (a.gather == 3 && P.nlA)
+      tc_cell_bf16_rings_kernel<4, false, 3, true><<<grid, 10 * 32, BR4.total, s>>>(P);
     else if (a.gather == 2)
       tc_cell_bf16_rings_kernel<2, false><<<grid, 6 * 32, BR.total, s>>>(P);
     else if (a.gather == 3)
@@ -1767,7 +1778,9 @@ __device__ __forceinline__ void assemble_quad(const AssembleParams& P, int64_t j
   }
   float yin[4] = {0.f, 0.f, 0.f, 0.f}, yp[4] = {0.f, 0.f, 0.f, 0.f};
   const bool vin = v4 && P.vin, vprev = v4 && P.vprev, vout = v4 && P.vout;
-  if (vin) {
+  if (P.shift == 0.f) {
+    // an application of H~ (no shift): Y_in is not read; sum - 0 * 0 equals sum - 0 * y_in
+  } else if (vin) {
     const float4 t = *reinterpret_cast<const float4*>(P.Yin + j * P.ld_in + c);
     yin[0] = t.x; yin[1] = t.y; yin[2] = t.z; yin[3] = t.w;
   } else {
