@@ -140,7 +140,7 @@ constexpr bool kMatrixFreeDefault = true;
 // blocks, projector and binary64 staging buffers); later calls regrow it.
 void release_scratch(chfsi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot, &ctx->cmaxb}) {
+  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot, &ctx->cmaxb, &ctx->pjb}) {
     dfree(ctx, b->ptr, b->bytes);
     b->ptr = nullptr;
     b->bytes = 0;
@@ -168,7 +168,8 @@ void free_device_data(chfsi_ctx* ctx) {
   release(ctx, ctx->d_Ht, (size_t)m.ncells * m.ne * m.ne * 8);
   release(ctx, ctx->d_wv, ctx->wv.size() * 8);
   release(ctx, ctx->d_fac, ctx->fac.size() * 8);
-  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes + ctx->tc.nl_bytes);   // packed copies
+  ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes + ctx->tc.nl_bytes +
+                              ctx->tc.pj_bytes);   // packed copies
   tc_free(ctx->tc);
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
@@ -278,10 +279,38 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
                   std::string("tensor-core cell data: ") + cudaGetErrorString(pe));
     }
   }
-  if (nl) {   // projection Z = C~^T Y; the expansion is fused into the assembly
+  // BF16x3 ring kernels take the projector terms on the tensor cores: the
+  // projection Z = C~^T Y as per-cell blocks over the owned rows (partial sums
+  // reduced per site in a fixed order) and the expansion C~ h Z as extra
+  // K-chunks of the cell products; the assembly then has no projector term
+  const bool nl_in_cells = nl && bf16 && tc_cell_bf16_nl_ok(ctx->cell_gather);
+  if (nl_in_cells && !ctx->tc.nl) {
+    NlCells nc;
+    build_nl_cells(m, ctx->hproj, nc);
+    cudaError_t pe = tc_pack_nl(ctx->tc, nc.chunk_off.data(), m.ncells, nc.zrow.data(), nc.nz_pos.data(),
+                                nc.nz_val.data(), (int64_t)nc.nz_val.size(), ctx->stream, &ctx->dev_bytes);
+    if (pe == cudaSuccess)
+      pe = tc_pack_proj(ctx->tc, m.ncells, ctx->hproj.nsite, nc.np.data(), nc.poff.data(), nc.prow.data(),
+                        nc.red_ptr.data(), nc.red_row.data(), nc.pz_pos.data(), nc.pz_val.data(),
+                        (int64_t)nc.pz_val.size(), ctx->stream, &ctx->dev_bytes);
+    if (pe == cudaErrorNotSupported) {
+      cudaGetLastError();   // too many sites on one cell's rows: the projection stays by site
+    } else if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("projector chunks: ") + cudaGetErrorString(pe));
+    }
+  }
+  if (nl) {   // projection Z = C~^T Y
     KTimer kt(ctx, 2);
-    CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
-                     (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
+    if (nl_in_cells && ctx->tc.pj) {
+      if ((st = grow(ctx, ctx->pjb, (size_t)ctx->tc.pj_rows * ncol * sizeof(float))) != CHFSI_OK) return st;
+      CK(tc_nl_project_cells(ctx->tc, ctx->d_dofmap, m.ncells, ctx->hproj.nsite, (const float*)Yin, ld_in,
+                             ncol, (float*)ctx->pjb.ptr, (float*)ctx->Zb.ptr, ctx->stream));
+    } else {
+      CK(tc_nl_project(ctx->d_site_ptr, ctx->d_site_dof, ctx->d_site_c32, ctx->hproj.nsite,
+                       (const float*)Yin, ld_in, ncol, (float*)ctx->Zb.ptr, ctx->stream));
+    }
   }
   // owner-computes: dense cell blocks R_e (one launch over all cells), then the
   // fixed-order assembly fused with the Chebyshev update
@@ -296,22 +325,7 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
   ra.split3 = prec == CHFSI_MIXED_TF32X3;
   ra.tile = ctx->cell_tile;
   ra.gather = ctx->cell_gather;
-  // BF16x3 ring kernels take the projector expansion as extra K-chunks of the
-  // cell products (the owned rows' share of C~ h Z lands in R); the assembly
-  // then has no projector term
-  const bool nl_in_cells = nl && bf16 && tc_cell_bf16_nl_ok(ra.gather);
   if (nl_in_cells) {
-    if (!ctx->tc.nl) {
-      NlCells nc;
-      build_nl_cells(m, ctx->hproj, nc);
-      cudaError_t pe = tc_pack_nl(ctx->tc, nc.chunk_off.data(), m.ncells, nc.zrow.data(), nc.nz_pos.data(),
-                                  nc.nz_val.data(), (int64_t)nc.nz_val.size(), ctx->stream, &ctx->dev_bytes);
-      if (pe != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
-                    std::string("projector chunks: ") + cudaGetErrorString(pe));
-      }
-    }
     ra.Z = (const float*)ctx->Zb.ptr;
     ra.ldz = ncol;
   }
@@ -856,7 +870,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   ctx->d_kfac = nullptr;
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
-                    &ctx->cmaxb,
+                    &ctx->cmaxb, &ctx->pjb,
                     &ctx->scfr, &ctx->scfw, &ctx->kW, &ctx->kT1, &ctx->kG, &ctx->kS, &ctx->kwork,
                     &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);

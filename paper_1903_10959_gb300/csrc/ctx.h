@@ -68,6 +68,7 @@ struct chfsi_ctx {
   cudaEvent_t lane_ev[kMaxLanes] = {};
   chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes], laneC[kMaxLanes];
   chfsi::DevBuf cmaxb;             // FP16x2: column maxima of the filter's blocks (3 x ncol words)
+  chfsi::DevBuf pjb;               // partial projections of the cells (pj_rows x ncol)
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double times[4] = {0, 0, 0, 0};

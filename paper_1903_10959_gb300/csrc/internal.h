@@ -117,6 +117,19 @@ struct NlCells {
   std::vector<int32_t> zrow;
   std::vector<int64_t> nz_pos;
   std::vector<double> nz_val;
+  // the projection Z = C~^T Y as the transposed blocks: cell e contributes the
+  // partial sums of its owned rows for its np[e] = 4 ns_e projectors (padded
+  // to 16) as rows prow[e] .. prow[e] + np[e] of a partial array; its block
+  // (K = the cell's nodes in chunks of 16, N = np[e]) starts at element
+  // poff[e]; pz_pos / pz_val its nonzeros (term 0, coefficients without h);
+  // red_ptr / red_row: per site, the partial rows (4 slot of its cells, in
+  // ascending cell order) whose sums give Z's rows 4 s .. 4 s + 3
+  std::vector<int32_t> np;
+  std::vector<int64_t> poff, prow;
+  std::vector<int64_t> pz_pos;
+  std::vector<double> pz_val;
+  std::vector<int32_t> red_ptr;
+  std::vector<int64_t> red_row;
 };
 void build_nl_cells(const HostMesh& m, const HostProjectors& hp, NlCells& out);
 

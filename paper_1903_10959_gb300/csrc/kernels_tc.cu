@@ -123,6 +123,9 @@ void tc_free(TcCellData& d) {
   if (d.nl) cudaFree(d.nl);
   if (d.nl_off) cudaFree(d.nl_off);
   if (d.nl_zrow) cudaFree(d.nl_zrow);
+  for (void* q : {(void*)d.pj, (void*)d.pj_np, (void*)d.pj_off, (void*)d.pj_row, (void*)d.pj_red_ptr,
+                  (void*)d.pj_red_row})
+    if (q) cudaFree(q);
   d = TcCellData();
 }
 
@@ -293,6 +296,99 @@ cudaError_t tc_pack_nl(TcCellData& d, const int32_t* chunk_off, int64_t ncells, 
   return cudaSuccess;
 }
 
+// Projection blocks: the three bf16 terms of each coefficient at its
+// position (term 0; the block of one chunk holds np[e] x 16 values per term).
+__global__ void tc_pack_proj_kernel(const int64_t* __restrict__ pos, const double* __restrict__ val, int64_t nnz,
+                                    const int64_t* __restrict__ poff, const int32_t* __restrict__ np,
+                                    int64_t ncells, uint16_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nnz) return;
+  const int64_t p = pos[i];
+  int64_t lo = 0, hi = ncells - 1;   // the cell whose block holds p
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (poff[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  const int64_t term = (int64_t)np[lo] * 16;
+  uint16_t b1, b2, b3;
+  bf16_split3(val[i], b1, b2, b3);
+  out[p] = b1;
+  out[p + term] = b2;
+  out[p + 2 * term] = b3;
+}
+
+cudaError_t tc_pack_proj(TcCellData& d, int64_t ncells, int nsite, const int32_t* np, const int64_t* poff,
+                         const int64_t* prow, const int32_t* red_ptr, const int64_t* red_row,
+                         const int64_t* pz_pos, const double* pz_val, int64_t nnz, cudaStream_t s,
+                         int64_t* dev_bytes) {
+  int npmax = 0;
+  for (int64_t e = 0; e < ncells; ++e) npmax = std::max(npmax, np[e]);
+  if (npmax > 256) return cudaErrorNotSupported;   // more than 64 sites on one cell's rows
+  const size_t bytes = std::max<size_t>((size_t)poff[ncells] * sizeof(uint16_t), 16);
+  const int64_t nred = red_ptr[nsite];
+  int64_t* dpos = nullptr;
+  double* dval = nullptr;
+  cudaError_t e = cudaMalloc(&d.pj, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&d.pj_np, (size_t)ncells * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d.pj_off, (size_t)(ncells + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d.pj_row, (size_t)(ncells + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&d.pj_red_ptr, (size_t)(nsite + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d.pj_red_row, std::max<size_t>((size_t)nred * 8, 8));
+  if (e == cudaSuccess && nnz > 0) e = cudaMalloc(&dpos, (size_t)nnz * 8);
+  if (e == cudaSuccess && nnz > 0) e = cudaMalloc(&dval, (size_t)nnz * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.pj, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pj_np, np, (size_t)ncells * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pj_off, poff, (size_t)(ncells + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pj_row, prow, (size_t)(ncells + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.pj_red_ptr, red_ptr, (size_t)(nsite + 1) * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nred > 0)
+    e = cudaMemcpyAsync(d.pj_red_row, red_row, (size_t)nred * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(dpos, pz_pos, (size_t)nnz * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(dval, pz_val, (size_t)nnz * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz > 0) {
+    note_launch();
+    tc_pack_proj_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(dpos, dval, nnz, d.pj_off, d.pj_np,
+                                                                       ncells, d.pj);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (dpos) cudaFree(dpos);
+  if (dval) cudaFree(dval);
+  if (e != cudaSuccess) {
+    for (void* q : {(void*)d.pj, (void*)d.pj_np, (void*)d.pj_off, (void*)d.pj_row, (void*)d.pj_red_ptr,
+                    (void*)d.pj_red_row})
+      if (q) cudaFree(q);
+    d.pj = nullptr;
+    d.pj_np = nullptr;
+    d.pj_off = nullptr;
+    d.pj_row = nullptr;
+    d.pj_red_ptr = nullptr;
+    d.pj_red_row = nullptr;
+    return e;
+  }
+  d.pj_rows = prow[ncells];
+  d.pj_npmax = npmax;
+  d.pj_bytes = bytes + (size_t)ncells * 4 + (size_t)(ncells + 1) * 16 + (size_t)(nsite + 1) * 4 + (size_t)nred * 8;
+  if (dev_bytes) *dev_bytes += (int64_t)d.pj_bytes;
+  return cudaSuccess;
+}
+
+// Z[4 s + t][c] = sum over the (cell, slot) partial rows of site s, in the
+// fixed (ascending cell) order of red_row.  One thread per (row of Z, column).
+__global__ void nl_proj_reduce_kernel(const int32_t* __restrict__ red_ptr, const int64_t* __restrict__ red_row,
+                                      const float* __restrict__ part, int nsite, int ncol,
+                                      float* __restrict__ Z) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)4 * nsite * ncol) return;
+  const int64_t zr = idx / ncol;
+  const int c = (int)(idx - zr * ncol);
+  const int site = (int)(zr >> 2), t = (int)(zr & 3);
+  float v = 0.f;
+  for (int k = red_ptr[site]; k < red_ptr[site + 1]; ++k) v += part[(red_row[k] + t) * ncol + c];
+  Z[zr * ncol + c] = v;
+}
+
 // ----------------------------------------------------------------- FP16x2 packing
 // Two fp16 terms carry about 22 significant bits, within a factor four of
 // binary32, and fp16 MMAs run at the bf16 rate: three kind::f16 MMAs per
@@ -436,6 +532,12 @@ struct RParams {
   const int32_t* nl_zrow;
   const float* Z;
   int64_t ldz;
+  // projection mode: per cell rows np[e] (B operand rows, output rows), block
+  // at element pj_off[e] of A, output rows from pj_row[e] of R
+  const int32_t* pj_np;
+  const int64_t* pj_off;
+  const int64_t* pj_row;
+  int pj_npmax;
 };
 
 template <int BN, bool MULTI>
@@ -1165,8 +1267,13 @@ struct BfrPlan {
 // npair gather warp pairs; each pair owns the Y stages i % npair of its
 // chunks i = pair (mod npair), so its parity waits stay sound.  nt: terms per
 // operand (3 for BF16x3, 2 for FP16x2).
-__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3) {
-  const BfPlan b = bf_plan(ne);
+__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3, int proj_nh = 0) {
+  BfPlan b = bf_plan(ne);
+  if (proj_nh > 0) {   // projection blocks: one part of up to proj_nh rows
+    b.np = 1;
+    b.nh = proj_nh;
+    b.alloc = proj_nh <= 32 ? 32 : (proj_nh <= 64 ? 64 : (proj_nh <= 128 ? 128 : 256));
+  }
   BfrPlan r;
   r.np = b.np;
   r.nh = b.nh;
@@ -1188,11 +1295,15 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3) {
 // NT = 2: the FP16x2 form (P.A the fp16 terms, P.cinv the per-cell inverse
 // scales, P.cmax the column maxima of Yin): three MMAs per chunk.
 // NLC: the projector chunks are compiled in (a separate instantiation, so the
-// kernel without projectors keeps its lean gather loop).
-template <int NPAIR, bool MULTI, int NT = 3, bool NLC = false>
+// kernel without projectors keeps its lean gather loop).  PROJ: the
+// projection Z = C~^T Y instead of the cell products: the streamed operand is
+// the cell's projection block (np[e] rows = its projectors, K = its nodes),
+// the result (128 columns x np[e]) goes to rows pj_row[e] .. of R.
+template <int NPAIR, bool MULTI, int NT = 3, bool NLC = false, bool PROJ = false>
 __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
   static_assert(NT == 3 || (NT == 2 && !MULTI), "BF16x3, or single-system FP16x2");
   static_assert(!NLC || (NT == 3 && !MULTI), "projector chunks: single-system BF16x3");
+  static_assert(!PROJ || (NT == 3 && !MULTI && !NLC), "projection: single-system BF16x3");
   constexpr int NTHR = (2 * NPAIR + 2) * 32;
   constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
   constexpr int YT = NT * 128 * BF_KC * 2;   // Y stage bytes
@@ -1200,7 +1311,9 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int64_t e = P.e_off + blockIdx.y;
   const int ne = P.ne, nk = P.nk;
-  const BfrPlan B = bfr_plan(ne, NPAIR, NT);
+  const BfrPlan B = bfr_plan(ne, NPAIR, NT, PROJ ? P.pj_npmax : 0);
+  const int nrow = PROJ ? P.pj_np[e] : B.nh;   // B-operand rows of this CTA
+  if (PROJ && nrow == 0) return;                // a cell owning no projector rows: nothing to do
   int h = blockIdx.x % B.np;
   int c0 = (blockIdx.x / B.np) * 128;
   if (MULTI) {   // item -> (system, cell, tile, part): binary search over the systems' first items
@@ -1227,8 +1340,8 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   const int ncv = min(128, P.ncol - c0);
   const int r0 = h * B.nh;
   const int SM = B.sm, SY = B.sy;
-  const int hrow = B.nh * 32;
-  const int mstage = NT * hrow;
+  const int hrow = nrow * 32;              // bytes of one term of a chunk (rows of 32 B)
+  const int mstage = NT * B.nh * 32;       // stage stride (the launch's largest block)
   unsigned char* ybase = smem + SM * mstage;                   // Y term stages
   uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * YT);
   // fa[SM] (matrix full, tx), ea[SM] (matrix empty), fy[SY] (Y full, 64), ey[SY] (Y empty), acc
@@ -1273,7 +1386,9 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   if (warp == WPROD) {
     if (lane == 0) {
       const int64_t term_bytes = (int64_t)P.mt * 4096;
-      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
+      const char* Ae = PROJ ? reinterpret_cast<const char*>(P.A) + P.pj_off[e] * 2
+                            : reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
+      const int64_t tstride = PROJ ? (int64_t)hrow : term_bytes;   // bytes between terms and chunks
       const char* An = NLC ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
                                  (int64_t)r0 * 32
                            : Ae;   // chunk i >= nk of the projector block
@@ -1291,7 +1406,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         const char* src = !NLC || i < nk ? Ae : An;
 #pragma unroll
         for (int p = 0; p < NT; ++p)
-          bulk_g2s(dst + p * hrow, src + ((int64_t)i * NT + p) * term_bytes, hrow, fa(s));
+          bulk_g2s(dst + p * hrow, src + ((int64_t)i * NT + p) * tstride, hrow, fa(s));
         ++issued;
       }
       if (*(volatile int*)abort_flag)
@@ -1299,7 +1414,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     }
   } else if (warp == WMMA) {
     if (lane == 0) {
-      const uint32_t idesc = NT == 3 ? idesc_bf16(128, B.nh) : idesc_f16(128, B.nh);
+      const uint32_t idesc = NT == 3 ? idesc_bf16(128, nrow) : idesc_f16(128, nrow);
       for (int i = 0; i < nkt; ++i) {
         const int sa = i % SM, sy = i % SY;
         if (!mbar_wait(fa(sa), (i / SM) & 1) || !mbar_wait(fy(sy), (i / SY) & 1) ||
@@ -1397,10 +1512,11 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     tc_fence_after();
     const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
     const int c = warp * 32 + lane;
-    float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+    float* dst = P.R + (PROJ ? P.pj_row[e] : (int64_t)e * ne + r0) * P.ldr + c0 + c;
+    const int rend = PROJ ? nrow : ne - r0;   // rows of this CTA's result
     // FP16x2: undo the cell's and the column's scales (exact powers of two)
     const float back = NT == 2 && c < ncv ? P.cinv[e] / f16_scale_of(__uint_as_float(P.cmax[c0 + c])) : 1.f;
-    for (int cb = 0; cb < B.nh; cb += 16) {
+    for (int cb = 0; cb < nrow; cb += 16) {
       float acc[16];
       __syncwarp();
       if (run) {
@@ -1410,7 +1526,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
       if (!run || c >= ncv) continue;
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (r0 + cb + j < ne) dst[(int64_t)(cb + j) * P.ldr] = NT == 2 ? acc[j] * back : acc[j];
+        if (cb + j < rend) dst[(int64_t)(cb + j) * P.ldr] = NT == 2 ? acc[j] * back : acc[j];
     }
     }
   }
@@ -1704,6 +1820,38 @@ cudaError_t tc_cell_f16_launch(const TcCellData& d, const TcApplyArgs& a, const 
     note_launch();
     tc_cell_bf16_rings_kernel<2, false, 2><<<grid, 6 * 32, BR.total, s>>>(P);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_nl_project_cells(const TcCellData& d, const int32_t* dofmap, int64_t ncells, int nsite,
+                                const float* Y, int64_t ldy, int ncol, float* part, float* Z, cudaStream_t s) {
+  if (ncells == 0 || ncol == 0 || nsite == 0) return cudaSuccess;
+  if (!d.pj) return cudaErrorInvalidValue;
+  const int nk16 = (d.ne + BF_KC - 1) / BF_KC;
+  RParams P{reinterpret_cast<const float*>(d.pj), dofmap, Y, part, ldy, ncol, d.ne, d.mt, nk16, 1, nullptr, 0, 0,
+            ncol, 0};
+  P.pj_np = d.pj_np;
+  P.pj_off = d.pj_off;
+  P.pj_row = d.pj_row;
+  P.pj_npmax = d.pj_npmax;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false, 3, false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  const BfrPlan BR = bfr_plan(d.ne, 2, 3, d.pj_npmax);
+  for (int64_t e0 = 0; e0 < ncells; e0 += 65535) {
+    P.e_off = e0;
+    dim3 grid((unsigned)((ncol + 127) / 128), (unsigned)std::min<int64_t>(65535, ncells - e0));
+    note_launch();
+    tc_cell_bf16_rings_kernel<2, false, 3, false, true><<<grid, 6 * 32, BR.total, s>>>(P);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t tot = (int64_t)4 * nsite * ncol;
+  note_launch();
+  nl_proj_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d.pj_red_ptr, d.pj_red_row, part, nsite,
+                                                                      ncol, Z);
   return cudaGetLastError();
 }
 

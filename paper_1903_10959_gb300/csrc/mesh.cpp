@@ -561,6 +561,42 @@ void build_nl_cells(const HostMesh& m, const HostProjectors& hp, NlCells& out) {
   for (int64_t e = 0; e < m.ncells; ++e)
     for (size_t i = 0; i < sites[e].size(); ++i)
       for (int t = 0; t < 4; ++t) out.zrow[(size_t)out.chunk_off[e] * 16 + 4 * i + t] = 4 * sites[e][i] + t;
+  // projection blocks
+  const int nk16 = (ne + 15) / 16;
+  out.np.assign(m.ncells, 0);
+  out.poff.assign(m.ncells + 1, 0);
+  out.prow.assign(m.ncells + 1, 0);
+  for (int64_t e = 0; e < m.ncells; ++e) {
+    out.np[e] = (int32_t)((4 * sites[e].size() + 15) / 16 * 16);
+    out.poff[e + 1] = out.poff[e] + (int64_t)nk16 * 3 * out.np[e] * 16;
+    out.prow[e + 1] = out.prow[e] + out.np[e];
+  }
+  for (int s = 0; s < hp.nsite; ++s)
+    for (int64_t pos = hp.site_ptr[s]; pos < hp.site_ptr[s + 1]; ++pos) {
+      const int32_t g = hp.site_dof[pos];
+      const int32_t ent = m.node_ent[m.node_ptr[g]];   // the owner's row: e ne + l
+      const int64_t e = ent / ne;
+      const int l = ent % ne;
+      const std::vector<int32_t>& st = sites[e];
+      const int slot = (int)(std::lower_bound(st.begin(), st.end(), s) - st.begin());
+      for (int t = 0; t < 4; ++t) {
+        const int k = 4 * slot + t, kc = l % 16;
+        const int64_t off = (k >> 3) * 128 + (kc >> 3) * 64 + (k & 7) * 8 + (kc & 7);
+        out.pz_pos.push_back(out.poff[e] + (int64_t)(l / 16) * 3 * out.np[e] * 16 + off);
+        out.pz_val.push_back(hp.site_c[4 * pos + t]);
+      }
+    }
+  out.red_ptr.assign(hp.nsite + 1, 0);
+  for (int64_t e = 0; e < m.ncells; ++e)
+    for (int32_t s : sites[e]) out.red_ptr[s + 1]++;
+  for (int s = 0; s < hp.nsite; ++s) out.red_ptr[s + 1] += out.red_ptr[s];
+  out.red_row.assign(out.red_ptr[hp.nsite], 0);
+  {
+    std::vector<int32_t> fill(out.red_ptr.begin(), out.red_ptr.end() - 1);
+    for (int64_t e = 0; e < m.ncells; ++e)     // ascending cells: fixed summation order
+      for (size_t i = 0; i < sites[e].size(); ++i)
+        out.red_row[fill[sites[e][i]]++] = out.prow[e] + 4 * (int64_t)i;
+  }
   for (int64_t e = 0; e < m.ncells; ++e) {
     const std::vector<int32_t>& st = sites[e];
     for (int l = 0; l < ne; ++l) {

@@ -29,6 +29,17 @@ struct TcCellData {
   int32_t* nl_off = nullptr;       // ncells + 1 chunk offsets
   int32_t* nl_zrow = nullptr;      // 16 rows of Z per chunk (-1: padding)
   size_t nl_bytes = 0;
+  // the projection Z = C~^T Y as per-cell BF16x3 blocks (NlCells::np / poff /
+  // prow) and the per-site reduction lists; packed with the chunks above
+  uint16_t* pj = nullptr;
+  int32_t* pj_np = nullptr;
+  int64_t* pj_off = nullptr;
+  int64_t* pj_row = nullptr;
+  int32_t* pj_red_ptr = nullptr;
+  int64_t* pj_red_row = nullptr;
+  int64_t pj_rows = 0;             // rows of the partial array
+  int pj_npmax = 0;
+  size_t pj_bytes = 0;
 };
 
 // Owner-computes form of one H~ Y step (no colouring): every cell writes its
@@ -54,6 +65,16 @@ struct TcApplyArgs {
 };
 // Whether tc_cell_bf16_launch can add the projector chunks for this gather mode.
 inline bool tc_cell_bf16_nl_ok(int gather) { return gather == 2 || gather == 3; }
+// Pack the projection blocks of build_nl_cells into d.pj (and its tables).
+cudaError_t tc_pack_proj(TcCellData& d, int64_t ncells, int nsite, const int32_t* np, const int64_t* poff,
+                         const int64_t* prow, const int32_t* red_ptr, const int64_t* red_row,
+                         const int64_t* pz_pos, const double* pz_val, int64_t nnz, cudaStream_t s,
+                         int64_t* dev_bytes);
+// Z (4 nsite x ncol, row stride ncol) = C~^T Y by the projection blocks on the
+// tensor cores: per cell the partial sums of its owned rows (a ring-kernel
+// launch into part, pj_rows x ncol), then the per-site sums in a fixed order.
+cudaError_t tc_nl_project_cells(const TcCellData& d, const int32_t* dofmap, int64_t ncells, int nsite,
+                                const float* Y, int64_t ldy, int ncol, float* part, float* Z, cudaStream_t s);
 // Pack the projector chunks (from build_nl_cells: nnz entries at nz_pos) into d.nl.
 cudaError_t tc_pack_nl(TcCellData& d, const int32_t* chunk_off, int64_t ncells, const int32_t* zrow,
                        const int64_t* nz_pos, const double* nz_val, int64_t nnz, cudaStream_t s,
