@@ -69,7 +69,7 @@ def parse():
                     help="wavefunction block of the filter (0: chosen by the autotuner)")
     ap.add_argument("--tile", type=int, default=64, choices=[64, 128],
                     help="cell-kernel column tile when --block is given")
-    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "c3", "batch", "serving"],
+    ap.add_argument("--workload", default="chfsi", choices=["chfsi", "c3", "batch", "serving", "kpoint"],
                     help="chfsi: the 16^3-cell p=6 FCC system; c3: 20^3 cells p=7 with "
                          "projectors, N=3000 (block 1100); batch: 64 small Dirichlet systems "
                          "filtered together; serving: request stream through the "
@@ -862,6 +862,93 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ k-points
+def mfk_flops_per_cell(p):
+    """Flops of one Bloch sum-factorised cell apply per complex vector (two real
+    columns): per real column the z / y / x passes of T = 1/2 K + 1/2 |k|^2 A and
+    of G = k.G (3 + 5 + 4 FMAs per pencil entry: 24 n1^4 flops), the potential
+    passes 4 (q n1^3 + q^2 n1^2 + q^3 n1) + q^3, and 3 n1^3 for the scaling and the
+    combination of the parts."""
+    n1, q = p + 1, p + 2
+    return 2 * (24 * n1 ** 4 + 4 * (q * n1 ** 3 + q * q * n1 * n1 + q ** 3 * n1) + q ** 3 + 3 * n1 ** 3)
+
+
+def run_kpoint(args):
+    """Bloch ChFSI at one wavevector (binary64, complex Hermitian H~(k)): the
+    8^3-cell p = 6 FCC box of the profiling case, N = 200 (+20) complex bands,
+    degree 40; seconds per iteration (difference of 3- and 1-iteration solves,
+    so the start block's CholGS / RR are excluded) and the roofline of the
+    Bloch matrix-free apply against the binary64 rate."""
+    import torch
+    from paper_1903_10959_gb300 import Context, workloads as W
+    s = W.fcc_periodic(ncell=8, p=6, L=15.0, n_fcc=2, n_want=200, degree=40, iters=3, block=220)
+    kvec = [0.11, 0.07, 0.03]
+    stream = torch.cuda.current_stream()
+    ctx = Context(s.ncell, s.L, s.p, periodic=True, stream=stream)
+    ctx.set_potential_gaussians(s.centres, s.depths, s.widths)
+    ctx.build()
+    ctx.set_kpoint(kvec)
+    M, n = ctx.ndofs, s.n_sub
+    b = ctx.bounds_kpoint(20, s.seed)
+    re = torch.tensor(W.start_block(s.seed, M, n), device="cuda")
+    im = torch.tensor(W.start_block(s.seed + 1, M, n), device="cuda")
+    X0 = torch.complex(re, im)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ctx.solve_kpoint(X0.clone(), 1, s.degree, b)                     # warm-up
+    t1 = ev_seconds(stream, lambda: ctx.solve_kpoint(X0.clone(), 1, s.degree, b))
+    t3 = ev_seconds(stream, lambda: ctx.solve_kpoint(X0.clone(), 3, s.degree, b))
+    Y = torch.empty_like(X0)
+    reps = max(3, args.steps)
+    ctx.apply_kpoint(X0, Y)
+    t_apply = ev_seconds(stream, lambda: [ctx.apply_kpoint(X0, Y) for _ in range(reps)]) / reps
+    # BF16x3 filter (binary64 CholGS / RR): T~_e = H~_e + 1/2 |k|^2 A~ per cell and
+    # the shared G~ on the tensor cores, binary32 column pairs
+    Xb = X0.clone()
+    ctx.solve_kpoint(Xb, 1, s.degree, b, prec="bf16x3")             # warm-up, packs
+    m1 = ev_seconds(stream, lambda: ctx.solve_kpoint(X0.clone(), 1, s.degree, b, prec="bf16x3"))
+    m3 = ev_seconds(stream, lambda: ctx.solve_kpoint(X0.clone(), 3, s.degree, b, prec="bf16x3"))
+    X32 = X0.to(torch.complex64)
+    Y32 = torch.empty_like(X32)
+    ctx.apply_kpoint_mixed(X32, Y32)
+    t_mixed = ev_seconds(stream, lambda: [ctx.apply_kpoint_mixed(X32, Y32) for _ in range(reps)]) / reps
+    clk = clocks.stop()
+    flops = s.ncell ** 3 * n * mfk_flops_per_cell(s.p)
+    achieved = flops / t_apply / 1e12
+    peak, note = dtype_peak("fp64", load_peaks())
+    per_iter = (t3 - t1) / 2
+    ne = (s.p + 1) ** 3
+    mflops = s.ncell ** 3 * n * 8 * ne * ne          # complex n_e x n_e block per cell and band
+    bpeak, bnote = dtype_peak("bf16x3", load_peaks())
+    line = {
+        "metric": "Bloch ChFSI s/iter (binary64, one k-point)", "value": per_iter, "unit": "s/iter",
+        "n_gpus": 1, "steps": 2, "warmup": 1, "ms_per_step": per_iter * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "fcc-periodic 8^3 cells p=6 L=15, %d unknowns, 32 Gaussian wells, k = %s "
+                               "bohr^-1, N=%d complex bands (+%d buffer), Chebyshev degree %d"
+                               % (M, kvec, s.n_want, s.n_buffer, s.degree)},
+        "solve_s": {"iters_1": t1, "iters_3": t3},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "mfk_cell_fp64_kernel (+ assembly)",
+                     "avg_apply_ms": t_apply * 1e3, "flops_per_apply": flops,
+                     "peak_note": note + "; achieved = executed Bloch sum-factorised flops (mfk_flops_per_cell) "
+                                         "per application of H~(k) to the block / event time"},
+        "bf16x3": {"s_per_iter": (m3 - m1) / 2, "solve_s": {"iters_1": m1, "iters_3": m3},
+                   "apply_ms": t_mixed * 1e3,
+                   "roofline": {"bound": "tensor", "achieved": mflops / t_mixed / 1e12, "peak": bpeak,
+                                "unit": "TFLOP/s", "frac": mflops / t_mixed / 1e12 / bpeak,
+                                "traffic": None,
+                                "kernel": "tc_cell_bf16_rings_kernel (Bloch pairs) + tc_assemble_kernel",
+                                "flops_per_apply": mflops,
+                                "peak_note": bnote + "; achieved = algorithmic N_c 8 n_e^2 flops per complex "
+                                                     "band (one complex n_e x n_e block per cell) / event time "
+                                                     "of the whole application (cell products + assembly)"}},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.destroy()
+
+
 # ------------------------------------------------------------------ batching
 def run_batch(args):
     """64 uneven Dirichlet systems (p = 5): the batched Chebyshev filter (one
@@ -970,6 +1057,9 @@ def main():
     args = parse()
     if args.workload == "serving" and args.impl != "reference":
         run_serving(args)
+        return
+    if args.workload == "kpoint" and args.impl != "reference":
+        run_kpoint(args)
         return
     if args.workload == "batch" and args.impl != "reference":
         run_batch(args)

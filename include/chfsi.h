@@ -497,6 +497,24 @@ chfsi_status chfsi_bounds_kpoint(chfsi_ctx* ctx, int lanczos_steps, uint64_t see
 chfsi_status chfsi_solve_kpoint(chfsi_ctx* ctx, double* X, int64_t ldx, int n, int iters, int degree,
                                 double b, double* evals_host);
 
+/* Mixed precision at k: one application Y = H~(k) X on binary32 column pairs
+ * (X, Y device, M x 2n floats, leading dimensions in floats, even, >= 2n),
+ * the cell products in BF16x3: T~_e = H~_e + 1/2 |k|^2 M^{-1/2} A_e M^{-1/2}
+ * on both columns of a pair and one shared block G~ = M^{-1/2} (k.G_e)
+ * M^{-1/2} on the swapped pair (re, im) -> (im, -re), the assembly as for
+ * the real operator.  Needs every cell to share the M^{-1/2} pattern (the
+ * uniform periodic box; CHFSI_ERR_ARG otherwise) and the cell matrices
+ * (CHFSI_ERR_STATE after a device-side potential). */
+chfsi_status chfsi_apply_kpoint_mixed(chfsi_ctx* ctx, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                                      int n);
+
+/* chfsi_solve_kpoint with a filter precision: CHFSI_FP64 (the binary64 solve)
+ * or CHFSI_MIXED_BF16X3: each iteration filters a binary32 copy of the block
+ * with the mixed application above (Eq. chebFilter), then CholGS and
+ * Rayleigh-Ritz run in binary64 on X as in chfsi_solve_kpoint. */
+chfsi_status chfsi_solve_kpoint_prec(chfsi_ctx* ctx, double* X, int64_t ldx, int n, int iters, int degree,
+                                     double b, chfsi_precision filter_prec, double* evals_host);
+
 /* ---------------------------------------------------------- domain decomposition
  * Partition of the mesh's cells over nranks ranks (the paper's primary level
  * of parallelism, Sec. 3.7: subdomains of the FE mesh on separate tasks; since

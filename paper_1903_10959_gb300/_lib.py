@@ -100,6 +100,9 @@ _SIGS = {
     "chfsi_set_cell_tile": (C.c_int, [_vp, C.c_int]),
     "chfsi_set_gemm_kernels": (C.c_int, [_vp, C.c_int, C.c_int]),
     "chfsi_set_filter_lanes": (C.c_int, [_vp, C.c_int]),
+    "chfsi_apply_kpoint_mixed": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_int]),
+    "chfsi_solve_kpoint_prec": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                          _vp]),
     "chfsi_autotune": (C.c_int, [_vp, _vp, _i64, C.c_int, C.c_int, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), _dp]),
     "chfsi_fill_uniform": (C.c_int, [_vp, _vp, _i64, _i64, C.c_int, C.c_uint64, C.c_uint64, C.c_int]),
@@ -412,12 +415,25 @@ class Context:
         self._check(self._lib.chfsi_bounds_kpoint(self._h, int(steps), int(seed), _ptr(b)))
         return float(b[0])
 
-    def solve_kpoint(self, X, iters, degree, b):
+    def solve_kpoint(self, X, iters, degree, b, prec="fp64"):
+        """ChFSI at k on a complex128 block; prec "bf16x3" filters in mixed precision."""
         px, ldx, n = self._cdev(X)
         ev = np.empty(n)
-        self._check(self._lib.chfsi_solve_kpoint(self._h, px, ldx, n, int(iters), int(degree), float(b),
-                                                 _ptr(ev)))
+        self._check(self._lib.chfsi_solve_kpoint_prec(self._h, px, ldx, n, int(iters), int(degree), float(b),
+                                                      _prec(prec), _ptr(ev)))
         return ev
+
+    def apply_kpoint_mixed(self, X, Y):
+        """Y = H~(k) X on complex64 blocks (BF16x3 cell products)."""
+        import torch
+        for t in (X, Y):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64 \
+                    or t.dim() != 2 or t.stride(1) != 1:
+                raise TypeError("mixed k-point blocks: 2-D CUDA complex64 tensors with unit column stride")
+        if X.shape != Y.shape:
+            raise ValueError("X and Y need the same shape")
+        self._check(self._lib.chfsi_apply_kpoint_mixed(self._h, X.data_ptr(), 2 * X.stride(0), Y.data_ptr(),
+                                                       2 * Y.stride(0), X.shape[1]))
 
     def set_cell_gather(self, mode):
         """BF16x3 cell kernel: "registers" (register gather, one ring), "async"

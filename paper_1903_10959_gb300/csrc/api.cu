@@ -171,6 +171,7 @@ void free_device_data(chfsi_ctx* ctx) {
   ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes + ctx->tc.nl_bytes +
                               ctx->tc.pj_bytes);   // packed copies
   tc_free(ctx->tc);
+  ctx->kpack_valid = false;   // the mixed Bloch packs hold the old cell matrices
   release(ctx, ctx->d_site_ptr, ctx->hproj.site_ptr.size() * 8);
   release(ctx, ctx->d_site_dof, ctx->hproj.site_dof.size() * 4);
   release(ctx, ctx->d_site_c, ctx->hproj.site_c.size() * 8);
@@ -868,6 +869,8 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
   release(ctx, ctx->d_msq, m.mass.size() * 8);
   if (ctx->d_kfac) cudaFree(ctx->d_kfac);
   ctx->d_kfac = nullptr;
+  for (void* q : {(void*)ctx->d_kA, (void*)ctx->d_kG, (void*)ctx->kbf, (void*)ctx->kgbf})
+    if (q) cudaFree(q);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
                     &ctx->cmaxb, &ctx->pjb,

@@ -57,6 +57,15 @@ struct chfsi_ctx {
   double kpt[3] = {0, 0, 0};       // Bloch wavevector of the k-point entry points
   bool kset = false;
   double* d_kfac = nullptr;        // k-point factors of the matrix-free Bloch apply
+  // mixed-precision Bloch apply: the shared cell blocks 1/2 |k|^2 A~ and G~
+  // (binary64 n_e x n_e on the device; empty when the mesh's scaling pattern
+  // differs between cells) and their BF16x3 packs for the current k
+  double* d_kA = nullptr;
+  double* d_kG = nullptr;
+  uint16_t* kbf = nullptr;         // T~_e = H~_e + 1/2 |k|^2 A~, every cell
+  uint16_t* kgbf = nullptr;        // G~, one block
+  size_t kbf_bytes = 0, kgbf_bytes = 0;
+  bool kpack_valid = false;
   bool scf_setup = false;          // scfb holds the load of 1 and the weights
   double scf_msum = 0.0;           // sum_j int N_j (the box volume)
   chfsi::DevBuf Db;                // density tables: M^{-1/2}, basis at Gauss points, weights

@@ -198,8 +198,10 @@ __device__ __forceinline__ void f16_split2_pair(float x0, float x1, uint32_t& w1
   w2 = cvt_f16x2(r1, r0);
 }
 
+// add (optional): an n_e x n_e matrix added to every cell's matrix first.
 __global__ void tc_pack_bf16_kernel(const double* __restrict__ Ht, uint16_t* __restrict__ out,
-                                    int64_t ncells, int ne, int mt, int nk16) {
+                                    int64_t ncells, int ne, int mt, int nk16,
+                                    const double* __restrict__ add = nullptr) {
   const int64_t per_chunk = (int64_t)mt * 2048;   // elements of one term, all tiles
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= ncells * nk16 * per_chunk) return;
@@ -212,13 +214,32 @@ __global__ void tc_pack_bf16_kernel(const double* __restrict__ Ht, uint16_t* __r
   const int w = (int)(rem - t * 2048);
   const int r = w / BF_KC, k = w % BF_KC;
   const int row = t * 128 + r, col = kc * BF_KC + k;
-  const double v = (row < ne && col < ne) ? Ht[(e * ne + row) * (int64_t)ne + col] : 0.0;
+  double v = (row < ne && col < ne) ? Ht[(e * ne + row) * (int64_t)ne + col] : 0.0;
+  if (add && row < ne && col < ne) v += add[(int64_t)row * ne + col];
   uint16_t b1, b2, b3;
   bf16_split3(v, b1, b2, b3);
   uint16_t* base = out + (e * nk16 + kc) * 3 * per_chunk + (int64_t)t * 2048 + bf_elem_off(r, k);
   base[0] = b1;
   base[per_chunk] = b2;
   base[2 * per_chunk] = b3;
+}
+
+cudaError_t tc_pack_bf16_matrices(const double* dH, const double* dadd, int64_t ncells, int ne, uint16_t** out,
+                                  size_t* bytes, cudaStream_t s) {
+  const int mt = (ne + 127) / 128, nk16 = (ne + BF_KC - 1) / BF_KC;
+  const size_t need = (size_t)ncells * nk16 * 3 * mt * 2048 * sizeof(uint16_t);
+  if (!*out) {
+    cudaError_t e = cudaMalloc(out, need);
+    if (e != cudaSuccess) {
+      *out = nullptr;
+      return e;
+    }
+    *bytes = need;
+  }
+  const int64_t n = ncells * (int64_t)nk16 * mt * 2048;
+  note_launch();
+  tc_pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dH, *out, ncells, ne, mt, nk16, dadd);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_pack_bf16_from_device(TcCellData& d, const double* dHt, cudaStream_t s,
@@ -1299,11 +1320,17 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3, int p
 // projection Z = C~^T Y instead of the cell products: the streamed operand is
 // the cell's projection block (np[e] rows = its projectors, K = its nodes),
 // the result (128 columns x np[e]) goes to rows pj_row[e] .. of R.
-template <int NPAIR, bool MULTI, int NT = 3, bool NLC = false, bool PROJ = false>
+// KPT: the Bloch term of H~(k): the K loop continues over a second pass of
+// the cell's nodes against one shared block (P.nlA: G~ = M^{-1/2} (k.G_e)
+// M^{-1/2}, the same for every cell of the uniform periodic mesh), the rows
+// of Y gathered with each (real, imaginary) column pair swapped and the new
+// imaginary part negated, so R holds T~_e Y_r + G~ Y_i, T~_e Y_i - G~ Y_r.
+template <int NPAIR, bool MULTI, int NT = 3, bool NLC = false, bool PROJ = false, bool KPT = false>
 __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_kernel(RParams P) {
   static_assert(NT == 3 || (NT == 2 && !MULTI), "BF16x3, or single-system FP16x2");
   static_assert(!NLC || (NT == 3 && !MULTI), "projector chunks: single-system BF16x3");
   static_assert(!PROJ || (NT == 3 && !MULTI && !NLC), "projection: single-system BF16x3");
+  static_assert(!KPT || (NT == 3 && !MULTI && !NLC && !PROJ), "Bloch term: single-system BF16x3");
   constexpr int NTHR = (2 * NPAIR + 2) * 32;
   constexpr int WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1;
   constexpr int YT = NT * 128 * BF_KC * 2;   // Y stage bytes
@@ -1381,7 +1408,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   // projector chunks (BF16x3, single system): K continues over the cell's
   // 4 ns_e projectors with the rows of Z as the gathered operand
   const int nl0 = NLC ? P.nl_off[e] : 0;
-  const int nkt = NLC ? nk + P.nl_off[e + 1] - nl0 : nk;
+  const int nkt = NLC ? nk + P.nl_off[e + 1] - nl0 : (KPT ? 2 * nk : nk);
 
   if (warp == WPROD) {
     if (lane == 0) {
@@ -1389,9 +1416,9 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
       const char* Ae = PROJ ? reinterpret_cast<const char*>(P.A) + P.pj_off[e] * 2
                             : reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
       const int64_t tstride = PROJ ? (int64_t)hrow : term_bytes;   // bytes between terms and chunks
-      const char* An = NLC ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
-                                 (int64_t)r0 * 32
-                           : Ae;   // chunk i >= nk of the projector block
+      const char* An = NLC || KPT ? reinterpret_cast<const char*>(P.nlA) + ((int64_t)nl0 - nk) * NT * term_bytes +
+                                        (int64_t)r0 * 32
+                                  : Ae;   // chunk i >= nk of the projector / Bloch block
       int issued = 0;
       for (int i = 0; i < nkt; ++i) {
         const int s = i % SM;
@@ -1403,7 +1430,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         if (*(volatile int*)abort_flag) break;
         const uint32_t dst = mbase + s * mstage;
         mbar_arrive_expect_tx(fa(s), NT * hrow);
-        const char* src = !NLC || i < nk ? Ae : An;
+        const char* src = !(NLC || KPT) || i < nk ? Ae : An;
 #pragma unroll
         for (int p = 0; p < NT; ++p)
           bulk_g2s(dst + p * hrow, src + ((int64_t)i * NT + p) * tstride, hrow, fa(s));
@@ -1466,16 +1493,22 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
       const int s = i % SY;
       float v[8][4];
       const bool zc = NLC && i >= nk;   // a projector chunk: rows of Z
+      const bool sw = KPT && i >= nk;   // a Bloch chunk: the cell's rows again, columns swapped
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int l = i * BF_KC + q * 8 + a;
+        const int l = (sw ? i - nk : i) * BF_KC + q * 8 + a;
         const int g = zc ? P.nl_zrow[(int64_t)(nl0 + i - nk) * BF_KC + q * 8 + a] : (l < ne ? dm[l] : -1);
         const float* src = zc ? P.Z + (int64_t)(g < 0 ? 0 : g) * P.ldz + c0
                               : P.Yin + (int64_t)(g < 0 ? 0 : g) * P.ld_in + c0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int c = lane + 32 * u;
-          v[a][u] = (g >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
+          if (KPT && sw) {   // (re, im) -> (im, -re)
+            const float y = (g >= 0 && c < ncv) ? __ldg(src + (c ^ 1)) : 0.f;
+            v[a][u] = (c & 1) ? -y : y;
+          } else {
+            v[a][u] = (g >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
+          }
         }
       }
       if (i >= SY && !mbar_wait(ey(s), ((i / SY) - 1) & 1)) {
@@ -1757,6 +1790,23 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
     P.nl_zrow = d.nl_zrow;
     P.Z = a.Z;
     P.ldz = a.ldz;
+  }
+  if (a.kG) {   // the Bloch block: the ring kernel with two-column pairs
+    if (a.Z || (a.ncol & 1) || (a.ld_in & 1)) return cudaErrorInvalidValue;
+    P.nlA = a.kG;
+    static std::once_flag attrk;
+    std::call_once(attrk, [] {
+      cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false, 3, false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    const BfrPlan BK = bfr_plan(d.ne, 2);
+    for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
+      P.e_off = e0;
+      dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+      note_launch();
+      tc_cell_bf16_rings_kernel<2, false, 3, false, false, true><<<grid, 6 * 32, BK.total, s>>>(P);
+    }
+    return cudaGetLastError();
   }
   static std::once_flag attr;
   std::call_once(attr, [] {

@@ -15,6 +15,12 @@
 //  RR      : H^ = X^H H~ X, H^ Q = Q D (zheevd, ascending), X <- X Q (Sec. 3.5).
 //  bounds  : k-step Lanczos on the real 2M-dimensional form of H~(k) (same
 //            spectrum, each value twice).
+//  mixed   : the filter on binary32 column pairs with BF16x3 cell products:
+//            T~_e = H~_e + 1/2 |k|^2 A~ on both columns of a pair, and one
+//            shared block G~ = M^{-1/2} (k.G) M^{-1/2} on the swapped pair
+//            (re, im) -> (im, -re), in one ring-kernel launch per step; the
+//            uniform periodic mesh gives every cell the same A~ and G~.
+//            CholGS / RR stay binary64 on the binary64 block.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -183,6 +189,98 @@ chfsi_status kfilter(chfsi_ctx* ctx, double* X, int64_t ldx, int n, int degree, 
   return CHFSI_OK;
 }
 
+// Pack the mixed-path blocks for the current k (after a rebuild or a new k).
+chfsi_status kpack_mixed(chfsi_ctx* ctx) {
+  if (ctx->kpack_valid) return CHFSI_OK;
+  const HostMesh& m = ctx->mesh;
+  if (!ctx->d_kA || !ctx->d_kG)
+    return kfail(ctx, CHFSI_ERR_ARG, "mixed k-points need every cell to share the M^{-1/2} pattern");
+  if (!ctx->d_Ht) return kfail(ctx, CHFSI_ERR_STATE, "no cell matrices (device-side potential)");
+  const bool fresh_a = !ctx->kbf, fresh_g = !ctx->kgbf;
+  KK(tc_pack_bf16_matrices(ctx->d_Ht, ctx->d_kA, m.ncells, m.ne, &ctx->kbf, &ctx->kbf_bytes, ctx->stream));
+  KK(tc_pack_bf16_matrices(ctx->d_kG, nullptr, 1, m.ne, &ctx->kgbf, &ctx->kgbf_bytes, ctx->stream));
+  if (fresh_a) ctx->dev_bytes += (int64_t)ctx->kbf_bytes;
+  if (fresh_g) ctx->dev_bytes += (int64_t)ctx->kgbf_bytes;
+  ctx->kpack_valid = true;
+  return CHFSI_OK;
+}
+
+// Mixed Bloch step on binary32 column pairs (ld in floats, nvec complex vectors):
+// Y = alpha (H~(k) Yin - shift Yin) + beta Yprev.
+chfsi_status kapply_mixed(chfsi_ctx* ctx, const float* Yin, int64_t ld_in, float* Yout, int64_t ld_out,
+                          const float* Yprev, int64_t ld_prev, int nvec, double alpha, double beta,
+                          double shift) {
+  const HostMesh& m = ctx->mesh;
+  const int ncol = 2 * nvec;
+  chfsi_status st;
+  if ((st = kgrow(ctx, ctx->kY, (size_t)m.ncells * m.ne * ncol * 4)) != CHFSI_OK) return st;
+  TcCellData view = ctx->tc;
+  view.bf = ctx->kbf;
+  TcApplyArgs ra{};
+  ra.dofmap = ctx->d_dofmap;
+  ra.ncells = m.ncells;
+  ra.ncol = ncol;
+  ra.Yin = Yin;
+  ra.ld_in = ld_in;
+  ra.R = (float*)ctx->kY.ptr;
+  ra.split3 = 1;
+  ra.gather = 2;
+  ra.kG = ctx->kgbf;
+  KK(tc_cell_bf16_launch(view, ra, ctx->stream));
+  AssembleParams ap{};
+  ap.node_ptr = ctx->d_node_ptr;
+  ap.node_ent = ctx->d_node_ent;
+  ap.M = m.ndofs;
+  ap.ncol = ncol;
+  ap.R = (const float*)ctx->kY.ptr;
+  ap.Yin = Yin;
+  ap.ld_in = ld_in;
+  ap.Yout = Yout;
+  ap.ld_out = ld_out;
+  ap.Yprev = beta != 0.0 ? Yprev : nullptr;
+  ap.ld_prev = ld_prev;
+  ap.alpha = (float)alpha;
+  ap.beta = (float)beta;
+  ap.shift = (float)shift;
+  KK(tc_assemble_launch(ap, ctx->stream));
+  return CHFSI_OK;
+}
+
+// The Chebyshev filter (Eq. chebFilter) of a binary32 block of column pairs.
+chfsi_status kfilter_mixed(chfsi_ctx* ctx, float* X, int64_t ldx, int n, int degree, double a, double b,
+                           double a0) {
+  const HostMesh& m = ctx->mesh;
+  chfsi_status st;
+  if ((st = kpack_mixed(ctx)) != CHFSI_OK) return st;
+  if ((st = kgrow(ctx, ctx->kwork, (size_t)m.ndofs * 2 * n * 4)) != CHFSI_OK) return st;
+  const double e = (b - a) / 2.0, c = (b + a) / 2.0, s1 = e / (a0 - c);
+  float* bufs[2] = {X, (float*)ctx->kwork.ptr};
+  int64_t lds[2] = {ldx, 2 * (int64_t)n};
+  int cur = 0;
+  double sig = s1;
+  for (int k = 1; k <= degree; ++k) {
+    double alpha, beta;
+    if (k == 1) {
+      alpha = s1 / e;
+      beta = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / s1 - sig);
+      alpha = 2.0 * sn / e;
+      beta = -sig * sn;
+      sig = sn;
+    }
+    const int nxt = 1 - cur;
+    if ((st = kapply_mixed(ctx, bufs[cur], lds[cur], bufs[nxt], lds[nxt], bufs[nxt], lds[nxt], n, alpha, beta,
+                           c)) != CHFSI_OK)
+      return st;
+    cur = nxt;
+  }
+  if (cur == 1)
+    KK(cudaMemcpy2DAsync(X, ldx * 4, ctx->kwork.ptr, 2 * (size_t)n * 4, 2 * (size_t)n * 4, m.ndofs,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  return CHFSI_OK;
+}
+
 // C (n1 x n2 complex, column-major, ld n1) = A^H B over the unknowns.
 chfsi_status kgram(chfsi_ctx* ctx, const double* A, int64_t lda, const double* B, int64_t ldb, int n1,
                    int n2, cuDoubleComplex* C) {
@@ -315,6 +413,60 @@ chfsi_status chfsi_set_kpoint(chfsi_ctx* ctx, const double* k) {
     ctx->dev_bytes += (int64_t)fac.size() * 8;
   }
   KK(cudaMemcpyAsync(ctx->d_kfac, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  // dense shared blocks of the mixed path: A3 = A_z (x) A_y (x) A_x and
+  // G3 = k_x A_z A_y C_x + k_y A_z C_y A_x + k_z C_z A_y A_x (node l = i + n1 (j + n1 kz)),
+  // scaled by the cells' M^{-1/2} pattern when that pattern is the same in every cell
+  const int ne = m.ne;
+  bool uniform = true;
+  std::vector<double> sc(ne);
+  for (int l = 0; l < ne; ++l) sc[l] = 1.0 / std::sqrt(m.mass[m.dofmap[l]]);
+  for (int64_t e = 1; e < m.ncells && uniform; ++e)
+    for (int l = 0; l < ne; ++l)
+      if (std::fabs(1.0 / std::sqrt(m.mass[m.dofmap[e * ne + l]]) - sc[l]) > 1e-12 * sc[l]) {
+        uniform = false;
+        break;
+      }
+  ctx->kpack_valid = false;
+  if (uniform) {
+    const double* Ax = base.data();
+    const double* Ay = Ax + nn;
+    const double* Az = Ay + nn;
+    std::vector<double> A3((size_t)ne * ne), G3((size_t)ne * ne);
+    for (int kz = 0; kz < n1; ++kz)
+      for (int jy = 0; jy < n1; ++jy)
+        for (int ix = 0; ix < n1; ++ix) {
+          const int l = ix + n1 * (jy + n1 * kz);
+          for (int kz2 = 0; kz2 < n1; ++kz2)
+            for (int jy2 = 0; jy2 < n1; ++jy2)
+              for (int ix2 = 0; ix2 < n1; ++ix2) {
+                const int l2 = ix2 + n1 * (jy2 + n1 * kz2);
+                const double az = Az[kz * n1 + kz2], ay = Ay[jy * n1 + jy2], ax = Ax[ix * n1 + ix2];
+                const double a = az * ay * ax;
+                const double g = az * ay * C[ix * n1 + ix2] + az * C[nn + jy * n1 + jy2] * ax +
+                                 C[2 * nn + kz * n1 + kz2] * ay * ax;
+                A3[(size_t)l * ne + l2] = 0.5 * k2 * a * sc[l] * sc[l2];
+                G3[(size_t)l * ne + l2] = g * sc[l] * sc[l2];
+              }
+        }
+    for (double** dp : {&ctx->d_kA, &ctx->d_kG})
+      if (!*dp) {
+        if (cudaMalloc(dp, (size_t)ne * ne * 8) != cudaSuccess) {
+          cudaGetLastError();
+          *dp = nullptr;
+          return kfail(ctx, CHFSI_ERR_OOM, "k-point blocks");
+        }
+        ctx->dev_bytes += (int64_t)ne * ne * 8;
+      }
+    KK(cudaMemcpyAsync(ctx->d_kA, A3.data(), A3.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    KK(cudaMemcpyAsync(ctx->d_kG, G3.data(), G3.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    for (double** dp : {&ctx->d_kA, &ctx->d_kG})
+      if (*dp) {
+        cudaFree(*dp);
+        *dp = nullptr;
+        ctx->dev_bytes -= (int64_t)ne * ne * 8;
+      }
+  }
   KK(cudaStreamSynchronize(ctx->stream));
   for (int d = 0; d < 3; ++d) ctx->kpt[d] = k[d];
   ctx->kset = true;
@@ -399,6 +551,50 @@ chfsi_status chfsi_bounds_kpoint(chfsi_ctx* ctx, int lanczos_steps, uint64_t see
     else lo = mid;
   }
   *b_out = hi + std::fabs(be[k - 1]);
+  return CHFSI_OK;
+}
+
+chfsi_status chfsi_apply_kpoint_mixed(chfsi_ctx* ctx, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                                      int n) {
+  chfsi_status st = kcheck(ctx);
+  if (st != CHFSI_OK) return st;
+  if (n < 0 || (n > 0 && (!X || !Y || ldx < 2 * n || ldy < 2 * n || (ldx & 1))))
+    return kfail(ctx, CHFSI_ERR_ARG, "bad X / Y / leading dimensions (in floats, even, >= 2 n)");
+  if (n == 0) return CHFSI_OK;
+  if ((st = kpack_mixed(ctx)) != CHFSI_OK) return st;
+  return kapply_mixed(ctx, X, ldx, Y, ldy, nullptr, 0, n, 1.0, 0.0, 0.0);
+}
+
+chfsi_status chfsi_solve_kpoint_prec(chfsi_ctx* ctx, double* X, int64_t ldx, int n, int iters, int degree,
+                                     double b, chfsi_precision filter_prec, double* evals_host) {
+  if (filter_prec == CHFSI_FP64) return chfsi_solve_kpoint(ctx, X, ldx, n, iters, degree, b, evals_host);
+  chfsi_status st = kcheck(ctx);
+  if (st != CHFSI_OK) return st;
+  if (filter_prec != CHFSI_MIXED_BF16X3) return kfail(ctx, CHFSI_ERR_ARG, "k-point filter: binary64 or BF16x3");
+  if (n < 1 || !X || ldx < 2 * n || iters < 0 || degree < 1 || !evals_host)
+    return kfail(ctx, CHFSI_ERR_ARG, "bad k-point solve arguments");
+  const HostMesh& m = ctx->mesh;
+  if ((st = kpack_mixed(ctx)) != CHFSI_OK) return st;
+  // binary32 copy of the block for the filter; CholGS / RR on the binary64 block
+  if ((st = kgrow(ctx, ctx->kvec, (size_t)m.ndofs * 2 * n * 4 + 16)) != CHFSI_OK) return st;
+  float* X32 = (float*)ctx->kvec.ptr;
+  const int64_t ld32 = 2 * (int64_t)n;
+  std::vector<double> D(n);
+  if ((st = kcholgs(ctx, X, ldx, n)) != CHFSI_OK) return st;
+  if ((st = krr(ctx, X, ldx, n, D.data())) != CHFSI_OK) return st;
+  for (int it = 0; it < iters; ++it) {
+    double a = D[n - 1], a0 = D[0];
+    if (!(a < b)) return kfail(ctx, CHFSI_ERR_ARG, "upper bound b must exceed the largest Ritz value");
+    if (!(a0 < a)) a0 = a - 1e-3 * std::max(1.0, std::fabs(a));
+    KK(launch_copy_cols(X, ldx, X32, ld32, m.ndofs, 2 * n, 1, 0, ctx->stream));
+    if ((st = kfilter_mixed(ctx, X32, ld32, n, degree, a, b, a0)) != CHFSI_OK) return st;
+    KK(launch_copy_cols(X32, ld32, X, ldx, m.ndofs, 2 * n, 0, 1, ctx->stream));
+    if ((st = kcholgs(ctx, X, ldx, n)) != CHFSI_OK) return st;
+    if ((st = krr(ctx, X, ldx, n, D.data())) != CHFSI_OK) return st;
+  }
+  if (tc_read_status(ctx->stream)) return kfail(ctx, CHFSI_ERR_TIMEOUT, "device wait timed out");
+  KK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(evals_host, D.data(), (size_t)n * 8);
   return CHFSI_OK;
 }
 

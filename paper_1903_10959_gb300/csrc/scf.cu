@@ -480,6 +480,7 @@ chfsi_status chfsi_set_potential_qp_device(chfsi_ctx* ctx, const double* v) {
   }
   ctx->dev_bytes -= (int64_t)(ctx->tc.bytes + ctx->tc.bf_bytes + ctx->tc.f16_bytes + ctx->tc.nl_bytes +
                               ctx->tc.pj_bytes);
+  ctx->kpack_valid = false;
   tc_free(ctx->tc);
   ctx->tc.ncells = m.ncells;
   ctx->tc.ne = m.ne;

@@ -62,9 +62,18 @@ struct TcApplyArgs {
   // operand, so R holds H~_loc Y plus the owned rows' share of C~ h Z
   const float* Z = nullptr;
   int64_t ldz = 0;
+  // Bloch term (complex blocks as (real, imaginary) column pairs): the shared
+  // BF16x3 block of G~ = M^{-1/2} (k.G_e) M^{-1/2}; the cell data then holds
+  // T~_e = H~_e + 1/2 |k|^2 M^{-1/2} A_e M^{-1/2}
+  const uint16_t* kG = nullptr;
 };
 // Whether tc_cell_bf16_launch can add the projector chunks for this gather mode.
 inline bool tc_cell_bf16_nl_ok(int gather) { return gather == 2 || gather == 3; }
+// BF16x3 terms of ncells n_e x n_e binary64 matrices (plus add, an n_e x n_e
+// matrix added to each, when not null) into *out (allocated on first use,
+// *bytes set), in the packed cell-matrix layout.
+cudaError_t tc_pack_bf16_matrices(const double* dH, const double* dadd, int64_t ncells, int ne, uint16_t** out,
+                                  size_t* bytes, cudaStream_t s);
 // Pack the projection blocks of build_nl_cells into d.pj (and its tables).
 cudaError_t tc_pack_proj(TcCellData& d, int64_t ncells, int nsite, const int32_t* np, const int64_t* poff,
                          const int64_t* prow, const int32_t* red_ptr, const int64_t* red_row,

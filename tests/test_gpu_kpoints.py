@@ -93,3 +93,46 @@ def test_solve_matches_dense_bands_and_time_reversal():
         assert np.abs(bands[0][:8] - bands[1][:8]).max() < 1e-10
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("p", [3, 5, 6])
+def test_mixed_apply_matches_oracle(p):
+    """BF16x3 Bloch apply on binary32 column pairs (T~_e on both columns, the
+    shared G~ on the swapped pair) against the oracle's complex H~(k): 1e-5
+    relative, as every BF16x3 application; ragged and multi-tile widths."""
+    s, prob, ctx = _system(3 if p <= 4 else 2, p, seed=p)
+    try:
+        for k in ([0.31, -0.17, 0.44], [0.0, 0.0, 0.0]):
+            ctx.set_kpoint(k)
+            for n in (1, 37, 70):
+                X0 = _cblock(9 + n, prob.ndofs, n).astype(np.complex64)
+                Y = torch.empty((prob.ndofs, n), dtype=torch.complex64, device=DEV)
+                ctx.apply_kpoint_mixed(torch.tensor(X0, device=DEV), Y)
+                ref = okp.BlochProblem(prob, k).apply_Htilde(X0.astype(np.complex128))
+                got = Y.cpu().numpy().astype(np.complex128)
+                assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), (k, n)
+    finally:
+        ctx.destroy()
+
+
+def test_mixed_solve_matches_dense_bands():
+    """ChFSI at k with the BF16x3 filter (binary64 CholGS / RR on the binary64
+    block): the wanted bands within the method statement's 1e-7 Ha of the
+    oracle's dense complex spectrum, an orthonormal block, and the same bands
+    as the binary64 solve to 1e-7 Ha."""
+    s, prob, ctx = _system(2, 3, L=5.0)
+    try:
+        n, k = 12, np.array([0.35, -0.2, 0.15])
+        exact = np.linalg.eigvalsh(okp.BlochProblem(prob, k).dense_Htilde())
+        ctx.set_kpoint(k)
+        b = ctx.bounds_kpoint(20, 3)
+        X = torch.tensor(_cblock(11, prob.ndofs, n), device=DEV)
+        ev = ctx.solve_kpoint(X, 30, 20, b * 1.01, prec="bf16x3")
+        assert np.abs(ev[:8] - exact[:8]).max() < 1e-7
+        Q = X.cpu().numpy()
+        assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-12
+        X64 = torch.tensor(_cblock(11, prob.ndofs, n), device=DEV)
+        ev64 = ctx.solve_kpoint(X64, 30, 20, b * 1.01)
+        assert np.abs(ev[:8] - ev64[:8]).max() < 1e-7
+    finally:
+        ctx.destroy()
