@@ -1330,13 +1330,12 @@ chfsi_status chfsi_density(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, co
   if (n_fr < 0 || n_fr > 0 && (!Xfr || ldfr < n_fr || !occ_fr_host) || !rho)
     return fail(ctx, CHFSI_ERR_ARG, "bad density arguments");
   const HostMesh& m = ctx->mesh;
-  // tables: M^{-1/2} (M doubles), basis at the Gauss points (q x n1), weights 2 (f - 1)
+  // tables: basis at the Gauss points (q x n1), weights 2 (f - 1); M^{-1/2} is resident
   const size_t nb = (size_t)m.q * m.n1;
-  if ((st = grow(ctx, ctx->Db, ((size_t)m.ndofs + nb + (size_t)n_fr + 8) * 8)) != CHFSI_OK) return st;
-  std::vector<double> h((size_t)m.ndofs + nb + (size_t)n_fr);
-  for (int64_t j = 0; j < m.ndofs; ++j) h[j] = 1.0 / std::sqrt(m.mass[j]);
-  std::copy(m.B.begin(), m.B.end(), h.begin() + m.ndofs);
-  for (int j = 0; j < n_fr; ++j) h[m.ndofs + nb + j] = 2.0 * (occ_fr_host[j] - 1.0);
+  if ((st = grow(ctx, ctx->Db, (nb + (size_t)n_fr + 8) * 8)) != CHFSI_OK) return st;
+  std::vector<double> h(nb + (size_t)n_fr);
+  std::copy(m.B.begin(), m.B.end(), h.begin());
+  for (int j = 0; j < n_fr; ++j) h[nb + j] = 2.0 * (occ_fr_host[j] - 1.0);
   double* d = (double*)ctx->Db.ptr;
   CK(cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
   DensityArgs a{};
@@ -1346,10 +1345,11 @@ chfsi_status chfsi_density(chfsi_ctx* ctx, const void* X, int64_t ldx, int n, co
   a.Xfr = n_fr > 0 ? Xfr : X;
   a.ldfr = n_fr > 0 ? ldfr : ldx;
   a.nfr = n_fr;
-  a.wfr = d + m.ndofs + nb;
+  a.wfr = d + nb;
   a.dofmap = ctx->d_dofmap;
-  a.minv_sqrt = d;
-  a.B = d + m.ndofs;
+  a.minv_sqrt = ctx->d_msq;
+  a.B = d;
+  a.Bh = m.B.data();
   a.ncells = m.ncells;
   a.n1 = m.n1;
   a.q = m.q;

@@ -154,11 +154,205 @@ __global__ void __launch_bounds__(DEN_THREADS) density_kernel(
   }
 }
 
+// Binary32 blocks, q = n1 + 1 (the default rule): the same three passes with
+// the lane as the column.  A CTA takes its cell's columns 32 at a time; every
+// buffer is [line element][32 columns], so each warp access is one
+// conflict-free row of shared memory and each gather load one 128-byte row of
+// X.  The 1-D matrix B lives in the kernel's parameter space (its entries are
+// constant-bank operands of the FMAs), the passes are fully unrolled for the
+// degree, and the z pass never stores its output: each lane squares its q
+// values, weights them by its column's weight, and the warp sums them over its
+// 32 columns by a reduce-scatter (log2 of the padded q halving steps, then the
+// remaining butterfly steps), which leaves every point's chunk sum on four
+// lanes.  The lane with (lane & 3) == 0 adds it to that point's accumulator,
+// a pair of binary32 words updated by Knuth's two-sum (about 44 bits; binary64
+// adds would cost a pass of the GB300's two-per-clock binary64 pipe per line),
+// so the column sum is binary32 within a chunk of 32 columns and carries the
+// pair's precision across chunks, in a fixed order (deterministic).
+constexpr int DEN32_THREADS = 256, DEN32_WARPS = DEN32_THREADS / 32;
+struct DenB {
+  float b[10 * 9];   // B (q x n1), row-major, q = n1 + 1 <= 10
+};
+
+template <int N1>
+struct Den32 {
+  static constexpr int Q = N1 + 1, NE = N1 * N1 * N1, NQ = Q * Q * Q;
+  static constexpr int LA = NE > N1 * Q * Q ? NE : N1 * Q * Q;   // psi, then the y pass output
+  static constexpr int LB = N1 * N1 * Q;                         // the x pass output
+  static constexpr int P2 = Q <= 4 ? 4 : (Q <= 8 ? 8 : 16);      // q padded to a power of two
+  static constexpr int LG = P2 == 4 ? 2 : (P2 == 8 ? 3 : 4);
+  static constexpr int LPW = (Q * Q + DEN32_WARPS - 1) / DEN32_WARPS;   // z lines per warp
+  static constexpr size_t SMEM = (size_t)(LA + LB) * 32 * 4 + (size_t)NE * 8;
+  static constexpr int MINB = SMEM <= 110 * 1024 + 512 ? 2 : 1;   // CTAs per SM the shared memory allows
+};
+
+template <int N1>
+__global__ void __launch_bounds__(DEN32_THREADS, Den32<N1>::MINB) density32_kernel(
+    const float* __restrict__ X, int64_t ldx, int n, const float* __restrict__ Xfr, int64_t ldfr,
+    int nfr, const double* __restrict__ wfr, const int32_t* __restrict__ dofmap,
+    const double* __restrict__ minv_sqrt, const DenB Bc, double* __restrict__ rho) {
+  using D = Den32<N1>;
+  constexpr int Q = D::Q, NE = D::NE, P2 = D::P2;
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  float* bufA = reinterpret_cast<float*>(dsm_raw);
+  float* bufB = bufA + D::LA * 32;
+  int32_t* sdm = reinterpret_cast<int32_t*>(bufB + D::LB * 32);
+  float* sms = reinterpret_cast<float*>(sdm + NE);
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int l = tid; l < NE; l += DEN32_THREADS) {
+    const int g = dofmap[e * NE + l];
+    sdm[l] = g;
+    sms[l] = g >= 0 ? (float)minv_sqrt[g] : 0.f;
+  }
+  float acc_h[D::LPW], acc_l[D::LPW];   // the point's sum as hi + lo
+#pragma unroll
+  for (int m = 0; m < D::LPW; ++m) acc_h[m] = acc_l[m] = 0.f;
+  __syncthreads();
+  const int nchunk_x = (n + 31) / 32, nchunk = nchunk_x + (nfr + 31) / 32;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const bool fr = ch >= nchunk_x;
+    const int c0 = (fr ? ch - nchunk_x : ch) * 32;
+    const int cv = min(32, (fr ? nfr : n) - c0);
+    const float* src = (fr ? Xfr : X) + c0 + lane;
+    const int64_t ld = fr ? ldfr : ldx;
+    const bool live = lane < cv;
+    const float w = !live ? 0.f : (fr ? (float)wfr[c0 + lane] : 2.f);
+    // 1. psi = M^{-1/2} x at the cell's nodes, one row of 32 columns per warp access
+    for (int l0 = warp; l0 < NE; l0 += 4 * DEN32_WARPS) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int l = l0 + u * DEN32_WARPS;
+        const int g = l < NE ? sdm[l] : -1;
+        v[u] = (g >= 0 && live) ? __ldg(src + (int64_t)g * ld) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int l = l0 + u * DEN32_WARPS;
+        if (l < NE) bufA[l * 32 + lane] = sms[l] * v[u];
+      }
+    }
+    __syncthreads();
+    // 2. x: bufB[(k n1 + j) q + a] = sum_i B[a][i] psi[(k n1 + j) n1 + i]
+    for (int kj = warp; kj < N1 * N1; kj += DEN32_WARPS) {
+      float in[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) in[i] = bufA[(kj * N1 + i) * 32 + lane];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) s = fmaf(Bc.b[a * N1 + i], in[i], s);
+        bufB[(kj * Q + a) * 32 + lane] = s;
+      }
+    }
+    __syncthreads();
+    // 3. y: bufA[(k q + b) q + a] = sum_j B[b][j] bufB[(k n1 + j) q + a]
+    for (int r = warp; r < N1 * Q; r += DEN32_WARPS) {
+      const int k = r / Q, a = r - k * Q;
+      float in[N1];
+#pragma unroll
+      for (int j = 0; j < N1; ++j) in[j] = bufB[((k * N1 + j) * Q + a) * 32 + lane];
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) s = fmaf(Bc.b[b * N1 + j], in[j], s);
+        bufA[((k * Q + b) * Q + a) * 32 + lane] = s;
+      }
+    }
+    __syncthreads();
+    // 4. z and the weighted squares: point ab + q^2 cz, psi = sum_k B[cz][k] bufA[k q^2 + ab]
+#pragma unroll
+    for (int m = 0; m < D::LPW; ++m) {
+      const int ab = warp + m * DEN32_WARPS;
+      if (ab >= Q * Q) break;
+      float in[N1];
+#pragma unroll
+      for (int k = 0; k < N1; ++k) in[k] = bufA[(k * Q * Q + ab) * 32 + lane];
+      float v[P2];
+#pragma unroll
+      for (int cz = 0; cz < P2; ++cz) {
+        float s = 0.f;
+        if (cz < Q) {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) s = fmaf(Bc.b[cz * N1 + k], in[k], s);
+        }
+        v[cz] = w * (s * s);
+      }
+      // reduce-scatter over the lanes: after step t the lane keeps the half
+      // of its values selected by lane bit (4 - t)
+      int cnt = P2;
+#pragma unroll
+      for (int t = 0; t < D::LG; ++t) {
+        const int off = 16 >> t;
+        const bool upper = (lane & off) != 0;
+        cnt >>= 1;
+#pragma unroll
+        for (int j = 0; j < P2 / 2; ++j) {
+          if (j < cnt) {
+            const float send = upper ? v[j] : v[j + cnt];
+            const float keep = upper ? v[j + cnt] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = D::LG; t < 5; ++t) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16 >> t);
+      int idx = 0;
+#pragma unroll
+      for (int t = 0; t < D::LG; ++t) idx |= ((lane >> (4 - t)) & 1) << (D::LG - 1 - t);
+      if ((lane & ((1 << (5 - D::LG)) - 1)) == 0 && idx < Q) {   // two-sum into (hi, lo)
+        const float x = v[0], t = __fadd_rn(acc_h[m], x), bp = __fsub_rn(t, acc_h[m]);
+        acc_l[m] = __fadd_rn(acc_l[m], __fadd_rn(__fsub_rn(acc_h[m], __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        acc_h[m] = t;
+      }
+    }
+    __syncthreads();
+  }
+  int idx = 0;
+#pragma unroll
+  for (int t = 0; t < D::LG; ++t) idx |= ((lane >> (4 - t)) & 1) << (D::LG - 1 - t);
+  if ((lane & ((1 << (5 - D::LG)) - 1)) == 0 && idx < Q) {
+#pragma unroll
+    for (int m = 0; m < D::LPW; ++m) {
+      const int ab = warp + m * DEN32_WARPS;
+      if (ab < Q * Q) rho[e * D::NQ + (int64_t)idx * Q * Q + ab] = (double)acc_h[m] + (double)acc_l[m];
+    }
+  }
+}
+
+template <int N1>
+static cudaError_t launch_density32(const DensityArgs& a, cudaStream_t s) {
+  using D = Den32<N1>;
+  DenB Bc;
+  for (int t = 0; t < D::Q * N1; ++t) Bc.b[t] = (float)a.Bh[t];
+  cudaFuncSetAttribute(density32_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::SMEM);
+  note_launch();
+  density32_kernel<N1><<<(unsigned)a.ncells, DEN32_THREADS, D::SMEM, s>>>(
+      (const float*)a.X, a.ldx, a.n, (const float*)a.Xfr, a.ldfr, a.nfr, a.wfr, a.dofmap, a.minv_sqrt, Bc,
+      a.rho);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_density(const DensityArgs& a, cudaStream_t s) {
   if (a.ncells == 0) return cudaSuccess;
   const int nq = a.q * a.q * a.q;
   if (a.q * a.n1 > 256 || nq > DEN_MAXPT * DEN_THREADS || a.n1 > DEN_MAXN)
     return cudaErrorInvalidValue;
+  if (!a.is_double && a.q == a.n1 + 1 && a.Bh && a.ncells <= 0x7fffffff) {
+    switch (a.n1) {
+      case 3: return launch_density32<3>(a, s);
+      case 4: return launch_density32<4>(a, s);
+      case 5: return launch_density32<5>(a, s);
+      case 6: return launch_density32<6>(a, s);
+      case 7: return launch_density32<7>(a, s);
+      case 8: return launch_density32<8>(a, s);
+      case 9: return launch_density32<9>(a, s);
+      default: break;
+    }
+  }
   const size_t es = a.is_double ? 8 : 4;
   int cb = 8;
   while (cb > 1 && den_smem(a.n1, a.q, cb).total * es > 100 * 1024) cb /= 2;   // two CTAs per SM

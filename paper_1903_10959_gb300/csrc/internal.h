@@ -61,6 +61,7 @@ struct DensityArgs {
   const int32_t* dofmap;     // device, ncells x n1^3
   const double* minv_sqrt;   // device, M^{-1/2} per unknown
   const double* B;           // device, q x n1 basis values at the Gauss points
+  const double* Bh;          // host copy of B (the binary32 kernel takes it as a parameter), may be null
   int64_t ncells;
   int n1, q, is_double;
   double* rho;               // device, ncells x q^3

@@ -3,7 +3,8 @@ the oracle (Sec. 3.5, Algorithms rr and dc, Eq. elecDensSP).
 
 Binary64: Ritz values 1e-10, rotated columns 1e-10 (up to sign), density
 1e-12 relative.  Mixed (3xTF32 projection and rotation; density interpolated
-in binary32, three passes of <= 9 terms, summed in binary64): Ritz values
+in binary32, three passes of <= 9 terms, summed in binary32 over 32 columns and
+in binary32 pairs across them): Ritz values
 1e-5 relative to the spectrum's scale, density 1e-6 relative."""
 import numpy as np
 import pytest
@@ -129,3 +130,39 @@ def test_full_pipeline_matches_full_rotation(case):
     ref = od.density(prob, XR * np.sqrt(f)[None, :])
     got = rho.cpu().numpy().reshape(prob.mesh.ncells, q ** 3)
     assert rel_fro(got, ref) < 1e-10
+
+
+@pytest.mark.parametrize("p,periodic", [(2, True), (5, False), (7, True), (8, True)])
+def test_density_binary32_kernel_degrees(p, periodic):
+    """The binary32 density kernel (lane = column, 32-column chunks, sums over
+    the columns by a warp reduce-scatter, binary32-pair accumulation across
+    chunks) against the oracle at p = 2 ... 8: several chunks with a ragged
+    tail for both blocks, partially occupied states with negative weights,
+    a Dirichlet mesh; and against the binary64 kernel on the same values."""
+    s = W.small_periodic(seed=40 + p, ncell=2, p=p, L=2.0 + 0.4 * p, n_wells=2, n_want=8)
+    if not periodic:
+        s.periodic = False
+        s.centres = 0.1 * s.L + 0.8 * s.centres
+    prob = oracle_problem(s)
+    ctx = gpu_context(s)
+    try:
+        n, n_fr = 70, 37
+        x32 = W.start_block(s.seed, prob.ndofs, n).astype(np.float32)
+        f32 = W.start_block(s.seed + 1, prob.ndofs, n_fr).astype(np.float32)
+        occ = np.linspace(0.05, 0.95, n_fr)
+        rho_ref = od.density(prob, x32.astype(np.float64), f32.astype(np.float64), occ)
+        q = prob.basis.q
+        rho = torch.empty(prob.mesh.ncells * q ** 3, dtype=torch.float64, device=DEV)
+        ctx.density(torch.tensor(x32, device=DEV), rho, torch.tensor(f32, device=DEV), occ, prec="mixed")
+        got = rho.cpu().numpy().reshape(prob.mesh.ncells, q ** 3)
+        assert rel_fro(got, rho_ref) < 1e-6
+        rho64 = torch.empty_like(rho)
+        ctx.density(torch.tensor(x32.astype(np.float64), device=DEV), rho64,
+                    torch.tensor(f32.astype(np.float64), device=DEV), occ, prec="fp64")
+        assert rel_fro(got, rho64.cpu().numpy().reshape(prob.mesh.ncells, q ** 3)) < 1e-6
+        # one column: a single ragged chunk, no partially occupied block
+        ctx.density(torch.tensor(x32[:, :1].copy(), device=DEV), rho, prec="mixed")
+        got1 = rho.cpu().numpy().reshape(prob.mesh.ncells, q ** 3)
+        assert rel_fro(got1, od.density(prob, x32[:, :1].astype(np.float64))) < 1e-6
+    finally:
+        ctx.destroy()
