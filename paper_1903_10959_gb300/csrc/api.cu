@@ -184,6 +184,67 @@ void free_device_data(chfsi_ctx* ctx) {
   ++ctx->build_gen;   // device pointers captured elsewhere (batch graphs) are now stale
 }
 
+// The tensor-core copies of the cell data a mixed precision needs (packed on
+// first use, on the context's stream): the BF16x3 / FP16x2 / TF32 cell
+// matrices and, for the BF16x3 ring kernels, the projector chunks and the
+// projection blocks.
+chfsi_status ensure_tc_data(chfsi_ctx* ctx, chfsi_precision prec) {
+  const HostMesh& m = ctx->mesh;
+  const bool nl = ctx->hproj.nsite > 0;
+  if (!ctx->d_Ht)
+    return fail(ctx, CHFSI_ERR_STATE, "no cell matrices: the potential was set on the device "
+                                      "(binary64 only until chfsi_build)");
+  const bool bf16 = prec == CHFSI_MIXED_BF16X3;
+  const bool f16 = prec == CHFSI_MIXED_F16X2;
+  if (f16 && !ctx->tc.f16) {
+    cudaError_t pe = tc_pack_f16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("FP16x2 cell data: ") + cudaGetErrorString(pe));
+    }
+  }
+  if (bf16 && !ctx->tc.bf) {
+    cudaError_t pe = tc_pack_bf16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("BF16x3 cell data: ") + cudaGetErrorString(pe));
+    }
+  }
+  if (!bf16 && !f16 && !ctx->tc.hi) {
+    cudaError_t pe = tc_pack_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("tensor-core cell data: ") + cudaGetErrorString(pe));
+    }
+  }
+  // BF16x3 ring kernels take the projector terms on the tensor cores: the
+  // projection Z = C~^T Y as per-cell blocks over the owned rows (partial sums
+  // reduced per site in a fixed order) and the expansion C~ h Z as extra
+  // K-chunks of the cell products; the assembly then has no projector term
+  const bool nl_in_cells = nl && bf16 && tc_cell_bf16_nl_ok(ctx->cell_gather);
+  if (nl_in_cells && !ctx->tc.nl) {
+    NlCells nc;
+    build_nl_cells(m, ctx->hproj, nc);
+    cudaError_t pe = tc_pack_nl(ctx->tc, nc.chunk_off.data(), m.ncells, nc.zrow.data(), nc.nz_pos.data(),
+                                nc.nz_val.data(), (int64_t)nc.nz_val.size(), ctx->stream, &ctx->dev_bytes);
+    if (pe == cudaSuccess)
+      pe = tc_pack_proj(ctx->tc, m.ncells, ctx->hproj.nsite, nc.np.data(), nc.poff.data(), nc.prow.data(),
+                        nc.red_ptr.data(), nc.red_row.data(), nc.pz_pos.data(), nc.pz_val.data(),
+                        (int64_t)nc.pz_val.size(), ctx->stream, &ctx->dev_bytes);
+    if (pe == cudaErrorNotSupported) {
+      cudaGetLastError();   // too many sites on one cell's rows: the projection stays by site
+    } else if (pe != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
+                  std::string("projector chunks: ") + cudaGetErrorString(pe));
+    }
+  }
+  return CHFSI_OK;
+}
+
 // One recurrence step over the ncol columns of a block:
 // Yout = alpha (H~ Yin - shift Yin) + beta Yprev, colour by colour.
 chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, int64_t ld_in,
@@ -251,57 +312,10 @@ chfsi_status apply_step(chfsi_ctx* ctx, chfsi_precision prec, const void* Yin, i
     return CHFSI_OK;
   }
   // mixed precisions: binary32 storage, tcgen05 TF32 (or BF16x3) cell products
-  if (!ctx->d_Ht)
-    return fail(ctx, CHFSI_ERR_STATE, "no cell matrices: the potential was set on the device "
-                                      "(binary64 only until chfsi_build)");
+  if ((st = ensure_tc_data(ctx, prec)) != CHFSI_OK) return st;
   const bool bf16 = prec == CHFSI_MIXED_BF16X3;
   const bool f16 = prec == CHFSI_MIXED_F16X2;
-  if (f16 && !ctx->tc.f16) {
-    cudaError_t pe = tc_pack_f16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
-    if (pe != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
-                  std::string("FP16x2 cell data: ") + cudaGetErrorString(pe));
-    }
-  }
-  if (bf16 && !ctx->tc.bf) {
-    cudaError_t pe = tc_pack_bf16_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
-    if (pe != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
-                  std::string("BF16x3 cell data: ") + cudaGetErrorString(pe));
-    }
-  }
-  if (!bf16 && !f16 && !ctx->tc.hi) {
-    cudaError_t pe = tc_pack_from_device(ctx->tc, ctx->d_Ht, ctx->stream, &ctx->dev_bytes);
-    if (pe != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
-                  std::string("tensor-core cell data: ") + cudaGetErrorString(pe));
-    }
-  }
-  // BF16x3 ring kernels take the projector terms on the tensor cores: the
-  // projection Z = C~^T Y as per-cell blocks over the owned rows (partial sums
-  // reduced per site in a fixed order) and the expansion C~ h Z as extra
-  // K-chunks of the cell products; the assembly then has no projector term
   const bool nl_in_cells = nl && bf16 && tc_cell_bf16_nl_ok(ctx->cell_gather);
-  if (nl_in_cells && !ctx->tc.nl) {
-    NlCells nc;
-    build_nl_cells(m, ctx->hproj, nc);
-    cudaError_t pe = tc_pack_nl(ctx->tc, nc.chunk_off.data(), m.ncells, nc.zrow.data(), nc.nz_pos.data(),
-                                nc.nz_val.data(), (int64_t)nc.nz_val.size(), ctx->stream, &ctx->dev_bytes);
-    if (pe == cudaSuccess)
-      pe = tc_pack_proj(ctx->tc, m.ncells, ctx->hproj.nsite, nc.np.data(), nc.poff.data(), nc.prow.data(),
-                        nc.red_ptr.data(), nc.red_row.data(), nc.pz_pos.data(), nc.pz_val.data(),
-                        (int64_t)nc.pz_val.size(), ctx->stream, &ctx->dev_bytes);
-    if (pe == cudaErrorNotSupported) {
-      cudaGetLastError();   // too many sites on one cell's rows: the projection stays by site
-    } else if (pe != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, pe == cudaErrorMemoryAllocation ? CHFSI_ERR_OOM : CHFSI_ERR_CUDA,
-                  std::string("projector chunks: ") + cudaGetErrorString(pe));
-    }
-  }
   if (nl) {   // projection Z = C~^T Y
     KTimer kt(ctx, 2);
     if (nl_in_cells && ctx->tc.pj) {
@@ -471,6 +485,7 @@ struct LaneScope {
     std::swap(ctx->Rb, ctx->laneR[l]);
     std::swap(ctx->Zb, ctx->laneZ[l]);
     std::swap(ctx->cmaxb, ctx->laneC[l]);
+    std::swap(ctx->pjb, ctx->laneP[l]);
   }
   ~LaneScope() {
     if (l == 0) return;
@@ -478,6 +493,7 @@ struct LaneScope {
     std::swap(ctx->Rb, ctx->laneR[l]);
     std::swap(ctx->Zb, ctx->laneZ[l]);
     std::swap(ctx->cmaxb, ctx->laneC[l]);
+    std::swap(ctx->pjb, ctx->laneP[l]);
     ctx->stream = saved;
   }
 };
@@ -492,6 +508,10 @@ chfsi_status filter_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int ncol, int deg
   const int tiles = (ncol + 127) / 128;
   const int L = is_mixed(prec) ? std::min(ctx->filter_lanes, tiles) : 1;
   if (L <= 1) return filter_range(ctx, X, ldx, ncol, degree, a, b, a0, prec);
+  // the shared cell data is packed before the lanes fork, so every lane's
+  // stream is ordered after it
+  chfsi_status st0 = ensure_tc_data(ctx, prec);
+  if (st0 != CHFSI_OK) return st0;
   for (int l = 0; l < L; ++l) {
     if (l > 0 && !ctx->lane_stream[l])
       CK(cudaStreamCreateWithFlags(&ctx->lane_stream[l], cudaStreamNonBlocking));
@@ -878,7 +898,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
                     &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);
   for (int l = 0; l < chfsi_ctx::kMaxLanes; ++l) {
-    for (DevBuf* b : {&ctx->laneT1[l], &ctx->laneR[l], &ctx->laneZ[l], &ctx->laneC[l]})
+    for (DevBuf* b : {&ctx->laneT1[l], &ctx->laneR[l], &ctx->laneZ[l], &ctx->laneC[l], &ctx->laneP[l]})
       dfree(ctx, b->ptr, b->bytes);
     if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
     if (ctx->lane_ev[l]) cudaEventDestroy(ctx->lane_ev[l]);

@@ -75,7 +75,7 @@ struct chfsi_ctx {
   int filter_lanes = 1;
   cudaStream_t lane_stream[kMaxLanes] = {};   // lane 0 runs on `stream`
   cudaEvent_t lane_ev[kMaxLanes] = {};
-  chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes], laneC[kMaxLanes];
+  chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes], laneC[kMaxLanes], laneP[kMaxLanes];
   chfsi::DevBuf cmaxb;             // FP16x2: column maxima of the filter's blocks (3 x ncol words)
   chfsi::DevBuf pjb;               // partial projections of the cells (pj_rows x ncol)
   cusolverDnHandle_t sol = nullptr;
