@@ -1545,21 +1545,57 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
     tc_fence_after();
     const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
     const int c = warp * 32 + lane;
-    float* dst = P.R + (PROJ ? P.pj_row[e] : (int64_t)e * ne + r0) * P.ldr + c0 + c;
-    const int rend = PROJ ? nrow : ne - r0;   // rows of this CTA's result
+    float* const rbase = P.R + (PROJ ? P.pj_row[e] : (int64_t)e * ne + r0) * P.ldr + c0;
+    const int rend = min(nrow, PROJ ? nrow : ne - r0);   // rows of this CTA's result
     // FP16x2: undo the cell's and the column's scales (exact powers of two)
     const float back = NT == 2 && c < ncv ? P.cinv[e] / f16_scale_of(__uint_as_float(P.cmax[c0 + c])) : 1.f;
-    for (int cb = 0; cb < nrow; cb += 16) {
-      float acc[16];
-      __syncwarp();
-      if (run) {
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
-        tmem_wait_ld();
-      }
-      if (!run || c >= ncv) continue;
+    // The result leaves through the rings, now idle (every MMA has completed):
+    // the four warps write groups of up to `cap` rows into shared memory, row
+    // r at [r][128 columns], and each thread then sends rows r = c (mod 128)
+    // with one bulk copy of ncv columns; the warps wait only until the copies
+    // have read shared memory, not for their writes to reach memory.
+    // Without 16-byte rows (ld or ncv not a multiple of 4) the threads store
+    // their column of each row directly.
+    const int cap = (SM * mstage + SY * YT) / 512 / 16 * 16;
+    if ((P.ldr & 3) == 0 && (ncv & 3) == 0 && cap >= 16) {
+      float* stage = reinterpret_cast<float*>(smem);
+      for (int g0 = 0; g0 < nrow; g0 += cap) {
+        const int g1 = min(nrow, g0 + cap);
+        for (int cb = g0; cb < g1; cb += 16) {
+          float acc[16];
+          __syncwarp();
+          if (run) {
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+            tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (cb + j < rend) dst[(int64_t)(cb + j) * P.ldr] = NT == 2 ? acc[j] * back : acc[j];
+            for (int j = 0; j < 16; ++j)
+              if (cb + j < g1) stage[(cb - g0 + j) * 128 + c] = NT == 2 ? acc[j] * back : acc[j];
+          }
+        }
+        fence_proxy_async_smem();
+        named_bar_sync(1, 128);
+        if (run) {
+          for (int r = g0 + c; r < min(g1, rend); r += 128)
+            bulk_s2g(rbase + (int64_t)r * P.ldr, smem_u32(stage + (r - g0) * 128), (uint32_t)ncv * 4);
+          bulk_commit();
+          bulk_wait_read0();
+        }
+        named_bar_sync(1, 128);   // the staging rows are free again
+      }
+    } else {
+      float* dst = rbase + c;
+      for (int cb = 0; cb < nrow; cb += 16) {
+        float acc[16];
+        __syncwarp();
+        if (run) {
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, acc);
+          tmem_wait_ld();
+        }
+        if (!run || c >= ncv) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (cb + j < rend) dst[(int64_t)(cb + j) * P.ldr] = NT == 2 ? acc[j] * back : acc[j];
+      }
     }
     }
   }
