@@ -1575,8 +1575,9 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         fence_proxy_async_smem();
         named_bar_sync(1, 128);
         if (run) {
+          const uint64_t pol = l2_evict_first();   // R is read once, by the next launch
           for (int r = g0 + c; r < min(g1, rend); r += 128)
-            bulk_s2g(rbase + (int64_t)r * P.ldr, smem_u32(stage + (r - g0) * 128), (uint32_t)ncv * 4);
+            bulk_s2g_hint(rbase + (int64_t)r * P.ldr, smem_u32(stage + (r - g0) * 128), (uint32_t)ncv * 4, pol);
           bulk_commit();
           bulk_wait_read0();
         }
