@@ -174,7 +174,13 @@ chfsi_status chfsi_set_gemm_kernels(chfsi_ctx* ctx, int tall, int gram);
  * shared by both operands; 1 = the rows staged by bulk async copies several
  * chunks ahead and split from shared memory (used when the block is 16-byte
  * aligned with a leading dimension and a column count that are multiples of
- * 4, else 0); 3 = as 2 with four gather warp pairs instead of two. */
+ * 4, else 0); 3 = as 2 with four gather warp pairs instead of two; 4 = both
+ * row parts of a cell per thread block (p = 6, 7; else 2); 5 = as 2 with
+ * three 128-column tiles per thread block, the rings running on across them
+ * and four epilogue warps; 6 = all column tiles per thread block, one block
+ * per SM with two accumulators (the MMAs of a tile overlap the epilogue of
+ * the previous one) and four gather warp pairs.  Modes 4-6 take no
+ * projector chunks (the projector term then stays in the assembly). */
 chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode);
 
 /* Cell operator of the binary64 path (every CHFSI_FP64 apply, and the

@@ -439,7 +439,7 @@ class Context:
         """BF16x3 cell kernel: "registers" (register gather, one ring), "async"
         (rows staged by bulk copies) or "rings" (register gather, separate matrix
         and Y rings)."""
-        self._check(self._lib.chfsi_set_cell_gather(self._h, {"registers": 0, "async": 1, "rings": 2, "rings4": 3, "whole": 4}[mode]))
+        self._check(self._lib.chfsi_set_cell_gather(self._h, {"registers": 0, "async": 1, "rings": 2, "rings4": 3, "whole": 4, "tiles": 5, "tiles2": 6}[mode]))
 
     def set_fp64_operator(self, op):
         """Binary64 cell operator: "cells" (stored cell matrices), "matrix-free"

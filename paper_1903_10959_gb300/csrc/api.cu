@@ -1079,9 +1079,11 @@ chfsi_status chfsi_set_cell_tile(chfsi_ctx* ctx, int tile) {
 
 chfsi_status chfsi_set_cell_gather(chfsi_ctx* ctx, int mode) {
   CHECK_CTX();
-  if (mode < 0 || mode > 4)
+  if (mode < 0 || mode > 6)
     return fail(ctx, CHFSI_ERR_ARG, "cell kernel variant: 0 one ring, 1 bulk async copies, 2 / 3 decoupled "
-                                    "rings with 2 / 4 gather warp pairs, 4 whole cell per thread block");
+                                    "rings with 2 / 4 gather warp pairs, 4 whole cell per thread block, "
+                                    "5 several column tiles per thread block, 6 the same with one thread block per SM "
+                                    "and two accumulators");
   ctx->cell_gather = mode;
   return CHFSI_OK;
 }

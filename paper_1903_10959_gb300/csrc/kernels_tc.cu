@@ -559,6 +559,7 @@ struct RParams {
   const int64_t* pj_off;
   const int64_t* pj_row;
   int pj_npmax;
+  int tpc;                  // multi-tile kernel: column tiles per CTA
 };
 
 template <int BN, bool MULTI>
@@ -1288,7 +1289,8 @@ struct BfrPlan {
 // npair gather warp pairs; each pair owns the Y stages i % npair of its
 // chunks i = pair (mod npair), so its parity waits stay sound.  nt: terms per
 // operand (3 for BF16x3, 2 for FP16x2).
-__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3, int proj_nh = 0) {
+__host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3, int proj_nh = 0,
+                                            bool one_cta = false) {
   BfPlan b = bf_plan(ne);
   if (proj_nh > 0) {   // projection blocks: one part of up to proj_nh rows
     b.np = 1;
@@ -1299,7 +1301,7 @@ __host__ __device__ inline BfrPlan bfr_plan(int ne, int npair, int nt = 3, int p
   r.np = b.np;
   r.nh = b.nh;
   r.alloc = b.alloc;
-  const int per_sm = 512 / b.alloc >= 3 ? 3 : 512 / b.alloc;
+  const int per_sm = one_cta ? 1 : (512 / b.alloc >= 3 ? 3 : 512 / b.alloc);
   const int budget = (per_sm >= 3 ? 72 : (per_sm == 2 ? 111 : 200)) * 1024 - kCellSmemTail;
   const int mstage = nt * b.nh * 32, ystage = nt * 128 * BF_KC * 2;
   r.sy = npair;
@@ -1605,6 +1607,225 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
   if (warp == WMMA) tmem_dealloc(tmem, B.alloc);
 }
 
+// ----------------------------------------------------------------- BF16x3 cell kernel, several column tiles per CTA
+// The product and arithmetic of the ring kernel (bit-identical results) with
+// one CTA per (cell, row part, group of P.tpc consecutive 128-column tiles):
+// the dof map is read once per group, both rings run on across the tiles
+// (one chunk counter g = tile * nk + chunk for slots and parities), and four
+// epilogue warps (6-9) drain each tile's accumulator while the gather warps
+// and the matrix producer already fill the rings for the next tile.  The MMA
+// warp starts a tile once the epilogue has released TMEM (tmem_empty).
+// Warps: 0-3 gather (two pairs), 4 matrix producer, 5 MMA, 6-9 epilogue.
+// NACC = 2: one CTA per SM with two TMEM accumulators (tile t in columns
+// 256 (t % 2) ..), so the MMAs of tile t + 1 run while the epilogue drains
+// tile t, deeper rings (the whole shared memory) and NPAIR gather pairs.
+constexpr int kTilesPerCta = 3;
+template <int NPAIR, int NACC>
+__global__ void __launch_bounds__((2 * NPAIR + 6) * 32, NACC == 1 ? 2 : 1) tc_cell_bf16_tiles_kernel(RParams P) {
+  constexpr int NT = 3, WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1, WEPI = 2 * NPAIR + 2;
+  constexpr int BFT_THREADS = (2 * NPAIR + 6) * 32;
+  constexpr int YT = NT * 128 * BF_KC * 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t e = P.e_off + blockIdx.y;
+  const int ne = P.ne, nk = P.nk;
+  const BfrPlan B = bfr_plan(ne, NPAIR, NT, 0, NACC == 2);
+  const int nrow = B.nh;
+  const int h = blockIdx.x % B.np;
+  const int ntiles = (P.ncol + 127) / 128;
+  const int t0 = (blockIdx.x / B.np) * P.tpc;
+  const int nt = min(P.tpc, ntiles - t0);   // tiles of this CTA (>= 1)
+  const int r0 = h * B.nh;
+  const int SM = B.sm, SY = B.sy;
+  const int hrow = nrow * 32;
+  const int mstage = NT * B.nh * 32;
+  unsigned char* ybase = smem + SM * mstage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ybase + SY * YT);
+  // fa[SM], ea[SM], fy[SY], ey[SY], acc[NACC] (MMA -> epilogue), tmem_empty[NACC] (epilogue -> MMA)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SM + 2 * SY + 2 * NACC);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int32_t* dm = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(bars) + 256);
+  const uint32_t mbase = smem_u32(smem);
+  const uint32_t ysb = smem_u32(ybase);
+  auto fa = [&](int q) { return smem_u32(bars + q); };
+  auto ea = [&](int q) { return smem_u32(bars + SM + q); };
+  auto fy = [&](int q) { return smem_u32(bars + 2 * SM + q); };
+  auto ey = [&](int q) { return smem_u32(bars + 2 * SM + SY + q); };
+  auto accb = [&](int b) { return smem_u32(bars + 2 * SM + 2 * SY + b); };
+  auto tmeb = [&](int b) { return smem_u32(bars + 2 * SM + 2 * SY + NACC + b); };
+  const uint32_t acols = NACC == 2 ? 512u : (uint32_t)B.alloc;
+
+  if (tid == 0) {
+    for (int q = 0; q < SM; ++q) {
+      mbar_init(fa(q), 1);
+      mbar_init(ea(q), 1);
+    }
+    for (int q = 0; q < SY; ++q) {
+      mbar_init(fy(q), 64);
+      mbar_init(ey(q), 1);
+    }
+    for (int b = 0; b < NACC; ++b) {
+      mbar_init(accb(b), 1);
+      mbar_init(tmeb(b), 128);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == WMMA) {
+    tmem_alloc(smem_u32(tmem_slot), acols);
+    tmem_relinquish();
+  }
+  for (int l = tid; l < ne; l += BFT_THREADS) dm[l] = P.dofmap[e * ne + l];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int G = nt * nk;   // chunks of this CTA
+
+  if (warp == WPROD) {
+    if (lane == 0) {
+      const int64_t term_bytes = (int64_t)P.mt * 4096;
+      const char* Ae = reinterpret_cast<const char*>(P.A) + e * (int64_t)nk * NT * term_bytes + (int64_t)r0 * 32;
+      int issued = 0;
+      for (int g = 0; g < G; ++g) {
+        const int q = g % SM, i = g % nk;
+        if (g >= SM && !mbar_wait(ea(q), ((g / SM) - 1) & 1)) {
+          atomicExch(&g_tc_status, 51);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        const uint32_t dst = mbase + q * mstage;
+        mbar_arrive_expect_tx(fa(q), NT * hrow);
+#pragma unroll
+        for (int p = 0; p < NT; ++p)
+          bulk_g2s(dst + p * hrow, Ae + ((int64_t)i * NT + p) * term_bytes, hrow, fa(q));
+        ++issued;
+      }
+      if (*(volatile int*)abort_flag)
+        for (int g = max(0, issued - SM); g < issued; ++g) mbar_wait(fa(g % SM), (g / SM) & 1);
+    }
+  } else if (warp == WMMA) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, nrow);
+      bool ok = true;
+      for (int t = 0; t < nt && ok; ++t) {
+        const int b = t % NACC;   // accumulator of tile t
+        if (t >= NACC && !mbar_wait(tmeb(b), ((t / NACC) - 1) & 1)) {   // drained tile t - NACC
+          atomicExch(&g_tc_status, 52);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(b * 256);
+        for (int i = 0; i < nk; ++i) {
+          const int g = t * nk + i;
+          const int sa = g % SM, sy = g % SY;
+          if (!mbar_wait(fa(sa), (g / SM) & 1) || !mbar_wait(fy(sy), (g / SY) & 1) ||
+              *(volatile int*)abort_flag) {
+            atomicExch(&g_tc_status, 53);
+            *(volatile int*)abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t yb = ysb + sy * YT;
+          const uint32_t hb = mbase + sa * mstage;
+          uint64_t y[NT], hd[NT];
+#pragma unroll
+          for (int p = 0; p < NT; ++p) {
+            y[p] = umma_desc(yb + p * 4096, 128, 256);
+            hd[p] = umma_desc(hb + p * hrow, 128, 256);
+          }
+          mma_f16(dacc, y[0], hd[2], idesc, i > 0);
+          mma_f16(dacc, y[1], hd[1], idesc, 1);
+          mma_f16(dacc, y[2], hd[0], idesc, 1);
+          mma_f16(dacc, y[0], hd[1], idesc, 1);
+          mma_f16(dacc, y[1], hd[0], idesc, 1);
+          mma_f16(dacc, y[0], hd[0], idesc, 1);
+          umma_commit(ea(sa));
+          umma_commit(ey(sy));
+        }
+        if (ok) umma_commit(accb(b));   // tile t's accumulator is complete
+      }
+    }
+  } else if (warp < 2 * NPAIR) {
+    // gather + split as the ring kernel; chunk g of this CTA is gathered by pair g % NPAIR
+    const int pair = warp >> 1, qw = warp & 1;
+    const bool withhold = g_tc_withhold != 0 && blockIdx.x == 0 && blockIdx.y == 0 && P.e_off == 0;
+    for (int g = pair; g < G; g += NPAIR) {
+      const int t = g / nk, i = g - t * nk;
+      const int c0 = (t0 + t) * 128, ncv = min(128, P.ncol - c0);
+      const int s = g % SY;
+      float v[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int l = i * BF_KC + qw * 8 + a;
+        const int gr = l < ne ? dm[l] : -1;
+        const float* src = P.Yin + (int64_t)(gr < 0 ? 0 : gr) * P.ld_in + c0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = lane + 32 * u;
+          v[a][u] = (gr >= 0 && c < ncv) ? __ldg(src + c) : 0.f;
+        }
+      }
+      if (g >= SY && !mbar_wait(ey(s), ((g / SY) - 1) & 1)) {
+        atomicExch(&g_tc_status, 54);
+        *(volatile int*)abort_flag = 1;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint16_t* ys = reinterpret_cast<uint16_t*>(ybase + s * YT);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = bf_elem_off(lane + 32 * u, qw * 8);
+        uint32_t w[NT][4];
+#pragma unroll
+        for (int a = 0; a < 8; a += 2) bf16_split3_pair(v[a][u], v[a + 1][u], w[0][a / 2], w[1][a / 2], w[2][a / 2]);
+#pragma unroll
+        for (int p = 0; p < NT; ++p)
+          *reinterpret_cast<uint4*>(ys + p * 128 * BF_KC + o) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async_smem();
+      if (!(withhold && warp == 0 && g == 0)) mbar_arrive(fy(s));
+    }
+  } else {
+    // epilogue warps: TMEM lane quarter warp % 4, column c of each tile
+    const int quarter = warp & 3, c = quarter * 32 + lane;
+    const uint64_t pol = l2_evict_first();   // R is read once, by the next launch
+    const int rend = min(nrow, ne - r0);
+    for (int t = 0; t < nt; ++t) {
+      const int b = t % NACC;
+      const bool okacc = mbar_wait(accb(b), (t / NACC) & 1);
+      if (!okacc) {
+        atomicExch(&g_tc_status, 55);
+        *(volatile int*)abort_flag = 1;
+      }
+      tc_fence_after();
+      const bool run = __all_sync(0xffffffffu, okacc && !*(volatile int*)abort_flag);
+      const int c0 = (t0 + t) * 128, ncv = min(128, P.ncol - c0);
+      float* dst = P.R + ((int64_t)e * ne + r0) * P.ldr + c0 + c;
+      for (int cb = 0; cb < nrow; cb += 16) {
+        float acc[16];
+        __syncwarp();
+        if (run) {
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + b * 256 + cb, acc);
+          tmem_wait_ld();
+        }
+        if (!run || c >= ncv) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (cb + j < rend) st_global_hint(dst + (int64_t)(cb + j) * P.ldr, acc[j], pol);
+      }
+      tc_fence_before();
+      if (!run) break;
+      mbar_arrive(tmeb(b));   // TMEM columns of tile t free for tile t + NACC
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WMMA) tmem_dealloc(tmem, acols);
+}
+
 // ----------------------------------------------------------------- BF16x3 cell kernel, whole cell per CTA
 // For cells split into two row parts (p = 6, 7): one CTA per (cell, 128-column
 // tile) computes both parts into two TMEM accumulators (columns [0, nh) and
@@ -1857,11 +2078,30 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
                          200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(tc_cell_bf16_whole_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_tiles_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(tc_cell_bf16_tiles_kernel<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
   const bool async = a.gather == 1 && tc_cell_bf16_async_ok(a);
   const BfaPlan BA = bfa_plan(d.ne);
   const BfrPlan BR = bfr_plan(d.ne, 2), BR4 = bfr_plan(d.ne, 4);
   const BfwPlan BW = bfw_plan(d.ne);
+  if ((a.gather == 5 || a.gather == 6) && !P.nlA) {   // several column tiles per CTA
+    const bool two = a.gather == 6;   // one CTA per SM, two accumulators, all tiles of a row part
+    const int ntiles = (a.ncol + 127) / 128;
+    P.tpc = two ? ntiles : std::min(ntiles, kTilesPerCta);
+    const int ngroups = (ntiles + P.tpc - 1) / P.tpc;
+    const BfrPlan BT = bfr_plan(d.ne, 4, 3, 0, true);
+    for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
+      P.e_off = e0;
+      dim3 grid((unsigned)(ngroups * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));
+      note_launch();
+      if (two)
+        tc_cell_bf16_tiles_kernel<4, 2><<<grid, 14 * 32, BT.total, s>>>(P);
+      else
+        tc_cell_bf16_tiles_kernel<2, 1><<<grid, 10 * 32, BR.total, s>>>(P);
+    }
+    return cudaGetLastError();
+  }
   for (int64_t e0 = 0; e0 < a.ncells; e0 += 65535) {
     P.e_off = e0;
     dim3 grid((unsigned)(((a.ncol + 127) / 128) * B.np), (unsigned)std::min<int64_t>(65535, a.ncells - e0));

@@ -82,6 +82,10 @@ __device__ __forceinline__ void bulk_s2g_hint(void* dst, uint32_t src, uint32_t 
                "r"(src), "r"(bytes), "l"(pol)
                : "memory");
 }
+// Global binary32 store under an L2 policy.
+__device__ __forceinline__ void st_global_hint(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
 // L2 policy: lines written or read under it are the first to be evicted.
 __device__ __forceinline__ uint64_t l2_evict_first() {
   uint64_t pol;

@@ -1,5 +1,6 @@
-"""The BF16x3 cell kernel variants -- the bulk-async-copy gather and the
-decoupled matrix / Y rings -- give the same bits as the register gather
+"""The BF16x3 cell kernel variants -- the bulk-async-copy gather, the
+decoupled matrix / Y rings, the whole cell per CTA and several column tiles
+per CTA -- give the same bits as the register gather
 (same split, same MMA order, same tiling), for every
 FE degree the kernel plans for, Dirichlet rows, ragged last column tiles and
 several 128-column tiles; an unaligned block falls back to the register
@@ -38,7 +39,7 @@ def test_async_gather_is_bit_identical(p, periodic):
     ctx = gpu_context(s)
     prob = oracle_problem(s)
     try:
-        for ncol in (4, 132, 260):                 # one ragged tile, 2 and 3 tiles
+        for ncol in (4, 132, 260, 520):            # one ragged tile, 2, 3 and 5 tiles
             x = W.start_block(ncol, ctx.ndofs, ncol).astype(np.float32)
             X = torch.tensor(x, device=DEV)
             ya = _apply(ctx, X, "async")
@@ -46,7 +47,11 @@ def test_async_gather_is_bit_identical(p, periodic):
             yg = _apply(ctx, X, "rings")
             y4 = _apply(ctx, X, "rings4")
             yw = _apply(ctx, X, "whole")
+            yt = _apply(ctx, X, "tiles")              # 3 tiles per CTA: groups of 1, 2, 3, 3 + 2
+            y2 = _apply(ctx, X, "tiles2")             # all tiles per CTA, two accumulators
             assert torch.equal(yw, yr), (p, periodic, ncol)
+            assert torch.equal(y2, yr), (p, periodic, ncol)
+            assert torch.equal(yt, yr), (p, periodic, ncol)
             assert torch.equal(ya, yr), (p, periodic, ncol)
             assert torch.equal(yg, yr), (p, periodic, ncol)
             assert torch.equal(y4, yr), (p, periodic, ncol)
