@@ -140,7 +140,7 @@ constexpr bool kMatrixFreeDefault = true;
 // blocks, projector and binary64 staging buffers); later calls regrow it.
 void release_scratch(chfsi_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot, &ctx->cmaxb, &ctx->pjb}) {
+  for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->Rb, &ctx->rot, &ctx->cmaxb, &ctx->pjb, &ctx->tinv}) {
     dfree(ctx, b->ptr, b->bytes);
     b->ptr = nullptr;
     b->bytes = 0;
@@ -611,15 +611,25 @@ chfsi_status cholgs_impl(chfsi_ctx* ctx, void* X, int64_t ldx, int n, chfsi_prec
   CK(cudaStreamSynchronize(ctx->stream));
   if (info != 0)
     return fail(ctx, CHFSI_ERR_NOT_SPD, "CholGS: potrf info = " + std::to_string(info));
-  // 3. L^{-1} (lower, in place)
-  std::vector<char> hwork(hws + 16);
-  CS(cusolverDnXtrtri(ctx->sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, S, n,
-                      ctx->work.ptr, dws, hwork.data(), hws, dinfo));
-  CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (info != 0) return fail(ctx, CHFSI_ERR_NOT_SPD, "CholGS: trtri info = " + std::to_string(info));
+  // 3. L^{-1} (lower triangle; the strict upper triangle zero): the
+  // warp-per-column forward substitution of kernels_fp64.cu (L_ii > 0 after
+  // potrf), cuSOLVER's trtri in place beyond its shared-memory limit
+  double* Linv = S;
+  if (trinv_lower_supported(n)) {
+    if ((st = grow(ctx, ctx->tinv, (size_t)n * n * 8)) != CHFSI_OK) return st;
+    Linv = (double*)ctx->tinv.ptr;
+    CK(cudaMemsetAsync(Linv, 0, (size_t)n * n * 8, ctx->stream));
+    CK(launch_trinv_lower_fp64(S, n, n, Linv, n, ctx->stream));
+  } else {
+    std::vector<char> hwork(hws + 16);
+    CS(cusolverDnXtrtri(ctx->sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n, CUDA_R_64F, S, n,
+                        ctx->work.ptr, dws, hwork.data(), hws, dinfo));
+    CK(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (info != 0) return fail(ctx, CHFSI_ERR_NOT_SPD, "CholGS: trtri info = " + std::to_string(info));
+  }
   // 4. X <- X L^{-T}: U(k, j) = Linv(j, k), nonzero for k <= j
-  return rotate_impl(ctx, prec, X, ldx, n, S, 1, 1);
+  return rotate_impl(ctx, prec, X, ldx, n, Linv, 1, 1);
 }
 
 // Rayleigh-Ritz.  fp64_apply: for the mixed precisions, evaluate H~ X with the
@@ -893,7 +903,7 @@ chfsi_status chfsi_destroy(chfsi_ctx* ctx) {
     if (q) cudaFree(q);
   for (DevBuf* b : {&ctx->T1, &ctx->Wb, &ctx->NLb, &ctx->Zb, &ctx->rot, &ctx->Ssq, &ctx->work,
                     &ctx->part, &ctx->vec, &ctx->lam, &ctx->Rb, &ctx->Db, &ctx->pol, &ctx->scfb, &ctx->scfq,
-                    &ctx->cmaxb, &ctx->pjb,
+                    &ctx->cmaxb, &ctx->pjb, &ctx->tinv,
                     &ctx->scfr, &ctx->scfw, &ctx->kW, &ctx->kT1, &ctx->kG, &ctx->kS, &ctx->kwork,
                     &ctx->kY, &ctx->kvec})
     dfree(ctx, b->ptr, b->bytes);

@@ -78,6 +78,7 @@ struct chfsi_ctx {
   chfsi::DevBuf laneT1[kMaxLanes], laneR[kMaxLanes], laneZ[kMaxLanes], laneC[kMaxLanes], laneP[kMaxLanes];
   chfsi::DevBuf cmaxb;             // FP16x2: column maxima of the filter's blocks (3 x ncol words)
   chfsi::DevBuf pjb;               // partial projections of the cells (pj_rows x ncol)
+  chfsi::DevBuf tinv;              // CholGS: L^{-1} (n x n binary64)
   cusolverDnHandle_t sol = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   double times[4] = {0, 0, 0, 0};

@@ -215,6 +215,11 @@ cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* X, in
 cudaError_t launch_axpy2(double* w, const double* v, const double* vp, int64_t M, double a,
                          double b, cudaStream_t s);
 cudaError_t launch_scal_copy(double* v, const double* w, int64_t M, double sc, cudaStream_t s);
+// X (lower triangle, column-major ldx) = L^{-1} for a lower triangular L
+// (column-major ldl, diagonal nonzero); X's strict upper triangle untouched.
+bool trinv_lower_supported(int n);
+cudaError_t launch_trinv_lower_fp64(const double* L, int64_t ldl, int n, double* X, int64_t ldx,
+                                    cudaStream_t s);
 
 // nonlocal: Z (nproj x ncol) = C~ Y ; NL (M x ncol) = C~^T h Z
 cudaError_t launch_nl_project_fp64(const int64_t* site_ptr, const int32_t* site_dof,

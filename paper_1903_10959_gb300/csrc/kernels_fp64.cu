@@ -526,4 +526,78 @@ cudaError_t launch_scal_copy(double* v, const double* w, int64_t M, double sc, c
   return cudaGetLastError();
 }
 
+// Inverse of a lower triangular binary64 matrix: the factor L of CholGS
+// (Algorithm CholGS, S = L L^T, then X <- X L^{-T}).  Column j of L^{-1} is
+// the forward substitution L x = e_j, one warp per column.  The warp walks its
+// rows in blocks of 32: lane l holds row k0 + l of the block and its 32
+// entries of L to the left of the diagonal; the block is solved in 32 steps
+// (x_t = b_t / L_tt broadcast by shuffle, the lanes below subtract L_lt x_t);
+// then every row below the block subtracts the block's 32 products at once,
+// with 32 independent coalesced loads of L per row (lanes over consecutive
+// rows), from a right-hand side kept in shared memory.  Summation order:
+// along increasing k within and across blocks, as a column-oriented forward
+// substitution.
+constexpr int TRI_WARPS = 4;
+__global__ void __launch_bounds__(TRI_WARPS * 32) trinv_lower_kernel(const double* __restrict__ L, int64_t ldl,
+                                                                     int n, double* __restrict__ X, int64_t ldx) {
+  extern __shared__ double tsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * TRI_WARPS + warp;
+  if (j >= n) return;                         // warp-uniform; the kernel uses no block barrier
+  double* b = tsm + (size_t)warp * (n + 32);  // right-hand side, b[r] for row j + r
+  double* xs = b + n;                         // the current block's solution
+  const int m = n - j;
+  for (int r = lane; r < m; r += 32) b[r] = r == 0 ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    const int kb = min(32, m - k0);
+    const int r = k0 + lane;
+    const bool own = lane < kb;
+    const int64_t i = (int64_t)j + r;
+    const double* Lrow = L + i + (int64_t)(j + k0) * ldl;   // L(i, j + k0 + t) at Lrow[t * ldl]
+    double Ld[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) Ld[t] = (own && t < lane) ? Lrow[(int64_t)t * ldl] : 0.0;
+    const double invd = own ? 1.0 / L[i + i * ldl] : 0.0;
+    double bi = own ? b[r] : 0.0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < kb) {
+        const double xt = __shfl_sync(0xffffffffu, bi * invd, t);
+        if (lane > t) bi = fma(-Ld[t], xt, bi);
+      }
+    }
+    const double x = bi * invd;
+    if (own) {
+      X[i + (int64_t)j * ldx] = x;
+      xs[lane] = x;
+    }
+    __syncwarp();
+    // rows below the block: b[r2] -= sum_t L(j + r2, j + k0 + t) x_t
+    for (int r2 = k0 + 32 + lane; r2 < m; r2 += 32) {
+      const double* Lr = L + (int64_t)j + r2 + (int64_t)(j + k0) * ldl;
+      double acc = b[r2];
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < kb) acc = fma(-Lr[(int64_t)t * ldl], xs[t], acc);
+      b[r2] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+bool trinv_lower_supported(int n) { return n > 0 && (size_t)TRI_WARPS * (n + 32) * 8 <= 200 * 1024; }
+
+cudaError_t launch_trinv_lower_fp64(const double* L, int64_t ldl, int n, double* X, int64_t ldx,
+                                    cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (!trinv_lower_supported(n)) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)TRI_WARPS * (n + 32) * 8;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(trinv_lower_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
+  trinv_lower_kernel<<<(unsigned)((n + TRI_WARPS - 1) / TRI_WARPS), TRI_WARPS * 32, smem, s>>>(L, ldl, n, X, ldx);
+  return cudaGetLastError();
+}
+
 }  // namespace chfsi
