@@ -115,6 +115,25 @@ def test_cholgs_parity(case):
     assert np.abs(Q.T @ Q - np.eye(23)).max() < 1e-13
 
 
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 65, 200])
+def test_cholgs_widths_around_the_inverse_blocks(n):
+    """CholGS at widths on both sides of the 32-row blocks of the library's
+    triangular inverse (one column, one short block, exactly one block, one
+    block and a row, several blocks with a ragged tail) against the oracle's
+    CholGS (Algorithm CholGS), and the block's orthonormality."""
+    s = _sys("c1")
+    ctx = gpu_context(s)
+    try:
+        X0 = W.start_block(40 + n, ctx.ndofs, n)
+        X = torch.tensor(X0, device=DEV)
+        ctx.cholgs(X)
+        Q = X.cpu().numpy()
+        assert rel_fro(Q, och.cholgs(X0)) < 1e-12
+        assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-13
+    finally:
+        ctx.destroy()
+
+
 def test_rayleigh_ritz_parity(case):
     s, prob, ctx = case
     X0 = och.cholgs(W.start_block(8, prob.ndofs, 21))
