@@ -353,8 +353,11 @@ def rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks, cell_ms, c
     executes per algorithmic flop are reported beside it, not folded into the
     peak.  Algorithmic bytes per launch = the cell matrices (N_c n_e^2 s_H) +
     the block read (M nb s_X) + the dense cell blocks written (N_c n_e nb s_X).
-    Assembly: the cell blocks read, Y_in / Y_prev read and Y_out written
-    (3 M nb s_X) and the unknown -> cell-row table ((M + 1 + N_c n_e) 4 B).
+    Assembly: the cell blocks read and Y_out written by every launch, Y_in
+    read by the m filter steps and Y_prev by the m - 1 after the first (the
+    application of H~ in Rayleigh-Ritz reads neither), the unknown -> cell-row
+    table ((M + 1 + N_c n_e) 4 B), and the projector term where the assembly
+    reads it.
     Filter step: cell kernel + assembly against the fused-recurrence minimum
     (3 s_X per unknown and vector + the cell matrices at s_H)."""
     ne = (s.p + 1) ** 3
@@ -393,10 +396,16 @@ def rooflines(prec, s, n, M, peaks, col_steps, steps_blocks, nblocks, cell_ms, c
     roof["executed_mma"] = {"passes_per_flop": passes, "tflops": passes * achieved,
                             "frac_of_peak": passes * achieved / peak,
                             "note": "MMA work the split-precision scheme issues (not the method's work)"}
-    asm_bytes = (col_steps * ncells * ne * sx + col_steps * 3 * M * sx
+    # every assembly launch reads the cell blocks and writes Y_out; the filter's
+    # degree steps also read Y_in (the shift) and, after the first, Y_prev; the
+    # application of H~ in Rayleigh-Ritz (one launch per block and iteration)
+    # reads neither
+    it_cols = col_steps / (s.degree + 1)
+    asm_bytes = (col_steps * (ncells * ne + M) * sx + it_cols * (2 * s.degree - 1) * M * sx
                  + steps_blocks * nblocks * (M + 1 + ncells * ne) * 4)
-    if len(s.nl_centres):
-        asm_bytes += col_steps * M * sx          # the projector term read by the assembly
+    if len(s.nl_centres) and not (prec == "bf16x3" and gather in ("rings", "rings4")):
+        asm_bytes += col_steps * M * sx          # the projector term, read by the assembly unless
+                                                 # the ring kernel took it as extra K-chunks
     asm_roof = {"bound": "hbm", "achieved": asm_bytes / (asm_ms / 1e3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "kernel": "tc_assemble_kernel",
                 "launches": int(asm_n), "avg_launch_ms": asm_ms / max(asm_n, 1),
