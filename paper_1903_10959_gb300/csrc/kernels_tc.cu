@@ -560,6 +560,7 @@ struct RParams {
   const int64_t* pj_row;
   int pj_npmax;
   int tpc;                  // multi-tile kernel: column tiles per CTA
+  int r_evict;              // write R under an evict_first L2 policy (R much larger than L2)
 };
 
 template <int BN, bool MULTI>
@@ -1577,9 +1578,16 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
         fence_proxy_async_smem();
         named_bar_sync(1, 128);
         if (run) {
-          const uint64_t pol = l2_evict_first();   // R is read once, by the next launch
-          for (int r = g0 + c; r < min(g1, rend); r += 128)
-            bulk_s2g_hint(rbase + (int64_t)r * P.ldr, smem_u32(stage + (r - g0) * 128), (uint32_t)ncv * 4, pol);
+          // R is read once, by the next launch: when it cannot stay in L2 it
+          // is written as the first to be evicted, ahead of the Y rows and
+          // cell matrices the other CTAs still read
+          const uint64_t pol = l2_evict_first();
+          for (int r = g0 + c; r < min(g1, rend); r += 128) {
+            float* d = rbase + (int64_t)r * P.ldr;
+            const uint32_t sa = smem_u32(stage + (r - g0) * 128);
+            if (P.r_evict) bulk_s2g_hint(d, sa, (uint32_t)ncv * 4, pol);
+            else bulk_s2g(d, sa, (uint32_t)ncv * 4);
+          }
           bulk_commit();
           bulk_wait_read0();
         }
@@ -1620,6 +1628,7 @@ __global__ void __launch_bounds__((2 * NPAIR + 2) * 32, 2) tc_cell_bf16_rings_ke
 // 256 (t % 2) ..), so the MMAs of tile t + 1 run while the epilogue drains
 // tile t, deeper rings (the whole shared memory) and NPAIR gather pairs.
 constexpr int kTilesPerCta = 3;
+constexpr double kL2Bytes = 129.0 * 1024 * 1024;   // GB300 L2
 template <int NPAIR, int NACC>
 __global__ void __launch_bounds__((2 * NPAIR + 6) * 32, NACC == 1 ? 2 : 1) tc_cell_bf16_tiles_kernel(RParams P) {
   constexpr int NT = 3, WPROD = 2 * NPAIR, WMMA = 2 * NPAIR + 1, WEPI = 2 * NPAIR + 2;
@@ -1814,7 +1823,10 @@ __global__ void __launch_bounds__((2 * NPAIR + 6) * 32, NACC == 1 ? 2 : 1) tc_ce
         if (!run || c >= ncv) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (cb + j < rend) st_global_hint(dst + (int64_t)(cb + j) * P.ldr, acc[j], pol);
+          if (cb + j < rend) {
+            if (P.r_evict) st_global_hint(dst + (int64_t)(cb + j) * P.ldr, acc[j], pol);
+            else dst[(int64_t)(cb + j) * P.ldr] = acc[j];
+          }
       }
       tc_fence_before();
       if (!run) break;
@@ -2041,6 +2053,7 @@ cudaError_t tc_cell_bf16_launch(const TcCellData& d, const TcApplyArgs& a, cudaS
   if (B.np * B.nh > d.mt * 128) return cudaErrorInvalidValue;   // parts stay inside the packed rows
   RParams P{reinterpret_cast<const float*>(d.bf), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
             nk16, 1, nullptr, 0, 0, a.ncol, 0};
+  P.r_evict = (double)a.ncells * d.ne * a.ncol * 4 > 2.0 * kL2Bytes;
   if (a.Z) {   // projector chunks: only the ring kernels take them
     if (!d.nl || !tc_cell_bf16_nl_ok(a.gather)) return cudaErrorInvalidValue;
     P.nlA = d.nl;
@@ -2135,6 +2148,7 @@ cudaError_t tc_cell_f16_launch(const TcCellData& d, const TcApplyArgs& a, const 
   if (B.np * B.nh > d.mt * 128) return cudaErrorInvalidValue;
   RParams P{reinterpret_cast<const float*>(d.f16), a.dofmap, a.Yin, a.R, a.ld_in, a.ncol, d.ne, d.mt,
             nk16, 1, nullptr, 0, 0, a.ncol, 0, cmax, d.f16_inv};
+  P.r_evict = (double)a.ncells * d.ne * a.ncol * 4 > 2.0 * kL2Bytes;
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_cell_bf16_rings_kernel<2, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
