@@ -95,7 +95,7 @@ size_t estimate_bytes(const chfsi_request& r) {
   b += M * B * es + M * B * 8;                                      // filter block, binary64 apply
   if (mixed) b += ncells * ne * B * 4;                              // dense cell blocks R_e
   b += std::max(n * n * 128 + (mixed ? ((size_t)64 << 20) : 0), n * 12288);  // Gram partials
-  b += n * n * 8 * 4 + n * 64 + 4096;                               // N x N, solver workspace
+  b += n * n * 8 * 5 + n * 64 + 4096;                               // N x N (S / H^, L^{-1}), solver workspace
   b += M * 24 + ((size_t)16 << 20);                                 // vectors, library slack
   if (mixed && r.polish_iters > 0)                                  // binary64 polish: staging
     b += M * n * 8 + M * n * 4 + M * B * 4;                         //  block, rotation, filter
