@@ -1,4 +1,6 @@
-"""chfsi_apply_noalloc: H~ X without device allocation, against chfsi_apply.
+"""chfsi_apply_noalloc: H~ X without device allocation, against the oracle's
+H~ X (Eqs. discreteHam, nonlocalHamDiscrete in the standard form of Eq. hep)
+and against chfsi_apply.
 
 The no-allocation entry point is for callers that cannot call cudaMalloc
 inside their step (a host framework whose own pool allocator owns the GPU's
@@ -15,7 +17,7 @@ import torch
 
 from paper_1903_10959_gb300 import ChfsiError, workloads as W
 
-from gpu_util import gpu_context, rel_fro
+from gpu_util import gpu_context, oracle_problem, rel_fro
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -35,14 +37,18 @@ def test_noalloc_apply_matches_apply_twice(which):
     ctx = gpu_context(s)
     try:
         ncol = 37
-        X = torch.tensor(W.start_block(5, ctx.ndofs, ncol), device=DEV)
+        X0 = W.start_block(5, ctx.ndofs, ncol)
+        X = torch.tensor(X0, device=DEV)
         Yref = torch.empty_like(X)
         ctx.apply(X, Yref)
         ref = Yref.cpu().numpy()
+        oracle = oracle_problem(s).apply_Htilde(X0)
         for _ in range(2):            # the shared scratch keeps the last call's contents
             Y = torch.full_like(X, float("nan"))
             ctx.apply_noalloc(X, Y)
-            assert rel_fro(Y.cpu().numpy(), ref) <= 1e-13
+            got = Y.cpu().numpy()
+            assert rel_fro(got, oracle) <= 1e-13
+            assert rel_fro(got, ref) <= 1e-13
     finally:
         ctx.destroy()
 
