@@ -170,3 +170,39 @@ def test_dropped_four_pi_in_poisson_is_caught(monkeypatch):
     phi = scf.poisson_periodic(prob, amp * np.cos(k * xq[..., 0]))
     exact = 4 * np.pi * amp / k ** 2 * np.cos(k * prob.mesh.dof_coords()[:, 0])
     assert np.abs(phi - exact).max() > 0.5 * np.abs(exact).max()
+
+
+def _mf_vs_dense_error():
+    """Relative difference of the oracle's matrix-free apply and its dense
+    cell-matrix apply (the pin of test_oracle_matrix_free.py) on a small
+    periodic box with wells."""
+    from oracle import matrix_free as mf
+    rng = np.random.default_rng(2)
+    c, d, w = rng.uniform(0, 5, (3, 3)), rng.uniform(1, 3, 3), rng.uniform(0.8, 1.2, 3)
+    prob = ham.wells_problem(2, 5, 5.0, True, c, d, w)
+    X = rng.uniform(-1, 1, (prob.ndofs, 4))
+    ref = prob.apply_Htilde(X)
+    return np.linalg.norm(mf.apply_Htilde(prob, X) - ref) / np.linalg.norm(ref)
+
+
+def test_matrix_free_quadrature_weight_without_jacobian_is_caught(monkeypatch):
+    from oracle import matrix_free as mf
+    assert _mf_vs_dense_error() < 1e-13
+    init = mf.MatrixFreeCell.__init__
+
+    def bad(self, p, h, q=None):
+        init(self, p, h, q)
+        self.W = self.W / (h / 2.0) ** 3          # potential weights without jac^3
+    monkeypatch.setattr(mf.MatrixFreeCell, "__init__", bad)
+    assert _mf_vs_dense_error() > 1e-3
+
+
+def test_matrix_free_mass_and_stiffness_factors_swapped_is_caught(monkeypatch):
+    from oracle import matrix_free as mf
+    init = mf.MatrixFreeCell.__init__
+
+    def bad(self, p, h, q=None):
+        init(self, p, h, q)
+        self.A, self.S = self.S, self.A           # the 1-D factors in each other's place
+    monkeypatch.setattr(mf.MatrixFreeCell, "__init__", bad)
+    assert _mf_vs_dense_error() > 1e-3
