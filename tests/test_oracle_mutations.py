@@ -206,3 +206,21 @@ def test_matrix_free_mass_and_stiffness_factors_swapped_is_caught(monkeypatch):
         self.A, self.S = self.S, self.A           # the 1-D factors in each other's place
     monkeypatch.setattr(mf.MatrixFreeCell, "__init__", bad)
     assert _mf_vs_dense_error() > 1e-3
+
+
+def test_shared_wrong_exchange_constant_is_caught(monkeypatch):
+    """Both LDA exchange functions with 3 / (2 pi) in place of 3 / pi stay
+    consistent with each other (the derivative pin holds) but miss the
+    uniform-gas constant."""
+    from oracle import scf
+    monkeypatch.setattr(scf, "lda_exchange_energy_density",
+                        lambda rho: -0.75 * np.cbrt(3.0 * np.maximum(rho, 0.0) / (2 * np.pi)))
+    monkeypatch.setattr(scf, "lda_exchange_potential",
+                        lambda rho: -np.cbrt(3.0 * np.maximum(rho, 0.0) / (2 * np.pi)))
+    rho = np.array([0.05, 0.4])
+    h = 1e-6 * rho
+    e = lambda r: r * scf.lda_exchange_energy_density(r)
+    assert np.allclose(scf.lda_exchange_potential(rho), (e(rho + h) - e(rho - h)) / (2 * h), rtol=1e-7)
+    rs = 1.0
+    eps = scf.lda_exchange_energy_density(np.array([3.0 / (4.0 * np.pi * rs ** 3)]))[0] * rs
+    assert abs(eps + 0.4581652932831429) > 1e-2

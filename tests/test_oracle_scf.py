@@ -42,6 +42,17 @@ def test_exchange_potential_is_the_energy_derivative():
     assert np.allclose(scf.lda_exchange_potential(rho), fd, rtol=1e-7)
 
 
+def test_exchange_energy_of_the_uniform_gas():
+    """Dirac exchange of the uniform electron gas: the energy per electron is
+    -(3/4)(9 / (4 pi^2))^{1/3} / r_s = -0.4581652932831429 / r_s Ha, with
+    rho = 3 / (4 pi r_s^3) (the textbook constant of the local density
+    approximation's exchange part)."""
+    for rs in (0.5, 1.0, 2.0, 5.0):
+        rho = 3.0 / (4.0 * np.pi * rs ** 3)
+        assert scf.lda_exchange_energy_density(np.array([rho]))[0] * rs == pytest.approx(-0.4581652932831429,
+                                                                                       rel=1e-13)
+
+
 def test_anderson_terminates_on_a_linear_fixed_point():
     """Anderson mixing with full history on x = G x + c is GMRES on
     (I - G) x = c: exact after at most n + 1 steps."""
